@@ -1,0 +1,205 @@
+"""DNN-SP2-PT in plain FP64 numpy, in the order of Algorithms 1-3 (oracle).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+The recursion (Sec. II B, Eq. (LinTransf), Eq. (eq:Sn); Sec. III A,
+Eq. (initialization), Eq. (S_n detailed), Eq. (dB)):
+
+    S_0   = (eps_N I - H) / (eps_N - eps_1)          initial normalisation
+    S1_0  = -H1 / (eps_N - eps_1)                     (Sec. III A, S_0(lambda))
+    X_n   = S_{n-1}^2                                 activation f^(0)
+    X1_n  = S_{n-1} S1_{n-1} + S1_{n-1} S_{n-1}       activation f^(1)
+    S_n   = sigma_n X_n  + (1 - sigma_n) S_{n-1}
+    S1_n  = sigma_n X1_n + (1 - sigma_n) S1_{n-1}
+
+with sigma_n chosen by Algorithm 1 and the layers stopped by the
+parameter-free criteria of Algorithm 2 (D^(0)) and Algorithm 3 (D^(1),
+Eq. (ConvCrit) with C_pt = 9).
+
+Readings taken where the text is silent or inconsistent:
+
+* The bias is (1 - sigma_n) S_{n-1} (Alg. 2 and Sec. II B's prose); the
+  S_n in the bias definition after Eq. (LinTransf) is read as S_{n-1}.
+* sign(0) in the branch rule of Alg. 1 gives sigma = -1 (2S - S^2).
+* At the layer n_c where D^(0) is declared converged, Alg. 2 leaves W_n
+  unset; the sigma_{n_c} computed by Alg. 1 at that layer is used for the
+  S1 update, and the flips sigma_n = -sigma_{n-1} follow from n_c + 1.
+* FroErr^(1)_{n-2} of Alg. 3 is undefined in the first two layers of the
+  D^(1) phase (n < n_c + 2); it is taken as +inf, so the test cannot fire
+  before one full sigma-flip pair has been applied.
+* Alg. 3 compares with a strict ">", which never fires when both sides are
+  exactly zero (an exactly idempotent S_0 and an exact S1, e.g. the 2x2
+  pin); ">=" is used.  A layer cap (max_layers) ends a run that does not
+  converge.
+* With several perturbations sharing one S_0 recursion, each direction k
+  runs its own Alg. 3 test and is frozen once it converges; the loop ends
+  when D^(0) and every direction have converged.
+* n_occ = 0 or n_occ = n are the trivial projectors 0 and I with zero
+  response; no layer runs.
+
+Everything else (N_X = Tr X_n, the N_S bookkeeping of Alg. 2, FroErr^(0)
+from the X_n of the converging layer) follows the algorithms as printed.
+
+Pinned by: agreement with ``sos.response_sos`` (a different route to the
+same limit), the 2x2 closed form, the invariants, and an independent plain
+SP2 run on the 2n x 2n block upper-triangular matrix [[H, H1], [0, H]]
+(Sec. III B) whose upper-right block must equal S1 layer by layer.
+"""
+
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+from .gershgorin import gershgorin_bounds
+
+
+@dataclass
+class SP2Result:
+    P: np.ndarray                       # S_0 at exit  (D^(0), orthogonal basis)
+    P1: np.ndarray                      # (k, n, n) S1 at exit (D^(1))
+    layers: int                         # number of layers run (last n)
+    d0_layer: int                       # n_c: layer at which D^(0) converged
+    converged: bool
+    sigma: List[int] = field(default_factory=list)        # sigma_1..sigma_layers
+    iderr: List[float] = field(default_factory=list)      # IdErr_n of the D^(0) phase
+    froerr0: float = 0.0
+    froerr1: List[List[float]] = field(default_factory=list)  # per k, indexed by n-1 (nan if unset)
+    d1_layer: List[int] = field(default_factory=list)    # per k: layer whose test fired
+    bounds: tuple = (0.0, 0.0)
+    checkpoints: dict = field(default_factory=dict)       # n -> S_n (if requested)
+
+
+def _sign_tie_minus(x):
+    return 1 if x > 0 else -1
+
+
+def sp2_pt(H, H1, n_occ, c_pt=9.0, c_d0=4.5, max_layers=100, bounds=None,
+           keep_states=False):
+    """Algorithms 1-3 in FP64.  H1: one (n, n) matrix or a (k, n, n) stack."""
+    H = np.asarray(H, dtype=np.float64)
+    H1 = np.asarray(H1, dtype=np.float64)
+    if H1.ndim == 2:
+        H1 = H1[None]
+    n = H.shape[0]
+    k = H1.shape[0]
+    if not (0 <= n_occ <= n):
+        raise ValueError("n_occ out of range")
+    if n_occ == 0 or n_occ == n:
+        P = np.zeros((n, n)) if n_occ == 0 else np.eye(n)
+        return SP2Result(P=P, P1=np.zeros((k, n, n)), layers=0, d0_layer=0,
+                         converged=True, froerr1=[[] for _ in range(k)],
+                         d1_layer=[0] * k)
+
+    # Alg. 1 inputs: spectral bound estimates of H^(0)
+    eps1, epsN = gershgorin_bounds(H) if bounds is None else bounds
+    # initial transform (Alg. 1): W_0 = -(eps_N - eps_1)^-1, B_0 = eps_N (eps_N - eps_1)^-1 I
+    W0 = -1.0 / (epsN - eps1)
+    S0 = W0 * H + (epsN / (epsN - eps1)) * np.eye(n)
+    NS = np.trace(S0)
+    S1 = [W0 * H1[j] for j in range(k)]                 # B_0^(1) = 0
+
+    n_layer = 1
+    d0_conv = False
+    d1_conv = [False] * k
+    sigma = {}
+    iderr = {}
+    froerr1 = [dict() for _ in range(k)]
+    froerr0 = None
+    d0_layer = 0
+    d1_layer = [0] * k
+    ckpt = {0: S0.copy()} if keep_states else {}
+    converged = True
+
+    while not (d0_conv and all(d1_conv)):
+        if n_layer > max_layers:
+            converged = False
+            n_layer -= 1
+            break
+        # activation f^(1) for every direction still running
+        X1 = [None] * k
+        for j in range(k):
+            if not d1_conv[j]:
+                X1[j] = S0 @ S1[j] + S1[j] @ S0
+        if not d0_conv:
+            X0 = S0 @ S0                                  # activation f^(0)
+            NX = np.trace(X0)
+            iderr[n_layer] = NS - NX
+            sigma[n_layer] = _sign_tie_minus(abs(2.0 * NS - NX - n_occ) - abs(NX - n_occ))
+            # ---- Alg. 2
+            stop = False
+            if iderr[n_layer] <= 0.0:
+                stop = True
+            elif (n_layer > 2 and sigma[n_layer - 1] != sigma[n_layer - 2]
+                  and iderr[n_layer] > c_d0 * iderr[n_layer - 2] ** 2):
+                stop = True
+            if stop:
+                d0_conv = True
+                d0_layer = n_layer
+                froerr0 = np.linalg.norm(S0 - X0, "fro")
+            else:
+                s = sigma[n_layer]
+                S0 = s * X0 + (1 - s) * S0
+                NS = s * NX + (1 - s) * NS
+                if keep_states:
+                    ckpt[n_layer] = S0.copy()
+        else:
+            sigma[n_layer] = -sigma[n_layer - 1]           # the sigma flip
+        # ---- Alg. 3, per direction
+        s = sigma[n_layer]
+        for j in range(k):
+            if d1_conv[j]:
+                continue
+            if d0_conv:
+                fe = np.linalg.norm(S1[j] - X1[j], "fro")
+                froerr1[j][n_layer] = fe
+                prev = froerr1[j].get(n_layer - 2)
+                if n_layer - 2 >= d0_layer and prev is not None and fe >= c_pt * froerr0 * prev:
+                    d1_conv[j] = True
+                    d1_layer[j] = n_layer
+            if not d1_conv[j]:
+                S1[j] = s * X1[j] + (1 - s) * S1[j]
+        n_layer += 1
+    else:
+        n_layer -= 1
+
+    layers = n_layer
+    fe_lists = []
+    for j in range(k):
+        fe_lists.append([froerr1[j].get(m, float("nan")) for m in range(1, layers + 1)])
+    return SP2Result(P=S0, P1=np.stack(S1), layers=layers, d0_layer=d0_layer,
+                     converged=converged,
+                     sigma=[sigma[m] for m in range(1, layers + 1)],
+                     iderr=[iderr[m] for m in sorted(iderr)],
+                     froerr0=float(froerr0) if froerr0 is not None else float("nan"),
+                     froerr1=fe_lists, d1_layer=d1_layer, bounds=(eps1, epsN),
+                     checkpoints=ckpt)
+
+
+def sp2_adjoint(H, G, n_occ, sigma_d0, bounds):
+    """dL/dH of L = Tr[G S_final] through the S_0 recursion with fixed branches.
+
+    The branch choices sigma_1..sigma_m of the layers that updated S_0 and
+    the spectral bounds are held constant (they are piecewise constant in H).
+    Reverse mode of S_n = sigma_n S_{n-1}^2 + (1 - sigma_n) S_{n-1} with a
+    symmetric cotangent Gbar_n = dL/dS_n gives
+        Gbar_{n-1} = sigma_n (S_{n-1} Gbar_n + Gbar_n S_{n-1}) + (1 - sigma_n) Gbar_n,
+    and S_0 = (eps_N I - H)/(eps_N - eps_1) gives dL/dH = -Gbar_0/(eps_N - eps_1).
+    Not in the paper; at convergence it equals the response P1 with H1 := G
+    (the Daleckii-Krein derivative is self-adjoint), which pins it.
+    """
+    H = np.asarray(H, dtype=np.float64)
+    G = np.asarray(G, dtype=np.float64)
+    n = H.shape[0]
+    eps1, epsN = bounds
+    S = ((epsN * np.eye(n)) - H) / (epsN - eps1)
+    states = [S]
+    for s in sigma_d0:
+        S = s * (S @ S) + (1 - s) * S
+        states.append(S)
+    Gbar = 0.5 * (G + G.T)
+    for idx in range(len(sigma_d0) - 1, -1, -1):
+        s = sigma_d0[idx]
+        Sp = states[idx]
+        Gbar = s * (Sp @ Gbar + Gbar @ Sp) + (1 - s) * Gbar
+    return -Gbar / (epsN - eps1)
