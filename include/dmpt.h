@@ -1,0 +1,159 @@
+/*
+ * dmpt.h -- C ABI of the GB300 (sm_103a) DNN-SP2-PT density-matrix response
+ * library (libdmpt.so).
+ *
+ * Given a symmetric Hamiltonian H (orthogonal basis), K symmetric first-order
+ * perturbations H1_k and an occupation count n_occ, the library computes the
+ * zero-temperature density matrix P = theta(mu I - H) (Sec. II B,
+ * Eq. (eq:theta)) and its first-order responses P1_k = dP(H + lambda H1_k)/
+ * dlambda at lambda = 0 (Sec. III A, Eq. (eq:D_k) with k = 1) with the SP2
+ * recursive Fermi-operator expansion in its deep-neural-network form
+ * (Sec. II B, Eq. (LinTransf); Sec. III A, Eq. (S_n detailed), Eq. (dB)),
+ * stopped by the parameter-free criteria of Algorithms 2 and 3
+ * (Sec. IV A, Eq. (ConvCrit)).
+ *
+ * Conventions shared by every call:
+ *  - Matrix arguments are DEVICE pointers owned by the caller, row-major,
+ *    n x n with leading dimension ld >= n (elements), float64.  Inputs are
+ *    assumed symmetric (not checked).  Stacks of K matrices are consecutive
+ *    blocks with stride n * ld elements.
+ *  - No call allocates device memory.  Scratch space is the caller's
+ *    workspace (device pointer, at least dmpt_workspace_size() bytes,
+ *    256-byte aligned); the library never frees it.
+ *  - Work is issued on the caller's `stream` (a cudaStream_t passed as
+ *    void*; NULL means the legacy default stream).
+ *  - Every call returns a dmpt_status and never aborts the process.
+ *    Argument errors are detected before any launch.  CUDA errors return
+ *    DMPT_ECUDA; the text is available from dmpt_last_error().
+ *  - The library only runs on an sm_103 device (GB300); other devices give
+ *    DMPT_EUNSUPPORTED from dmpt_create().
+ */
+#ifndef DMPT_H
+#define DMPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DMPT_MAX_K 8        /* perturbation directions per call           */
+#define DMPT_MAX_LAYERS 256 /* upper bound of dmpt_options.max_layers      */
+
+typedef enum {
+  DMPT_OK = 0,
+  DMPT_EINVAL = 1,        /* bad argument (null pointer, n < 1, ld < n, ...)  */
+  DMPT_EWORKSPACE = 2,    /* workspace null, too small or misaligned          */
+  DMPT_ENOTCONV = 3,      /* max_layers reached; last iterate written         */
+  DMPT_ENUMERIC = 4,      /* non-finite value or empty spectral interval      */
+  DMPT_ETIMEOUT = 5,      /* a device-side wait hit its time limit            */
+  DMPT_ECUDA = 6,         /* CUDA runtime / driver error                      */
+  DMPT_EUNSUPPORTED = 7   /* device or option not supported                   */
+} dmpt_status;
+
+/* Arithmetic of the layer products (Sec. II C, Eq. (DualMat2),
+ * Eq. (S0 tensor core); Sec. III D, Eq. (S0S1 tensor core)).
+ *  DMPT_FP64:      FP64 masters, FP64 SIMT products.
+ *  DMPT_FP32:      FP32 masters, FP32 SIMT products ("GPU-only" form).
+ *  DMPT_DUAL_FP16: FP32 masters split into FP16 hi + lo, products
+ *                  hi*hi + hi*lo + lo*hi on tcgen05 tensor cores with FP32
+ *                  accumulation (lo*lo dropped).
+ *  DMPT_DUAL_BF16: same with BF16 halves. */
+typedef enum {
+  DMPT_FP64 = 0,
+  DMPT_FP32 = 1,
+  DMPT_DUAL_FP16 = 2,
+  DMPT_DUAL_BF16 = 3
+} dmpt_precision;
+
+typedef struct {
+  int precision;        /* dmpt_precision                                     */
+  int max_layers;       /* layer cap, 1..DMPT_MAX_LAYERS (default 100)        */
+  double c_pt;          /* C_pt of Eq. (ConvCrit) / Alg. 3 (default 9.0)     */
+  double c_d0;          /* factor of the Alg. 2 test (default 4.5)            */
+  int operand_scaling;  /* 1: exact power-of-two scaling of the 16-bit halves
+                           (FP16 range); 0: none (default 1)                  */
+  int sync_every;       /* layers issued between host polls of the device
+                           state (default 4)                                  */
+  int timing;           /* 1: time every layer-product launch with CUDA events
+                           on `stream` and report it in dmpt_info             */
+  double timeout_s;     /* limit of any device-side spin wait (default 2.0)   */
+  int ckpt_every;       /* >0: keep S every ckpt_every layers plus the branch
+                           sequence in the workspace, for dmpt_sp2_backward   */
+  int reserved[7];
+} dmpt_options;
+
+/* Filled on the host by dmpt_sp2_response (when info != NULL). */
+typedef struct {
+  int status;                        /* same as the return value             */
+  int layers;                        /* last layer n run                     */
+  int d0_layer;                      /* layer at which Alg. 2 fired          */
+  int converged;                     /* 1 if Alg. 2 and every Alg. 3 fired   */
+  int d1_layer[DMPT_MAX_K];          /* layer at which Alg. 3 fired, per k   */
+  double eps_min, eps_max;           /* Gershgorin bounds used (Alg. 1)      */
+  double froerr0;                    /* FroErr^(0) of Alg. 2                 */
+  double froerr1[DMPT_MAX_K];        /* last FroErr^(1)_n of Alg. 3, per k   */
+  double ms_layers;                  /* summed device time of the layer
+                                        products (timing = 1), else 0        */
+  int product_launches;              /* layer-product kernel launches        */
+  int timed_launches;                /* launches covered by ms_layers        */
+  double mma_flops;                  /* flops issued by the layer products   */
+  double alg_flops;                  /* algorithmic flops: (2 + 3K) 2n^3 per
+                                        D0 layer, 3K 2n^3 per D1-only layer
+                                        (Eq. (flop rate formula), 2/FMA)     */
+  signed char sigma[DMPT_MAX_LAYERS];/* sigma_1..sigma_layers                */
+} dmpt_info;
+
+typedef struct dmpt_ctx* dmpt_handle;
+
+/* Create a context on CUDA device `device` (made current for the call).
+ * Checks that the device is sm_103.  *h receives the handle. */
+dmpt_status dmpt_create(dmpt_handle* h, int device);
+dmpt_status dmpt_destroy(dmpt_handle h);
+
+/* Fill `o` with the defaults listed in dmpt_options. */
+void dmpt_default_options(dmpt_options* o);
+
+const char* dmpt_status_string(dmpt_status s);
+/* Last error text of this handle (never NULL; "" when none). */
+const char* dmpt_last_error(dmpt_handle h);
+
+/* Bytes of workspace dmpt_sp2_response needs for (n, k, o->precision);
+ * 0 for invalid arguments. */
+size_t dmpt_workspace_size(int64_t n, int k, const dmpt_options* o);
+
+/* Gershgorin spectral bounds of H (Sec. II B; Alg. 1 inputs eps_1, eps_N):
+ *   eps[0] = min_i (H_ii - sum_{j != i} |H_ij|),
+ *   eps[1] = max_i (H_ii + sum_{j != i} |H_ij|),
+ * computed in FP64 on the device.  `eps` is a device pointer to 2 doubles.
+ * Asynchronous on `stream`. */
+dmpt_status dmpt_bounds(dmpt_handle h, const double* H, int64_t n, int64_t ld,
+                        double* eps, void* stream);
+
+/* Density matrix and first-order responses by DNN-SP2-PT (Algorithms 1-3).
+ *   H      device, n x n (ld), float64, symmetric.
+ *   H1     device, k blocks of n x n (ld), float64, each symmetric.
+ *   k      1..DMPT_MAX_K directions sharing one S_0 recursion (each has its
+ *          own Alg. 3 test and stops independently).
+ *   n_occ  0..n.  n_occ = 0 or n gives P = 0 or I and P1 = 0 at once.
+ *   o      options (NULL: defaults).
+ *   P      device n x n (ld) output, may be NULL.
+ *   P1     device, k blocks n x n (ld) outputs.
+ *   info   host pointer, may be NULL.
+ *   workspace / ws_bytes: caller scratch of dmpt_workspace_size() bytes.
+ * The call issues all work on `stream` and synchronises that stream every
+ * o->sync_every layers to read the convergence flag; it returns when the
+ * outputs are written.  Returns DMPT_ENOTCONV (outputs = last iterate) when
+ * max_layers is reached, DMPT_ENUMERIC on non-finite values or
+ * eps_N <= eps_1 for 0 < n_occ < n. */
+dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1,
+                              int k, int64_t n, int64_t ld, int64_t n_occ,
+                              const dmpt_options* o, double* P, double* P1,
+                              dmpt_info* info, void* workspace, size_t ws_bytes,
+                              void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMPT_H */

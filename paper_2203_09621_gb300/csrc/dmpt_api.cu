@@ -1,0 +1,315 @@
+// C ABI of libdmpt.so (declared in include/dmpt.h): argument checking,
+// workspace carving and the host side of the layer loop of Algorithm 1.
+//
+// The host only issues launches.  Each layer is one product kernel (SIMT for
+// FP64 / FP32, tcgen05 for the dual forms) followed by the one-block decide
+// kernel that applies Algorithms 2 and 3 on the device.  Every
+// `sync_every` layers the host reads the device "done" flag; launches that
+// follow a finished run exit at once.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "dmpt_internal.cuh"
+
+struct dmpt_ctx {
+  int device = 0;
+  int sm_count = 0;
+  char err[512] = {0};
+  std::vector<cudaEvent_t> events;  // timing pairs, created on first use
+};
+
+namespace {
+
+using namespace dmpt;
+
+dmpt_status fail(dmpt_handle h, dmpt_status s, const char* fmt, const char* what = "") {
+  if (h) snprintf(h->err, sizeof(h->err), fmt, what);
+  return s;
+}
+
+dmpt_status cuda_fail(dmpt_handle h, cudaError_t e, const char* where) {
+  if (h) snprintf(h->err, sizeof(h->err), "%s: %s", where, cudaGetErrorString(e));
+  return DMPT_ECUDA;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool valid_options(const dmpt_options* o) {
+  if (o->precision < DMPT_FP64 || o->precision > DMPT_DUAL_BF16) return false;
+  if (o->max_layers < 1 || o->max_layers > DMPT_MAX_LAYERS) return false;
+  if (!(o->c_pt > 0.0) || !(o->c_d0 > 0.0)) return false;
+  if (o->sync_every < 1) return false;
+  if (!(o->timeout_s > 0.0)) return false;
+  if (o->ckpt_every < 0) return false;
+  return true;
+}
+
+__global__ void state_init_kernel(State* st, int k, int max_layers, int precision, double n_occ,
+                                  double c_pt, double c_d0) {
+  st->n_layer = 0;
+  st->done = 0;
+  st->status = DMPT_OK;
+  st->timeout_flag = 0;
+  st->k = k;
+  st->max_layers = max_layers;
+  st->precision = precision;
+  st->n_occ = n_occ;
+  st->c_pt = c_pt;
+  st->c_d0 = c_d0;
+  st->plan_square = 0;
+  st->plan_write0 = 0;
+  for (int j = 0; j < kMaxK; ++j) st->plan_resp[j] = 0;
+}
+
+double layer_alg_flops(double n, int prec, bool square, int active) {
+  const double n3x2 = 2.0 * n * n * n;
+  if (prec >= DMPT_DUAL_FP16) return ((square ? 2.0 : 0.0) + 3.0 * active) * n3x2;
+  return ((square ? 1.0 : 0.0) + 1.0 * active) * n3x2;
+}
+
+double layer_mma_flops(const Layout& L, double per /* one full-K single-term pass */,
+                       bool square, int active) {
+  const bool dual = L.precision >= DMPT_DUAL_FP16;
+  return (square ? (dual ? 3.0 : 1.0) : 0.0) * per + active * (dual ? 6.0 : 2.0) * per;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dmpt_default_options(dmpt_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = DMPT_DUAL_FP16;
+  o->max_layers = 100;
+  o->c_pt = 9.0;
+  o->c_d0 = 4.5;
+  o->operand_scaling = 1;
+  o->sync_every = 4;
+  o->timing = 0;
+  o->timeout_s = 2.0;
+  o->ckpt_every = 0;
+}
+
+const char* dmpt_status_string(dmpt_status s) {
+  switch (s) {
+    case DMPT_OK: return "DMPT_OK";
+    case DMPT_EINVAL: return "DMPT_EINVAL: invalid argument";
+    case DMPT_EWORKSPACE: return "DMPT_EWORKSPACE: workspace missing, too small or misaligned";
+    case DMPT_ENOTCONV: return "DMPT_ENOTCONV: layer cap reached before convergence";
+    case DMPT_ENUMERIC: return "DMPT_ENUMERIC: non-finite value or empty spectral interval";
+    case DMPT_ETIMEOUT: return "DMPT_ETIMEOUT: a device-side wait timed out";
+    case DMPT_ECUDA: return "DMPT_ECUDA: CUDA error";
+    case DMPT_EUNSUPPORTED: return "DMPT_EUNSUPPORTED: unsupported device or option";
+  }
+  return "unknown dmpt_status";
+}
+
+const char* dmpt_last_error(dmpt_handle h) { return h ? h->err : ""; }
+
+dmpt_status dmpt_create(dmpt_handle* h, int device) {
+  if (!h) return DMPT_EINVAL;
+  *h = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+    return DMPT_EINVAL;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return DMPT_ECUDA;
+  if (!(prop.major == 10 && prop.minor == 3)) return DMPT_EUNSUPPORTED;
+  dmpt_ctx* c = new dmpt_ctx();
+  c->device = device;
+  c->sm_count = prop.multiProcessorCount;
+  *h = c;
+  return DMPT_OK;
+}
+
+dmpt_status dmpt_destroy(dmpt_handle h) {
+  if (!h) return DMPT_EINVAL;
+  {
+    DeviceGuard g(h->device);
+    for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  }
+  delete h;
+  return DMPT_OK;
+}
+
+size_t dmpt_workspace_size(int64_t n, int k, const dmpt_options* o) {
+  dmpt_options d;
+  dmpt_default_options(&d);
+  if (!o) o = &d;
+  if (n < 1 || k < 1 || k > DMPT_MAX_K || !valid_options(o)) return 0;
+  return make_layout(n, k, o->precision).total;
+}
+
+dmpt_status dmpt_bounds(dmpt_handle h, const double* H, int64_t n, int64_t ld, double* eps,
+                        void* stream) {
+  if (!h) return DMPT_EINVAL;
+  if (!H || !eps) return fail(h, DMPT_EINVAL, "dmpt_bounds: null pointer%s");
+  if (n < 1 || ld < n) return fail(h, DMPT_EINVAL, "dmpt_bounds: need n >= 1 and ld >= n%s");
+  if (((uintptr_t)eps) % 8) return fail(h, DMPT_EINVAL, "dmpt_bounds: eps not 8-byte aligned%s");
+  DeviceGuard g(h->device);
+  cudaError_t e = launch_bounds(H, n, ld, eps, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "dmpt_bounds");
+  return DMPT_OK;
+}
+
+dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, int k,
+                              int64_t n, int64_t ld, int64_t n_occ, const dmpt_options* o,
+                              double* P, double* P1, dmpt_info* info, void* workspace,
+                              size_t ws_bytes, void* stream) {
+  if (!h) return DMPT_EINVAL;
+  h->err[0] = 0;
+  dmpt_options defaults;
+  dmpt_default_options(&defaults);
+  if (!o) o = &defaults;
+  if (info) memset(info, 0, sizeof(*info));
+  if (!H || !H1 || !P1) return fail(h, DMPT_EINVAL, "dmpt_sp2_response: null %s", "H/H1/P1");
+  if (k < 1 || k > DMPT_MAX_K) return fail(h, DMPT_EINVAL, "dmpt_sp2_response: k out of range%s");
+  if (n < 1 || ld < n) return fail(h, DMPT_EINVAL, "dmpt_sp2_response: need n >= 1, ld >= n%s");
+  if (n_occ < 0 || n_occ > n) return fail(h, DMPT_EINVAL, "dmpt_sp2_response: n_occ out of [0, n]%s");
+  if (!valid_options(o)) return fail(h, DMPT_EINVAL, "dmpt_sp2_response: invalid options%s");
+  if (o->ckpt_every != 0)
+    return fail(h, DMPT_EUNSUPPORTED, "dmpt_sp2_response: ckpt_every is not supported%s");
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceGuard g(h->device);
+
+  if (n_occ == 0 || n_occ == n) {
+    cudaError_t e = launch_trivial(n, k, ld, n_occ == n, P, P1, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "dmpt_sp2_response (trivial)");
+    if (info) {
+      info->status = DMPT_OK;
+      info->converged = 1;
+    }
+    return DMPT_OK;
+  }
+
+  const Layout L = make_layout(n, k, o->precision);
+  if (!workspace) return fail(h, DMPT_EWORKSPACE, "dmpt_sp2_response: null workspace%s");
+  if (((uintptr_t)workspace) % 256)
+    return fail(h, DMPT_EWORKSPACE, "dmpt_sp2_response: workspace not 256-byte aligned%s");
+  if (ws_bytes < L.total)
+    return fail(h, DMPT_EWORKSPACE, "dmpt_sp2_response: workspace too small%s");
+  const bool dual = o->precision >= DMPT_DUAL_FP16;
+
+  char* base = (char*)workspace;
+  State* st = (State*)(base + L.off_state);
+  cudaError_t e = cudaMemsetAsync(st, 0, sizeof(State), s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "state reset");
+  state_init_kernel<<<1, 1, 0, s>>>(st, k, o->max_layers, o->precision, (double)n_occ, o->c_pt,
+                                    o->c_d0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "state init");
+  if ((e = launch_bounds(H, n, ld, &st->eps1, s)) != cudaSuccess) return cuda_fail(h, e, "bounds");
+  const int init_blocks = 1024;
+  if ((e = launch_init(L, workspace, H, H1, ld, init_blocks, s)) != cudaSuccess)
+    return cuda_fail(h, e, "init");
+  if ((e = launch_decide(L, workspace, kDecideInit, init_blocks, s)) != cudaSuccess)
+    return cuda_fail(h, e, "decide(init)");
+  if (dual && (e = launch_split(L, workspace, s)) != cudaSuccess) return cuda_fail(h, e, "split");
+
+  // events for per-launch timing of the layer products
+  const int max_layers = o->max_layers;
+  if (o->timing && (int)h->events.size() < 2 * max_layers) {
+    while ((int)h->events.size() < 2 * max_layers) {
+      cudaEvent_t ev;
+      if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(h, e, "event create");
+      h->events.push_back(ev);
+    }
+  }
+
+  int launched = 0;
+  int64_t entries = 0;
+  double pass_flops = 0.0;
+  int done = 0;
+  while (launched < max_layers && !done) {
+    for (int j = 0; j < o->sync_every && launched < max_layers; ++j) {
+      if (o->timing) cudaEventRecord(h->events[2 * launched], s);
+      e = dual ? launch_layer_tc(L, workspace, s, o->timeout_s, &entries, &pass_flops)
+               : launch_layer_simt(L, workspace, s, &entries, &pass_flops);
+      if (e != cudaSuccess) return cuda_fail(h, e, "layer product");
+      if (o->timing) cudaEventRecord(h->events[2 * launched + 1], s);
+      if ((e = launch_decide(L, workspace, kDecideLayer, entries, s)) != cudaSuccess)
+        return cuda_fail(h, e, "decide(layer)");
+      ++launched;
+    }
+    if ((e = cudaMemcpyAsync(&done, &st->done, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
+        cudaSuccess)
+      return cuda_fail(h, e, "poll");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(h, e, "layer loop");
+  }
+  if ((e = launch_finalize(L, workspace, P, P1, ld, s)) != cudaSuccess)
+    return cuda_fail(h, e, "finalize");
+
+  State* host_state = new State;
+  e = cudaMemcpyAsync(host_state, st, sizeof(State), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    delete host_state;
+    return cuda_fail(h, e, "state readback");
+  }
+  dmpt_status status = (dmpt_status)host_state->status;
+  if (!host_state->done) status = DMPT_ENOTCONV;
+  if (info) {
+    const State& S = *host_state;
+    info->status = status;
+    info->layers = S.layers_run;
+    info->d0_layer = S.d0_layer;
+    bool all1 = S.d0_conv != 0;
+    for (int j = 0; j < k; ++j) {
+      info->d1_layer[j] = S.d1_layer[j];
+      all1 = all1 && S.d1_conv[j];
+      // last FroErr^(1) recorded for direction j
+      const int last = S.d1_conv[j] ? S.d1_layer[j] : S.layers_run;
+      info->froerr1[j] = (last >= 1 && last <= DMPT_MAX_LAYERS) ? S.froerr1[j][last] : 0.0;
+    }
+    info->converged = (status == DMPT_OK && all1) ? 1 : 0;
+    info->eps_min = S.eps1;
+    info->eps_max = S.epsN;
+    info->froerr0 = S.froerr0;
+    for (int m = 1; m <= S.layers_run && m <= DMPT_MAX_LAYERS; ++m) info->sigma[m - 1] = S.sigma[m];
+    info->product_launches = launched;
+    double mma = 0.0, alg = 0.0;
+    for (int m = 1; m <= S.layers_run; ++m) {
+      const bool sq = S.d0_layer == 0 || m <= S.d0_layer;
+      int active = 0;
+      for (int j = 0; j < k; ++j) active += (S.d1_conv[j] ? m <= S.d1_layer[j] : true) ? 1 : 0;
+      mma += layer_mma_flops(L, pass_flops, sq, active);
+      alg += layer_alg_flops((double)n, o->precision, sq, active);
+    }
+    info->mma_flops = mma;
+    info->alg_flops = alg;
+    if (o->timing) {
+      double total = 0.0;
+      int timed = 0;
+      for (int m = 0; m < S.layers_run && m < launched; ++m) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->events[2 * m], h->events[2 * m + 1]) == cudaSuccess) {
+          total += ms;
+          ++timed;
+        }
+      }
+      info->ms_layers = total;
+      info->timed_launches = timed;
+    }
+  }
+  delete host_state;
+  if (status == DMPT_ETIMEOUT) fail(h, status, "a device-side wait timed out%s");
+  if (status == DMPT_ENUMERIC) fail(h, status, "non-finite values or eps_N <= eps_1%s");
+  if (status == DMPT_ENOTCONV) fail(h, status, "max_layers reached%s");
+  return status;
+}
+
+}  // extern "C"

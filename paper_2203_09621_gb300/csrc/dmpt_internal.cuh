@@ -1,0 +1,113 @@
+// Internal declarations shared by the translation units of libdmpt.so.
+//
+// Device-resident control: the whole layer loop of Algorithms 1-3 runs on the
+// GPU.  After each layer product, a one-block "decide" kernel reduces the
+// per-tile FP64 partial sums written by the product's epilogue, applies the
+// Alg. 2 / Alg. 3 tests and plans the next layer (branch sigma_n, whether the
+// square is computed and stored, which directions still run, operand scale
+// exponents).  The product kernels read that plan from State at launch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dmpt.h"
+
+namespace dmpt {
+
+constexpr int kMaxK = DMPT_MAX_K;
+constexpr int kMaxL = DMPT_MAX_LAYERS;
+constexpr int kPad = 256;   // internal matrices are zero-padded to a multiple of this
+constexpr int kNQ = 4;      // partial sums per (job, tile): see Partial* below
+
+// Partial-sum slots per (job, tile).  Job 0 is the square (S0), job 1+k the
+// response of direction k.
+enum : int {
+  kQTrace = 0,    // job 0: sum of the new diagonal          (Tr S_n)
+  kQFroNew = 1,   // ||S_new||_F^2 over the tile (both triangles)
+  kQFroDiff = 2,  // ||S_old - X||_F^2  (FroErr^(0) / FroErr^(1)_n of Alg. 2 / 3)
+  kQBad = 3       // count of non-finite values seen
+};
+
+// Device state block (lives at the start of the workspace).
+struct State {
+  int n_layer;          // layer the next product computes (1-based)
+  int done;             // 1: converged, failed or capped; later launches are no-ops
+  int status;           // dmpt_status
+  int timeout_flag;     // set by a kernel whose bounded wait expired
+  int d0_conv;          // Alg. 2 has fired
+  int d0_layer;         // layer at which it fired
+  int cur0;             // ping-pong buffer holding the current S0
+  int sigma_cur;        // sigma of the planned layer
+  int plan_square;      // planned layer computes X = S0^2
+  int plan_write0;      // ... and stores S0_n = sigma X + (1 - sigma) S0_{n-1}
+  int s0_exp;           // power-of-two exponent of the 16-bit S0 copies
+  int k;                // directions
+  int max_layers;
+  int precision;
+  int layers_run;       // layers whose product finished
+  int pad0;
+  int cur1[kMaxK];
+  int d1_conv[kMaxK];
+  int d1_layer[kMaxK];
+  int plan_resp[kMaxK];
+  int s1_exp_cur[kMaxK];   // exponent of the current 16-bit S1 copies
+  int s1_exp_next[kMaxK];  // exponent the planned layer's epilogue writes with
+  double n_occ, c_pt, c_d0;
+  double eps1, epsN;
+  double NS, NX;           // Tr S0 and ||S0||_F^2 of the current S0
+  double froerr0;
+  double s1_fro2[kMaxK];   // ||S1_k||_F^2 of the current S1_k
+  double iderr[kMaxL + 2];
+  double froerr1[kMaxK][kMaxL + 2];
+  signed char sigma[kMaxL + 2];
+};
+
+// Workspace layout (byte offsets from the workspace base, 256-aligned).
+struct Layout {
+  int64_t n, Np;          // logical and padded size
+  int k;
+  int precision;
+  size_t elem;            // bytes per master element (8 or 4)
+  size_t off_state, off_partials, off_master, off_ops16, total;
+  int64_t partial_tiles;  // entries per job in the partials array
+};
+
+Layout make_layout(int64_t n, int k, int precision);
+
+// Upper-triangular tile count for block size bt.
+inline int64_t upper_tiles(int64_t Np, int bt) {
+  int64_t t = Np / bt;
+  return t * (t + 1) / 2;
+}
+
+// ---- launchers (kernels_simt.cu) ----
+cudaError_t launch_bounds(const double* H, int64_t n, int64_t ld, double* eps_out,
+                          cudaStream_t s);
+cudaError_t launch_init(const Layout& L, void* ws, const double* H, const double* H1,
+                        int64_t ld, int blocks, cudaStream_t s);
+cudaError_t launch_decide(const Layout& L, void* ws, int mode, int64_t entries,
+                          cudaStream_t s);
+// Layer-product launchers.  *entries: partial-sum entries per job (tiles);
+// *pass_flops: flops of one full-K, single-term pass over all tiles.
+cudaError_t launch_layer_simt(const Layout& L, void* ws, cudaStream_t s, int64_t* entries,
+                              double* pass_flops);
+cudaError_t launch_split(const Layout& L, void* ws, cudaStream_t s);
+cudaError_t launch_finalize(const Layout& L, void* ws, double* P, double* P1,
+                            int64_t ld, cudaStream_t s);
+cudaError_t launch_trivial(int64_t n, int k, int64_t ld, int full, double* P,
+                           double* P1, cudaStream_t s);
+int simt_tile(int precision);
+
+// ---- tensor-core path (kernels_tc.cu) ----
+cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double timeout_s,
+                            int64_t* entries, double* pass_flops);
+int tc_tile();
+
+enum DecideMode { kDecideInit = 0, kDecideLayer = 1 };
+
+// State-dependent exponent for the 16-bit copies of S1: chosen so that a
+// bound of the largest element maps to <= 2^14 (FP16 max is 65504).
+constexpr int kFp16TargetExp = 14;
+
+}  // namespace dmpt

@@ -1,0 +1,674 @@
+// Element-wise kernels, device-side control of Algorithms 1-3, and the SIMT
+// (FP64 / FP32) layer product with its fused epilogue.
+//
+// Matrices inside the workspace are n x n zero-padded to Np x Np (Np a
+// multiple of 256).  Zero padding is invariant under the SP2 layers
+// (0^2 = 0, 2*0 - 0^2 = 0) and adds nothing to traces or norms, so the
+// product kernels need no bounds checks.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include "dmpt_internal.cuh"
+
+namespace dmpt {
+
+static inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+Layout make_layout(int64_t n, int k, int precision) {
+  Layout L{};
+  L.n = n;
+  L.Np = ((n + kPad - 1) / kPad) * kPad;
+  L.k = k;
+  L.precision = precision;
+  L.elem = (precision == DMPT_FP64) ? 8 : 4;
+  size_t off = 0;
+  L.off_state = off;
+  off = align256(off + sizeof(State));
+  // one partial entry per upper tile of the smallest product tile (64) or
+  // per block of the init kernel, whichever is larger
+  int64_t tiles = upper_tiles(L.Np, 64);
+  L.partial_tiles = tiles > 1024 ? tiles : 1024;
+  L.off_partials = off;
+  off = align256(off + (size_t)(1 + k) * (size_t)L.partial_tiles * kNQ * sizeof(double));
+  const size_t mat = (size_t)L.Np * (size_t)L.Np;
+  L.off_master = off;
+  off = align256(off + 2 * (size_t)(1 + k) * mat * L.elem);
+  if (precision == DMPT_DUAL_FP16 || precision == DMPT_DUAL_BF16) {
+    L.off_ops16 = off;
+    off = align256(off + 2 * (size_t)(1 + k) * 2 * mat * 2);
+  } else {
+    L.off_ops16 = 0;
+  }
+  L.total = off;
+  return L;
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic block reduction of NV doubles (fixed tree, fixed order).
+template <int NV, int NT>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* smem /* NT*NV */) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) smem[i * NT + tid] = v[i];
+  __syncthreads();
+  for (int s = NT / 2; s > 0; s >>= 1) {
+    if (tid < s) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) smem[i * NT + tid] += smem[i * NT + tid + s];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = smem[i * NT];
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Gershgorin bounds (Sec. II B; Alg. 1 inputs).  Min / max are taken with
+// 64-bit integer atomics on an order-preserving encoding of the doubles, so
+// the result is independent of the order in which rows finish and the call
+// needs no scratch memory beyond its 2-double output.
+
+__device__ __forceinline__ long long dkey(double x) {
+  long long b = __double_as_longlong(x);
+  return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFLL);
+}
+__device__ __forceinline__ double dkey_inv(long long k) {
+  long long b = k >= 0 ? k : (k ^ 0x7FFFFFFFFFFFFFFFLL);
+  return __longlong_as_double(b);
+}
+
+__global__ void bounds_init_kernel(long long* key) {
+  key[0] = dkey(INFINITY);
+  key[1] = dkey(-INFINITY);
+}
+
+// one warp per row; row r: centre H_rr, radius sum_{j != r} |H_rj|
+__global__ void bounds_rows_kernel(const double* __restrict__ H, int64_t n, int64_t ld,
+                                   long long* key) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double lo = INFINITY, hi = -INFINITY;
+  for (int64_t r = warp; r < n; r += nwarps) {
+    const double* row = H + r * ld;
+    double s = 0.0;
+    for (int64_t j = lane; j < n; j += 32) s += fabs(row[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const double d = row[r];
+    const double rad = s - fabs(d);
+    lo = fmin(lo, d - rad);
+    hi = fmax(hi, d + rad);
+  }
+  if (lane == 0 && warp < n) {
+    atomicMin(&key[0], dkey(lo));
+    atomicMax(&key[1], dkey(hi));
+  }
+}
+
+__global__ void bounds_fin_kernel(long long* key) {
+  double lo = dkey_inv(key[0]);
+  double hi = dkey_inv(key[1]);
+  double* out = reinterpret_cast<double*>(key);
+  out[0] = lo;
+  out[1] = hi;
+}
+
+cudaError_t launch_bounds(const double* H, int64_t n, int64_t ld, double* eps_out,
+                          cudaStream_t s) {
+  long long* key = reinterpret_cast<long long*>(eps_out);
+  bounds_init_kernel<<<1, 1, 0, s>>>(key);
+  int64_t warps = n < 152 * 64 ? n : 152 * 64;
+  int blocks = (int)((warps * 32 + 255) / 256);
+  bounds_rows_kernel<<<blocks, 256, 0, s>>>(H, n, ld, key);
+  bounds_fin_kernel<<<1, 1, 0, s>>>(key);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Initial normalisation layer (Alg. 1; Sec. III A, S_0(lambda)):
+//   S0 = (eps_N I - H) / (eps_N - eps_1),  S1_k = -H1_k / (eps_N - eps_1).
+// Only the upper triangle (j >= i) of H and H1 is read, so the stored
+// matrices are exactly symmetric.  Partial sums per block: Tr S0, ||S0||_F^2,
+// ||S1_k||_F^2 and a count of non-finite values.
+
+template <typename T>
+__global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const double* __restrict__ H,
+                                                   const double* __restrict__ H1, int64_t n,
+                                                   int64_t Np, int64_t ld, int k,
+                                                   double* partials, int64_t ptiles) {
+  __shared__ double red[3 * 256];
+  const double e1 = st->eps1, eN = st->epsN;
+  const double w = 1.0 / (eN - e1);
+  const size_t mat = (size_t)Np * Np;
+  double tr = 0.0, f0 = 0.0, bad = 0.0;
+  double f1[kMaxK];
+#pragma unroll
+  for (int j = 0; j < kMaxK; ++j) f1[j] = 0.0;
+  const int64_t total = (int64_t)Np * Np;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / Np, c = idx - r * Np;
+    const bool in = r < n && c < n;
+    const int64_t src = (r <= c ? r * ld + c : c * ld + r);
+    double s0 = 0.0;
+    if (in) s0 = ((r == c ? eN : 0.0) - H[src]) * w;
+    const T t0 = (T)s0;
+    master[idx] = t0;
+    const double d0 = (double)t0;
+    if (r == c) tr += d0;
+    f0 += d0 * d0;
+    if (!isfinite(d0)) bad += 1.0;
+    for (int j = 0; j < k; ++j) {
+      double s1 = 0.0;
+      if (in) s1 = -H1[(size_t)j * n * ld + src] * w;
+      const T t1 = (T)s1;
+      master[(size_t)(1 + j) * mat + idx] = t1;
+      const double d1 = (double)t1;
+      f1[j] += d1 * d1;
+      if (!isfinite(d1)) bad += 1.0;
+    }
+  }
+  // job 0: trace, fro, bad
+  {
+    double v[3] = {tr, f0, bad};
+    block_sum<3, 256>(v, red);
+    if (threadIdx.x == 0) {
+      double* p = partials + ((size_t)0 * ptiles + blockIdx.x) * kNQ;
+      p[kQTrace] = v[0];
+      p[kQFroNew] = v[1];
+      p[kQFroDiff] = 0.0;
+      p[kQBad] = v[2];
+    }
+  }
+  for (int j = 0; j < k; ++j) {
+    double v[1] = {f1[j]};
+    block_sum<1, 256>(v, red);
+    if (threadIdx.x == 0) {
+      double* p = partials + ((size_t)(1 + j) * ptiles + blockIdx.x) * kNQ;
+      p[kQTrace] = 0.0;
+      p[kQFroNew] = v[0];
+      p[kQFroDiff] = 0.0;
+      p[kQBad] = 0.0;
+    }
+  }
+}
+
+cudaError_t launch_init(const Layout& L, void* ws, const double* H, const double* H1,
+                        int64_t ld, int blocks, cudaStream_t s) {
+  char* base = (char*)ws;
+  State* st = (State*)(base + L.off_state);
+  double* partials = (double*)(base + L.off_partials);
+  if (L.precision == DMPT_FP64)
+    init_kernel<double><<<blocks, 256, 0, s>>>(st, (double*)(base + L.off_master), H, H1, L.n,
+                                               L.Np, ld, L.k, partials, L.partial_tiles);
+  else
+    init_kernel<float><<<blocks, 256, 0, s>>>(st, (float*)(base + L.off_master), H, H1, L.n,
+                                              L.Np, ld, L.k, partials, L.partial_tiles);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Device-side control (Alg. 1 branch rule, Alg. 2, Alg. 3).
+
+__device__ int fp16_exponent_for(double bound) {
+  // exponent e with bound * 2^e < 2^kFp16TargetExp
+  if (!(bound > 0.0) || !isfinite(bound)) return 0;
+  int e = kFp16TargetExp - (ilogb(bound) + 1);
+  return e < -100 ? -100 : (e > 100 ? 100 : e);
+}
+
+// Plan layer n (Alg. 1: branch choice; Alg. 2: D0 stopping tests).
+__device__ void plan_layer(State* st, int n) {
+  int sigma;
+  if (!st->d0_conv) {
+    const double NS = st->NS, NX = st->NX, no = st->n_occ;
+    const double iderr = NS - NX;
+    // sigma_n = sign(|2 N_S - N_X - N_occ| - |N_X - N_occ|); sign(0) -> -1
+    const double arg = fabs(2.0 * NS - NX - no) - fabs(NX - no);
+    sigma = arg > 0.0 ? 1 : -1;
+    st->iderr[n] = iderr;
+    st->sigma[n] = (signed char)sigma;
+    bool stop = iderr <= 0.0;
+    if (!stop && n > 2 && st->sigma[n - 1] != st->sigma[n - 2] &&
+        iderr > st->c_d0 * st->iderr[n - 2] * st->iderr[n - 2])
+      stop = true;
+    st->plan_square = 1;
+    if (stop) {
+      st->d0_conv = 1;
+      st->d0_layer = n;
+      st->plan_write0 = 0;  // this layer's square only measures FroErr^(0)
+    } else {
+      st->plan_write0 = 1;
+    }
+  } else {
+    sigma = -(int)st->sigma[n - 1];  // the sigma flip of Alg. 1
+    st->sigma[n] = (signed char)sigma;
+    st->plan_square = 0;
+    st->plan_write0 = 0;
+  }
+  st->sigma_cur = sigma;
+  for (int j = 0; j < st->k; ++j) {
+    st->plan_resp[j] = !st->d1_conv[j];
+    // |S1_n|_max <= ||S1_n||_2 <= (2 ||S0||_2 + |1 - sigma|) ||S1_{n-1}||_2
+    //            <= 4.5 ||S1_{n-1}||_F   (spectrum of S0 within [-0.25, 1.25])
+    st->s1_exp_next[j] = st->precision == DMPT_DUAL_FP16
+                             ? fp16_exponent_for(4.5 * sqrt(st->s1_fro2[j]))
+                             : 0;
+  }
+  st->n_layer = n;
+}
+
+__global__ void __launch_bounds__(256) decide_kernel(State* st, const double* __restrict__ partials,
+                                                     int64_t ptiles, int64_t entries, int mode) {
+  __shared__ double red[kNQ * 256];
+  __shared__ double sums[kMaxK + 1][kNQ];
+  if (st->done) return;
+  const int k = st->k;
+  for (int job = 0; job <= k; ++job) {
+    const bool ran = mode == kDecideInit ||
+                     (job == 0 ? st->plan_square != 0 : st->plan_resp[job - 1] != 0);
+    if (!ran) continue;  // uniform across the block
+    double v[kNQ] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t e = threadIdx.x; e < entries; e += 256) {
+      const double* p = partials + ((size_t)job * ptiles + e) * kNQ;
+#pragma unroll
+      for (int q = 0; q < kNQ; ++q) v[q] += p[q];
+    }
+    block_sum<kNQ, 256>(v, red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int q = 0; q < kNQ; ++q) sums[job][q] = v[q];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+
+  if (mode == kDecideInit) {
+    if (!(st->epsN > st->eps1) || !isfinite(st->epsN) || !isfinite(st->eps1) ||
+        sums[0][kQBad] > 0.0) {
+      st->status = DMPT_ENUMERIC;
+      st->done = 1;
+      return;
+    }
+    st->NS = sums[0][kQTrace];
+    st->NX = sums[0][kQFroNew];
+    st->s0_exp = st->precision == DMPT_DUAL_FP16 ? kFp16TargetExp - 1 : 0;
+    st->cur0 = 0;
+    st->d0_conv = 0;
+    st->d0_layer = 0;
+    st->layers_run = 0;
+    st->froerr0 = 0.0;
+    for (int j = 0; j < k; ++j) {
+      st->cur1[j] = 0;
+      st->d1_conv[j] = 0;
+      st->d1_layer[j] = 0;
+      st->s1_fro2[j] = sums[1 + j][kQFroNew];
+      st->s1_exp_cur[j] = st->precision == DMPT_DUAL_FP16
+                              ? fp16_exponent_for(sqrt(st->s1_fro2[j]))
+                              : 0;
+    }
+    plan_layer(st, 1);
+    return;
+  }
+
+  // ---- a layer product has finished: apply its results
+  const int n = st->n_layer;
+  if (st->timeout_flag) {
+    st->status = DMPT_ETIMEOUT;
+    st->done = 1;
+    return;
+  }
+  double bad = 0.0;
+  if (st->plan_square) bad += sums[0][kQBad];
+  for (int j = 0; j < k; ++j)
+    if (st->plan_resp[j]) bad += sums[1 + j][kQBad];
+  if (bad > 0.0) {
+    st->status = DMPT_ENUMERIC;
+    st->done = 1;
+    return;
+  }
+  if (st->plan_square) {
+    if (st->plan_write0) {
+      st->NS = sums[0][kQTrace];    // Tr S_n      (N_S of Alg. 2)
+      st->NX = sums[0][kQFroNew];   // ||S_n||_F^2 = Tr S_n^2 (N_X of the next layer)
+      st->cur0 ^= 1;
+    } else {
+      st->froerr0 = sqrt(sums[0][kQFroDiff]);  // FroErr^(0) of Alg. 2
+    }
+  }
+  for (int j = 0; j < k; ++j) {
+    if (!st->plan_resp[j]) continue;
+    const double fe = sqrt(sums[1 + j][kQFroDiff]);  // FroErr^(1)_n of Alg. 3
+    st->froerr1[j][n] = fe;
+    bool fired = false;
+    if (st->d0_conv && n - 2 >= st->d0_layer)
+      fired = fe >= st->c_pt * st->froerr0 * st->froerr1[j][n - 2];
+    if (fired) {
+      st->d1_conv[j] = 1;  // keep S1_{n-1}: the buffer written by this layer is dropped
+      st->d1_layer[j] = n;
+    } else {
+      st->cur1[j] ^= 1;
+      st->s1_fro2[j] = sums[1 + j][kQFroNew];
+      st->s1_exp_cur[j] = st->s1_exp_next[j];
+    }
+  }
+  st->layers_run = n;
+  bool all1 = true;
+  for (int j = 0; j < k; ++j) all1 = all1 && st->d1_conv[j];
+  if (st->d0_conv && all1) {
+    st->status = DMPT_OK;
+    st->done = 1;
+    st->n_layer = n + 1;
+    return;
+  }
+  if (n + 1 > st->max_layers) {
+    st->status = DMPT_ENOTCONV;
+    st->done = 1;
+    st->n_layer = n + 1;
+    return;
+  }
+  plan_layer(st, n + 1);
+}
+
+cudaError_t launch_decide(const Layout& L, void* ws, int mode, int64_t entries, cudaStream_t s) {
+  char* base = (char*)ws;
+  decide_kernel<<<1, 256, 0, s>>>((State*)(base + L.off_state),
+                                  (const double*)(base + L.off_partials), L.partial_tiles,
+                                  entries, mode);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// SIMT layer product with fused epilogue (FP64 and FP32 forms).
+//
+// Grid: (upper tiles, 1 + K).  Job 0 computes X = S0 S0 (Sec. II B,
+// Eq. (DNN-SP2_act)) for tile (I, J), I <= J; job 1+k computes
+// X1 = S0 S1_k + S1_k S0 (activation f^(1), Eq. (eq:activation-function))
+// as one accumulation over two K-passes.  Both operands are read as row
+// panels: for symmetric B, B[k][j] = B[j][k].  The epilogue applies
+// S_n = sigma X + (1 - sigma) S_{n-1} (Eq. (eq:Sn); Alg. 2 / Alg. 3 updates)
+// to the elements with row <= col, stores them at (r, c) and (c, r) in the
+// other ping-pong buffer, and reduces the Alg. 2 / 3 norms in FP64.
+
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using type = float4;
+  static constexpr int width = 4;
+};
+template <>
+struct Vec<double> {
+  using type = double2;
+  static constexpr int width = 2;
+};
+
+template <typename T, int TM>
+__device__ __forceinline__ int frag_index(int t, int m) {
+  // the TM rows (cols) of a thread: two runs of TM/2 contiguous elements,
+  // the second BT/2 after the first
+  constexpr int H = TM / 2;
+  constexpr int BT = 16 * TM;
+  return m < H ? t * H + m : BT / 2 + t * H + (m - H);
+}
+
+template <typename T, int TM, int BK>
+__global__ void __launch_bounds__(256)
+    layer_simt_kernel(State* st, T* __restrict__ master, int64_t Np, int k,
+                      double* __restrict__ partials, int64_t ptiles) {
+  constexpr int BT = 16 * TM;
+  constexpr int VW = Vec<T>::width;
+  using V = typename Vec<T>::type;
+  constexpr int CPR = BK / VW;                 // vectors per tile row
+  constexpr int NV = BT * BK / (256 * VW);     // vectors per thread per operand
+  constexpr int PAD = VW;
+
+  __shared__ __align__(16) T As[BK][BT + PAD];
+  __shared__ __align__(16) T Bs[BK][BT + PAD];
+  __shared__ double red[4 * 256];
+
+  if (st->done) return;
+  const int job = blockIdx.y;
+  const int run = job == 0 ? st->plan_square : st->plan_resp[job - 1];
+  if (!run) return;
+
+  // upper tile (I, J), I <= J, row-major over the upper triangle
+  const int T_ = (int)(Np / BT);
+  int64_t t = blockIdx.x;
+  int I = 0;
+  while (t >= T_ - I) {
+    t -= T_ - I;
+    ++I;
+  }
+  const int J = I + (int)t;
+
+  const size_t mat = (size_t)Np * Np;
+  const int cur0 = st->cur0;
+  const int cur = job == 0 ? cur0 : st->cur1[job - 1];
+  const T* S0 = master + (size_t)(cur0 * (1 + k)) * mat;
+  const T* Sj = master + (size_t)(cur * (1 + k) + job) * mat;   // S0 (job 0) or S1_k
+  T* out = master + (size_t)((cur ^ 1) * (1 + k) + job) * mat;
+
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  T acc[TM][TM];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TM; ++j) acc[i][j] = T(0);
+
+  const int passes = job == 0 ? 1 : 2;
+  for (int pass = 0; pass < passes; ++pass) {
+    // pass 0: A = S0 rows I, B = Sj rows J;  pass 1: A = Sj rows I, B = S0 rows J
+    const T* A = (pass == 0 ? S0 : Sj) + (size_t)I * BT * Np;
+    const T* B = (pass == 0 ? Sj : S0) + (size_t)J * BT * Np;
+    V ra[NV], rb[NV];
+    auto gload = [&](int kb) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const int idx = tid + 256 * v;
+        const int row = idx / CPR, cq = idx % CPR;
+        ra[v] = *reinterpret_cast<const V*>(A + (size_t)row * Np + kb + cq * VW);
+        rb[v] = *reinterpret_cast<const V*>(B + (size_t)row * Np + kb + cq * VW);
+      }
+    };
+    auto sstore = [&]() {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const int idx = tid + 256 * v;
+        const int row = idx / CPR, cq = idx % CPR;
+        const T* pa = reinterpret_cast<const T*>(&ra[v]);
+        const T* pb = reinterpret_cast<const T*>(&rb[v]);
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+          As[cq * VW + e][row] = pa[e];
+          Bs[cq * VW + e][row] = pb[e];
+        }
+      }
+    };
+    gload(0);
+    for (int kb = 0; kb < Np; kb += BK) {
+      __syncthreads();
+      sstore();
+      __syncthreads();
+      if (kb + BK < Np) gload(kb + BK);
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        T a[TM], b[TM];
+#pragma unroll
+        for (int m = 0; m < TM; ++m) a[m] = As[kk][frag_index<T, TM>(ty, m)];
+#pragma unroll
+        for (int m = 0; m < TM; ++m) b[m] = Bs[kk][frag_index<T, TM>(tx, m)];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TM; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+    }
+  }
+
+  // ---- fused epilogue
+  const T sg = (T)st->sigma_cur;
+  const T om = (T)1 - sg;
+  const bool write = job == 0 ? st->plan_write0 != 0 : true;
+  double tr = 0.0, fnew = 0.0, fdiff = 0.0, bad = 0.0;
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int64_t r = (int64_t)I * BT + frag_index<T, TM>(ty, i);
+#pragma unroll
+    for (int j = 0; j < TM; ++j) {
+      const int64_t c = (int64_t)J * BT + frag_index<T, TM>(tx, j);
+      if (r > c) continue;  // owned by the mirrored element
+      const T x = acc[i][j];
+      const T old = Sj[(size_t)r * Np + c];
+      const double w = (r == c) ? 1.0 : 2.0;
+      const double dd = (double)old - (double)x;
+      fdiff += w * dd * dd;
+      if (!isfinite((double)x)) bad += 1.0;
+      if (write) {
+        const T nw = sg * x + om * old;
+        out[(size_t)r * Np + c] = nw;
+        if (r != c) out[(size_t)c * Np + r] = nw;
+        const double dn = (double)nw;
+        fnew += w * dn * dn;
+        if (r == c) tr += dn;
+      }
+    }
+  }
+  double v[4] = {tr, fnew, fdiff, bad};
+  block_sum<4, 256>(v, red);
+  if (tid == 0) {
+    double* p = partials + ((size_t)job * ptiles + blockIdx.x) * kNQ;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) p[q] = v[q];
+  }
+}
+
+int simt_tile(int precision) { return precision == DMPT_FP64 ? 64 : 128; }
+
+cudaError_t launch_layer_simt(const Layout& L, void* ws, cudaStream_t s, int64_t* entries,
+                              double* pass_flops) {
+  char* base = (char*)ws;
+  State* st = (State*)(base + L.off_state);
+  double* partials = (double*)(base + L.off_partials);
+  const int bt = simt_tile(L.precision);
+  dim3 grid((unsigned)upper_tiles(L.Np, bt), 1 + L.k);
+  if (L.precision == DMPT_FP64)
+    layer_simt_kernel<double, 4, 8><<<grid, 256, 0, s>>>(st, (double*)(base + L.off_master),
+                                                         L.Np, L.k, partials, L.partial_tiles);
+  else
+    layer_simt_kernel<float, 8, 16><<<grid, 256, 0, s>>>(st, (float*)(base + L.off_master),
+                                                         L.Np, L.k, partials, L.partial_tiles);
+  if (entries) *entries = upper_tiles(L.Np, bt);
+  if (pass_flops) *pass_flops = (double)upper_tiles(L.Np, bt) * bt * bt * (double)L.Np * 2.0;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Dual split of the initial layer (Sec. II C, Eq. (DualMat2)):
+//   hi = R16[2^e X],  lo = R16[2^e X - hi]   (round to nearest even),
+// with e = s0_exp for S0 and s1_exp_cur[k] for S1_k (exact power-of-two
+// scaling keeps FP16 values in range; BF16 uses e = 0).
+
+template <typename H16>
+__device__ __forceinline__ H16 to16(float x);
+template <>
+__device__ __forceinline__ __half to16<__half>(float x) { return __float2half_rn(x); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float x) {
+  return __float2bfloat16_rn(x);
+}
+__device__ __forceinline__ float from16(__half x) { return __half2float(x); }
+__device__ __forceinline__ float from16(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+template <typename H16>
+__global__ void split_kernel(const State* st, const float* __restrict__ master, H16* ops,
+                             int64_t Np, int k) {
+  const size_t mat = (size_t)Np * Np;
+  const int m = blockIdx.y;  // matrix: 0 = S0, 1 + j = S1_j
+  const int cur = m == 0 ? st->cur0 : st->cur1[m - 1];
+  const int e = m == 0 ? st->s0_exp : st->s1_exp_cur[m - 1];
+  const float* src = master + (size_t)(cur * (1 + k) + m) * mat;
+  H16* hi = ops + ((size_t)(cur * (1 + k) + m) * 2 + 0) * mat;
+  H16* lo = ops + ((size_t)(cur * (1 + k) + m) * 2 + 1) * mat;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < mat;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const float x = ldexpf(src[i], e);
+    const H16 h = to16<H16>(x);
+    hi[i] = h;
+    lo[i] = to16<H16>(x - from16(h));
+  }
+}
+
+cudaError_t launch_split(const Layout& L, void* ws, cudaStream_t s) {
+  char* base = (char*)ws;
+  const State* st = (const State*)(base + L.off_state);
+  dim3 grid(152 * 4, 1 + L.k);
+  if (L.precision == DMPT_DUAL_FP16)
+    split_kernel<__half><<<grid, 256, 0, s>>>(st, (const float*)(base + L.off_master),
+                                              (__half*)(base + L.off_ops16), L.Np, L.k);
+  else
+    split_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(st, (const float*)(base + L.off_master),
+                                                     (__nv_bfloat16*)(base + L.off_ops16),
+                                                     L.Np, L.k);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Outputs: P = S0, P1_k = S1_k (orthogonal basis, Z = I), as float64.
+
+template <typename T>
+__global__ void finalize_kernel(const State* st, const T* __restrict__ master, double* P,
+                                double* P1, int64_t n, int64_t Np, int64_t ld, int k) {
+  const size_t mat = (size_t)Np * Np;
+  const int m = blockIdx.y;
+  if (m == 0 && P == nullptr) return;
+  const int cur = m == 0 ? st->cur0 : st->cur1[m - 1];
+  const T* src = master + (size_t)(cur * (1 + k) + m) * mat;
+  double* dst = m == 0 ? P : P1 + (size_t)(m - 1) * n * ld;
+  const int64_t total = n * n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / n, c = i - r * n;
+    dst[r * ld + c] = (double)src[(size_t)r * Np + c];
+  }
+}
+
+cudaError_t launch_finalize(const Layout& L, void* ws, double* P, double* P1, int64_t ld,
+                            cudaStream_t s) {
+  char* base = (char*)ws;
+  const State* st = (const State*)(base + L.off_state);
+  dim3 grid(152 * 4, 1 + L.k);
+  if (L.precision == DMPT_FP64)
+    finalize_kernel<double><<<grid, 256, 0, s>>>(st, (const double*)(base + L.off_master), P,
+                                                 P1, L.n, L.Np, ld, L.k);
+  else
+    finalize_kernel<float><<<grid, 256, 0, s>>>(st, (const float*)(base + L.off_master), P, P1,
+                                                L.n, L.Np, ld, L.k);
+  return cudaGetLastError();
+}
+
+// n_occ = 0 (full = 0) or n_occ = n (full = 1): P = 0 or I, P1 = 0.
+__global__ void trivial_kernel(int64_t n, int k, int64_t ld, int full, double* P, double* P1) {
+  const int m = blockIdx.y;
+  if (m == 0 && P == nullptr) return;
+  double* dst = m == 0 ? P : P1 + (size_t)(m - 1) * n * ld;
+  const int64_t total = n * n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / n, c = i - r * n;
+    dst[r * ld + c] = (m == 0 && full && r == c) ? 1.0 : 0.0;
+  }
+}
+
+cudaError_t launch_trivial(int64_t n, int k, int64_t ld, int full, double* P, double* P1,
+                           cudaStream_t s) {
+  dim3 grid(152, 1 + k);
+  trivial_kernel<<<grid, 256, 0, s>>>(n, k, ld, full, P, P1);
+  return cudaGetLastError();
+}
+
+}  // namespace dmpt

@@ -1,0 +1,650 @@
+// Dual-precision layer product on the sm_103a tensor cores (tcgen05 + TMEM
+// + TMA), with the SP2 layer update fused into the epilogue.
+//
+// What one launch computes (one deep layer of Sec. III, Algorithm 1):
+//   square   (job 0):   X  = S0 S0             ~ hi*hi + hi*lo + lo*hi
+//                       (Sec. II C, Eq. (S0 tensor core): A + B + B^T)
+//   response (job 1+k): X1 = S0 S1_k + S1_k S0 ~ sum of the 3-term dual
+//                       products of both orders (Sec. III D,
+//                       Eq. (FP32S0S1), Eq. (S0S1 tensor core))
+// each accumulated in FP32 in tensor memory, and then
+//   S_n = sigma X + (1 - sigma) S_{n-1}      (Eq. (eq:Sn); Alg. 2 and 3)
+// written as an FP32 master plus its new hi/lo split (Eq. (DualMat2)).
+//
+// Symmetry (Sec. III D): every S is symmetric, so the B operand of a row
+// block product can be read as a row panel (B[k][j] = B[j][k], "K-major"
+// for both operands) and only tiles holding elements with row <= col are
+// computed; the epilogue stores each such element at (r, c) and (c, r).
+// The response needs both orders S0 S1 and S1 S0 for a tile, which are two
+// K passes into the same accumulator.
+//
+// Kernel structure (persistent, one CTA per SM, 192 threads):
+//   warp 0      TMA producer: 4-stage ring of {A_hi, A_lo, B_hi, B_lo}
+//               tiles (128x32, 128x32, 256x32, 256x32 16-bit, 64B swizzle)
+//   warp 1      TMEM owner and MMA issuer: tcgen05.mma.cta_group::1
+//               kind::f16, M = 128, N = 256, K = 16, FP32 accumulate, two
+//               256-column accumulators in TMEM (double buffered)
+//   warps 2..5  epilogue: tcgen05.ld of one row per thread, fused update,
+//               stores, deterministic FP64 partial norms per tile
+// Every mbarrier wait is bounded in time; on expiry the CTA raises
+// State::timeout_flag, drains its copies in flight (bounded), frees TMEM and
+// returns, and the host reports DMPT_ETIMEOUT.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include <type_traits>
+
+#include "dmpt_internal.cuh"
+
+namespace dmpt {
+namespace tc {
+
+constexpr int BM = 128;          // rows per tile (TMEM lanes)
+constexpr int BN = 256;          // columns per tile
+constexpr int BK = 32;           // K elements per stage (64 B rows)
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;   // 8 KB
+constexpr int B_BYTES = BN * BK * 2;   // 16 KB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 48 KB
+constexpr int TMEM_COLS = 512;   // two accumulators of BN columns
+constexpr int NUM_THREADS = 192;
+constexpr int EPI_THREADS = 128;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* align */ + 1024 /* barriers etc */ +
+                           EPI_THREADS * 4 * 8;
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false when `limit_ns` passes or another role of this CTA
+// has aborted.  On expiry it raises both abort flags.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns,
+                                          volatile int* abort_smem, int* timeout_global) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  uint32_t it = 0;
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((++it & 255) == 0) {
+      if (*abort_smem) return false;
+      if (gtimer() - t0 > limit_ns) {
+        *abort_smem = 1;
+        atomicExch(timeout_global, 1);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor, K-major operand with 64-byte swizzle:
+// rows of 64 B, 8-row groups 512 B apart (SBO), version 1, layout 4.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;             // LBO (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;    // SBO
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)4 << 61;             // SWIZZLE_64B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A/B = F16 (0) or BF16 (1),
+// both K-major, N = 256, M = 128.
+__host__ __device__ constexpr uint32_t make_idesc(int ab_type) {
+  return (1u << 4) | ((uint32_t)ab_type << 7) | ((uint32_t)ab_type << 10) |
+         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// FP16 / BF16 rounding (round to nearest even) used by the dual split.
+template <bool BF>
+struct Cvt;
+template <>
+struct Cvt<false> {
+  using T = __half;
+  static __device__ __forceinline__ T to(float x) { return __float2half_rn(x); }
+  static __device__ __forceinline__ float from(T h) { return __half2float(h); }
+};
+template <>
+struct Cvt<true> {
+  using T = __nv_bfloat16;
+  static __device__ __forceinline__ T to(float x) { return __float2bfloat16_rn(x); }
+  static __device__ __forceinline__ float from(T h) { return __bfloat162float(h); }
+};
+
+// AND of a predicate over the 128 epilogue threads (named barrier 1).
+__device__ __forceinline__ int epi_all(int pred) {
+  int out;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.b32 q, %1, 0;\n\t"
+      "bar.red.and.pred p, 1, 128, q;\n\t"
+      "selp.s32 %0, 1, 0, p;\n\t}"
+      : "=r"(out)
+      : "r"(pred)
+      : "memory");
+  return out;
+}
+
+// ---------------------------------------------------------------------------
+// Work items: (job, tile).  Tiles: 128-row block I and 256-column block J
+// with I <= 2J + 1 (the tile holds some element with row <= col).  Tile t
+// is J-major: tiles of column block J are t = J(J+1) ... J(J+1) + 2J + 1.
+
+__host__ __device__ inline int64_t num_tiles(int64_t Np) {
+  const int64_t tj = Np / BN;
+  return tj * (tj + 1);
+}
+__device__ __forceinline__ void tile_coords(int64_t t, int* I, int* J) {
+  int j = (int)((sqrt(4.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while ((int64_t)(j + 1) * (j + 2) <= t) ++j;
+  while ((int64_t)j * (j + 1) > t) --j;
+  *J = j;
+  *I = (int)(t - (int64_t)j * (j + 1));
+}
+
+struct Plan {
+  int njobs;          // jobs run this layer
+  int jobs[kMaxK + 1];  // job ids in item order (responses first)
+  int cur[kMaxK + 1];   // current buffer of each job's matrix
+  int e_cur[kMaxK + 1]; // exponent of the current 16-bit copies of that matrix
+  int e_new[kMaxK + 1]; // exponent for the new copies
+};
+
+__device__ __forceinline__ int zslice(int buf, int m, int part, int k) {
+  return (buf * (1 + k) + m) * 2 + part;
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    layer_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                    State* st, float* __restrict__ master, uint16_t* __restrict__ ops,
+                    int64_t Np, int k, double* __restrict__ partials, int64_t ptiles,
+                    uint64_t limit_ns) {
+  using CV = Cvt<BF16>;
+  using H16 = typename CV::T;
+  extern __shared__ uint8_t smem_raw[];
+  if (st->done) return;
+
+  // ---- plan of this layer (identical in every CTA)
+  Plan pl;
+  pl.njobs = 0;
+  for (int j = 0; j < k; ++j)
+    if (st->plan_resp[j]) pl.jobs[pl.njobs++] = 1 + j;
+  if (st->plan_square) pl.jobs[pl.njobs++] = 0;
+  if (pl.njobs == 0) return;
+  const int cur0 = st->cur0;
+  const int sigma = st->sigma_cur;
+  const int write0 = st->plan_write0;
+  const int s0e = st->s0_exp;
+
+  const int64_t tiles = num_tiles(Np);
+  const int64_t items = tiles * pl.njobs;
+  const int kblocks = (int)(Np / BK);
+
+  // ---- shared memory carve-up (1024-aligned stage ring)
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw);
+  const uint32_t ring = base;
+  uint8_t* misc = gbase + STAGES * STAGE_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(misc);  // full, empty, tfull, tempty, drain
+  const uint32_t bar_full = smem_u32(bars);
+  const uint32_t bar_empty = bar_full + 8 * STAGES;
+  const uint32_t bar_tfull = bar_empty + 8 * STAGES;
+  const uint32_t bar_tempty = bar_tfull + 8 * 2;
+  const uint32_t bar_drain = bar_tempty + 8 * 2;
+  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(misc + 128);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(misc + 136);
+  double* red = reinterpret_cast<double*>(misc + 1024);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(bar_full + 8 * s, 1);
+      mbar_init(bar_empty + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bar_tfull + 8 * b, 1);
+      mbar_init(bar_tempty + 8 * b, 4);   // one arrive per epilogue warp
+    }
+    mbar_init(bar_drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32((const void*)tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  int* timeout_global = &st->timeout_flag;
+
+  if (warp == 0) {
+    // ================= TMA producer =================
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int inflight = 0;  // stages issued whose completion this thread has not observed
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        const int job = pl.jobs[it / tiles];
+        int I, J;
+        tile_coords(it % tiles, &I, &J);
+        const int passes = job == 0 ? 1 : 2;
+        const int mj = job;  // matrix of this job: 0 = S0, 1 + j = S1_j
+        const int curj = job == 0 ? cur0 : st->cur1[job - 1];
+        for (int pass = 0; pass < passes && ok; ++pass) {
+          // pass 0: A = S0 rows of I, B = S_job rows of J; pass 1: swapped
+          const int mA = pass == 0 ? 0 : mj, bufA = pass == 0 ? cur0 : curj;
+          const int mB = pass == 0 ? mj : 0, bufB = pass == 0 ? curj : cur0;
+          const int zAh = zslice(bufA, mA, 0, k), zAl = zslice(bufA, mA, 1, k);
+          const int zBh = zslice(bufB, mB, 0, k), zBl = zslice(bufB, mB, 1, k);
+          for (int kb = 0; kb < kblocks; ++kb) {
+            if (!mbar_wait(bar_empty + 8 * stage, phase ^ 1, limit_ns, abort_flag,
+                           timeout_global)) {
+              ok = false;
+              break;
+            }
+            const uint32_t sA = ring + stage * STAGE_BYTES;
+            const uint32_t fb = bar_full + 8 * stage;
+            mbar_expect_tx(fb, STAGE_BYTES);
+            tma_load_3d(sA, &mapA, kb * BK, I * BM, zAh, fb);
+            tma_load_3d(sA + A_BYTES, &mapA, kb * BK, I * BM, zAl, fb);
+            tma_load_3d(sA + 2 * A_BYTES, &mapB, kb * BK, J * BN, zBh, fb);
+            tma_load_3d(sA + 2 * A_BYTES + B_BYTES, &mapB, kb * BK, J * BN, zBl, fb);
+            inflight = inflight < STAGES ? inflight + 1 : STAGES;
+            if (++stage == STAGES) {
+              stage = 0;
+              phase ^= 1;
+            }
+          }
+        }
+      }
+      if (!ok) {
+        // drain: wait (bounded) until the copies already issued have landed
+        int s = stage;
+        uint32_t ph = phase;
+        for (int i = 0; i < inflight; ++i) {
+          if (--s < 0) {
+            s = STAGES - 1;
+            ph ^= 1;
+          }
+          const uint64_t t0 = gtimer();
+          while (!mbar_try_wait(bar_full + 8 * s, ph) && gtimer() - t0 < limit_ns) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ================= MMA issuer =================
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc(BF16 ? 1 : 0);
+      int stage = 0;
+      uint32_t phase = 0;
+      int ab = 0;
+      uint32_t abphase = 0;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        const int job = pl.jobs[it / tiles];
+        const int passes = job == 0 ? 1 : 2;
+        if (!mbar_wait(bar_tempty + 8 * ab, abphase ^ 1, limit_ns, abort_flag, timeout_global)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t d = tmem_base + (uint32_t)(ab * BN);
+        uint32_t acc = 0;
+        for (int pass = 0; pass < passes && ok; ++pass) {
+          for (int kb = 0; kb < kblocks; ++kb) {
+            if (!mbar_wait(bar_full + 8 * stage, phase, limit_ns, abort_flag, timeout_global)) {
+              ok = false;
+              break;
+            }
+            fence_after();
+            const uint32_t sA = ring + stage * STAGE_BYTES;
+            const uint64_t ah = sw64_desc(sA), al = sw64_desc(sA + A_BYTES);
+            const uint64_t bh = sw64_desc(sA + 2 * A_BYTES);
+            const uint64_t bl = sw64_desc(sA + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint64_t off = (uint64_t)((kk * 32) >> 4);  // 16 elements = 32 B
+              mma_f16(d, ah + off, bh + off, idesc, acc);        // hi * hi
+              acc = 1;
+              mma_f16(d, ah + off, bl + off, idesc, 1);          // hi * lo
+              mma_f16(d, al + off, bh + off, idesc, 1);          // lo * hi
+            }
+            mma_commit(bar_empty + 8 * stage);  // frees the stage when these MMAs finish
+            if (++stage == STAGES) {
+              stage = 0;
+              phase ^= 1;
+            }
+          }
+        }
+        if (!ok) break;
+        mma_commit(bar_tfull + 8 * ab);  // accumulator ready
+        if (++ab == 2) {
+          ab = 0;
+          abphase ^= 1;
+        }
+      }
+      // wait (bounded) until every MMA this thread issued has completed, so
+      // TMEM is idle before it is freed
+      mma_commit(bar_drain);
+      const uint64_t t0 = gtimer();
+      while (!mbar_try_wait(bar_drain, 0) && gtimer() - t0 < limit_ns) {
+      }
+    }
+  } else {
+    // ================= epilogue (warps 2..5) =================
+    const int q = warp & 3;                 // TMEM lane quadrant of this warp
+    const int rloc = 32 * q + lane;         // row within the tile
+    const int et = threadIdx.x - 64;        // 0..127
+    const size_t mat = (size_t)Np * Np;
+    int ab = 0;
+    uint32_t abphase = 0;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+      const int job = pl.jobs[it / tiles];
+      const int64_t t = it % tiles;
+      int I, J;
+      tile_coords(t, &I, &J);
+      const bool ok = mbar_wait(bar_tfull + 8 * ab, abphase, limit_ns, abort_flag, timeout_global);
+      // all 128 epilogue threads take the same branch (warp-collective
+      // tcgen05.ld follows)
+      if (!epi_all(ok && !*abort_flag)) break;
+      fence_after();
+
+      const int curj = job == 0 ? cur0 : st->cur1[job - 1];
+      const int e_cur = job == 0 ? s0e : st->s1_exp_cur[job - 1];
+      const int e_new = job == 0 ? s0e : st->s1_exp_next[job - 1];
+      const float unscale = ldexpf(1.0f, -(s0e + e_cur));   // exact powers of two
+      const float scale_new = ldexpf(1.0f, e_new);
+      const float sg = (float)sigma, om = 1.0f - (float)sigma;
+      const bool write = job != 0 || write0;
+      const float* Sold = master + (size_t)(curj * (1 + k) + job) * mat;
+      float* Snew = master + (size_t)((curj ^ 1) * (1 + k) + job) * mat;
+      H16* hi_new = reinterpret_cast<H16*>(ops) + (size_t)zslice(curj ^ 1, job, 0, k) * mat;
+      H16* lo_new = reinterpret_cast<H16*>(ops) + (size_t)zslice(curj ^ 1, job, 1, k) * mat;
+
+      const int64_t r = (int64_t)I * BM + rloc;
+      double tr = 0.0, fnew = 0.0, fdiff = 0.0, bad = 0.0;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        float x[32];
+        tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * BN + c0), x);
+        const int64_t cb = (int64_t)J * BN + c0;   // first global column of the chunk
+        if (r > cb + 31) continue;                 // no element with r <= c in this chunk
+        const float* po = Sold + (size_t)r * Np + cb;
+        float old[32];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+          const float4 o4 = *reinterpret_cast<const float4*>(po + 4 * v);
+          old[4 * v + 0] = o4.x;
+          old[4 * v + 1] = o4.y;
+          old[4 * v + 2] = o4.z;
+          old[4 * v + 3] = o4.w;
+        }
+        float nw[32];
+        H16 nh[32], nl[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float xv = x[i] * unscale;
+          const int64_t c = cb + i;
+          const bool own = c >= r;
+          const double w = (c == r) ? 1.0 : 2.0;
+          if (!isfinite(xv)) bad += own ? 1.0 : 0.0;
+          const double dd = (double)old[i] - (double)xv;
+          fdiff += own ? w * dd * dd : 0.0;
+          const float n1 = sg * xv + om * old[i];
+          nw[i] = n1;
+          const double dn = (double)n1;
+          fnew += (own && write) ? w * dn * dn : 0.0;
+          tr += (own && write && c == r) ? dn : 0.0;
+          const float y = n1 * scale_new;
+          const H16 h = CV::to(y);
+          nh[i] = h;
+          nl[i] = CV::to(y - CV::from(h));
+        }
+        if (!write) continue;
+        // direct stores at (r, c)
+        if (r <= cb) {
+          float* pn = Snew + (size_t)r * Np + cb;
+#pragma unroll
+          for (int v = 0; v < 8; ++v)
+            *reinterpret_cast<float4*>(pn + 4 * v) =
+                make_float4(nw[4 * v], nw[4 * v + 1], nw[4 * v + 2], nw[4 * v + 3]);
+          uint4* ph = reinterpret_cast<uint4*>(hi_new + (size_t)r * Np + cb);
+          uint4* plo = reinterpret_cast<uint4*>(lo_new + (size_t)r * Np + cb);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            ph[v] = *reinterpret_cast<const uint4*>(&nh[8 * v]);
+            plo[v] = *reinterpret_cast<const uint4*>(&nl[8 * v]);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int64_t c = cb + i;
+            if (c >= r) {
+              Snew[(size_t)r * Np + c] = nw[i];
+              hi_new[(size_t)r * Np + c] = nh[i];
+              lo_new[(size_t)r * Np + c] = nl[i];
+            }
+          }
+        }
+        // mirrored stores at (c, r): for fixed c the warp's 32 rows are contiguous
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int64_t c = cb + i;
+          if (c > r) {
+            Snew[(size_t)c * Np + r] = nw[i];
+            hi_new[(size_t)c * Np + r] = nh[i];
+            lo_new[(size_t)c * Np + r] = nl[i];
+          }
+        }
+      }
+      // accumulator drained: hand the TMEM buffer back to the MMA warp
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar_tempty + 8 * ab);
+      if (++ab == 2) {
+        ab = 0;
+        abphase ^= 1;
+      }
+      // deterministic tile reduction over the 128 epilogue threads
+      red[0 * EPI_THREADS + et] = tr;
+      red[1 * EPI_THREADS + et] = fnew;
+      red[2 * EPI_THREADS + et] = fdiff;
+      red[3 * EPI_THREADS + et] = bad;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      for (int s = EPI_THREADS / 2; s > 0; s >>= 1) {
+        if (et < s) {
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) red[qq * EPI_THREADS + et] += red[qq * EPI_THREADS + et + s];
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+      }
+      if (et == 0) {
+        double* p = partials + ((size_t)job * ptiles + t) * kNQ;
+        p[kQTrace] = red[0];
+        p[kQFroNew] = red[EPI_THREADS];
+        p[kQFroDiff] = red[2 * EPI_THREADS];
+        p[kQBad] = red[3 * EPI_THREADS];
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+    }
+  }
+
+  // ---- teardown: everyone done (or aborted); free TMEM
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(TMEM_COLS));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, void* base, int64_t Np, int slices, int box_rows, bool bf16) {
+  auto enc = get_encoder();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)Np, (cuuint64_t)Np, (cuuint64_t)slices};
+  cuuint64_t strides[2] = {(cuuint64_t)Np * 2, (cuuint64_t)Np * Np * 2};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                   3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace tc
+
+int tc_tile() { return tc::BN; }
+
+cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double timeout_s,
+                            int64_t* entries, double* pass_flops) {
+  using namespace tc;
+  char* base = (char*)ws;
+  const bool bf16 = L.precision == DMPT_DUAL_BF16;
+  const int slices = 2 * (1 + L.k) * 2;
+  CUtensorMap mA, mB;
+  if (!make_map(&mA, base + L.off_ops16, L.Np, slices, BM, bf16) ||
+      !make_map(&mB, base + L.off_ops16, L.Np, slices, BN, bf16))
+    return cudaErrorInvalidValue;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(layer_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         SMEM_BYTES);
+    cudaFuncSetAttribute(layer_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         SMEM_BYTES);
+  }
+  const int64_t tiles = num_tiles(L.Np);
+  // the number of jobs is only known on the device; size the grid for the
+  // largest case and let surplus CTAs exit
+  int64_t max_items = tiles * (1 + L.k);
+  int grid = (int)(max_items < sms ? max_items : sms);
+  const uint64_t limit_ns = (uint64_t)(timeout_s * 1e9);
+  State* st = (State*)(base + L.off_state);
+  float* master = (float*)(base + L.off_master);
+  uint16_t* ops = (uint16_t*)(base + L.off_ops16);
+  double* partials = (double*)(base + L.off_partials);
+  if (bf16)
+    layer_tc_kernel<true><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(mA, mB, st, master, ops, L.Np,
+                                                                L.k, partials, L.partial_tiles,
+                                                                limit_ns);
+  else
+    layer_tc_kernel<false><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(mA, mB, st, master, ops, L.Np,
+                                                                 L.k, partials, L.partial_tiles,
+                                                                 limit_ns);
+  if (entries) *entries = tiles;
+  if (pass_flops) *pass_flops = (double)tiles * BM * BN * (double)L.Np * 2.0;
+  return cudaGetLastError();
+}
+
+}  // namespace dmpt

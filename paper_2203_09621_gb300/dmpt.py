@@ -1,0 +1,269 @@
+"""Thin ctypes binding of libdmpt.so (the C ABI in include/dmpt.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  PyTorch provides device memory and the stream.  If the library is
+missing the binding raises; there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libdmpt.so")
+
+DMPT_MAX_K = 8
+DMPT_MAX_LAYERS = 256
+
+PRECISIONS = {"fp64": 0, "fp32": 1, "dual_fp16": 2, "dual_bf16": 3}
+
+STATUS = {
+    0: "DMPT_OK", 1: "DMPT_EINVAL", 2: "DMPT_EWORKSPACE", 3: "DMPT_ENOTCONV",
+    4: "DMPT_ENUMERIC", 5: "DMPT_ETIMEOUT", 6: "DMPT_ECUDA", 7: "DMPT_EUNSUPPORTED",
+}
+
+
+class DmptOptions(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("max_layers", ctypes.c_int),
+        ("c_pt", ctypes.c_double),
+        ("c_d0", ctypes.c_double),
+        ("operand_scaling", ctypes.c_int),
+        ("sync_every", ctypes.c_int),
+        ("timing", ctypes.c_int),
+        ("timeout_s", ctypes.c_double),
+        ("ckpt_every", ctypes.c_int),
+        ("reserved", ctypes.c_int * 7),
+    ]
+
+
+class DmptInfo(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("layers", ctypes.c_int),
+        ("d0_layer", ctypes.c_int),
+        ("converged", ctypes.c_int),
+        ("d1_layer", ctypes.c_int * DMPT_MAX_K),
+        ("eps_min", ctypes.c_double),
+        ("eps_max", ctypes.c_double),
+        ("froerr0", ctypes.c_double),
+        ("froerr1", ctypes.c_double * DMPT_MAX_K),
+        ("ms_layers", ctypes.c_double),
+        ("product_launches", ctypes.c_int),
+        ("timed_launches", ctypes.c_int),
+        ("mma_flops", ctypes.c_double),
+        ("alg_flops", ctypes.c_double),
+        ("sigma", ctypes.c_byte * DMPT_MAX_LAYERS),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libdmpt.so and declare its exported functions."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run __graft_entry__.build() "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(path)
+    vp, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    lib.dmpt_create.argtypes = [ctypes.POINTER(vp), c_int]
+    lib.dmpt_create.restype = c_int
+    lib.dmpt_destroy.argtypes = [vp]
+    lib.dmpt_destroy.restype = c_int
+    lib.dmpt_default_options.argtypes = [ctypes.POINTER(DmptOptions)]
+    lib.dmpt_default_options.restype = None
+    lib.dmpt_status_string.argtypes = [c_int]
+    lib.dmpt_status_string.restype = ctypes.c_char_p
+    lib.dmpt_last_error.argtypes = [vp]
+    lib.dmpt_last_error.restype = ctypes.c_char_p
+    lib.dmpt_workspace_size.argtypes = [i64, c_int, ctypes.POINTER(DmptOptions)]
+    lib.dmpt_workspace_size.restype = ctypes.c_size_t
+    lib.dmpt_bounds.argtypes = [vp, vp, i64, i64, vp, vp]
+    lib.dmpt_bounds.restype = c_int
+    lib.dmpt_sp2_response.argtypes = [vp, vp, vp, c_int, i64, i64, i64,
+                                      ctypes.POINTER(DmptOptions), vp, vp,
+                                      ctypes.POINTER(DmptInfo), vp, ctypes.c_size_t, vp]
+    lib.dmpt_sp2_response.restype = c_int
+    _lib = lib
+    return lib
+
+
+class DmptError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+@dataclass
+class Info:
+    status: int
+    layers: int
+    d0_layer: int
+    converged: bool
+    d1_layer: list
+    eps_min: float
+    eps_max: float
+    froerr0: float
+    froerr1: list
+    ms_layers: float
+    product_launches: int
+    timed_launches: int
+    mma_flops: float
+    alg_flops: float
+    sigma: list
+
+    @classmethod
+    def from_c(cls, ci: DmptInfo, k: int) -> "Info":
+        return cls(status=ci.status, layers=ci.layers, d0_layer=ci.d0_layer,
+                   converged=bool(ci.converged), d1_layer=list(ci.d1_layer[:k]),
+                   eps_min=ci.eps_min, eps_max=ci.eps_max, froerr0=ci.froerr0,
+                   froerr1=list(ci.froerr1[:k]), ms_layers=ci.ms_layers,
+                   product_launches=ci.product_launches, timed_launches=ci.timed_launches,
+                   mma_flops=ci.mma_flops, alg_flops=ci.alg_flops,
+                   sigma=list(ci.sigma[:ci.layers]))
+
+
+def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_scaling=1,
+            sync_every=4, timing=False, timeout_s=2.0) -> DmptOptions:
+    lib = load_library()
+    o = DmptOptions()
+    lib.dmpt_default_options(ctypes.byref(o))
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.max_layers = int(max_layers)
+    o.c_pt = float(c_pt)
+    o.c_d0 = float(c_d0)
+    o.operand_scaling = int(operand_scaling)
+    o.sync_every = int(sync_every)
+    o.timing = int(bool(timing))
+    o.timeout_s = float(timeout_s)
+    return o
+
+
+class Context:
+    """A dmpt handle on one CUDA device plus a cached workspace tensor."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        self.lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("dmpt needs a CUDA device (GB300, sm_103a)")
+        self.device = device
+        h = ctypes.c_void_p()
+        st = self.lib.dmpt_create(ctypes.byref(h), device)
+        if st != 0:
+            raise DmptError(st, self.lib.dmpt_status_string(st).decode())
+        self.h = h
+        self._ws = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dmpt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != 0:
+            raise DmptError(st, self.lib.dmpt_last_error(self.h).decode())
+
+    def workspace_size(self, n: int, k: int, opts: DmptOptions) -> int:
+        return int(self.lib.dmpt_workspace_size(n, k, ctypes.byref(opts)))
+
+    def workspace(self, nbytes: int):
+        import torch
+        if self._ws is None or self._ws.numel() < nbytes:
+            self._ws = None
+            self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=f"cuda:{self.device}")
+        ptr = self._ws.data_ptr()
+        off = (-ptr) % 256
+        return ptr + off, self._ws.numel() - off
+
+    def bounds(self, H, stream=None):
+        """Gershgorin (eps_1, eps_N) of a float64 CUDA matrix H, as a 2-element tensor."""
+        import torch
+        n = H.shape[0]
+        eps = torch.empty(2, dtype=torch.float64, device=H.device)
+        s = stream if stream is not None else torch.cuda.current_stream(H.device)
+        self._check(self.lib.dmpt_bounds(self.h, H.data_ptr(), n, H.stride(0), eps.data_ptr(),
+                                         ctypes.c_void_p(s.cuda_stream)))
+        return eps
+
+    def sp2_response(self, H, H1, n_occ: int, precision="dual_fp16", out=None,
+                     want_P=True, stream=None, raise_on_error=True, **kw):
+        """P and P1 of (H, H1) by DNN-SP2-PT on the device.
+
+        H: (n, n) float64 CUDA tensor; H1: (n, n) or (k, n, n).  Returns
+        (P or None, P1 of shape (k, n, n), Info).
+        """
+        import torch
+        if H.dtype != torch.float64 or H1.dtype != torch.float64:
+            raise TypeError("H and H1 must be float64")
+        if not (H.is_cuda and H1.is_cuda):
+            raise TypeError("H and H1 must be CUDA tensors")
+        n = H.shape[0]
+        if H1.dim() == 2:
+            H1 = H1.unsqueeze(0)
+        k = H1.shape[0]
+        H = H.contiguous()
+        H1 = H1.contiguous()
+        opts = options(precision=precision, **kw)
+        if out is None:
+            P1 = torch.empty(k, n, n, dtype=torch.float64, device=H.device)
+            P = torch.empty(n, n, dtype=torch.float64, device=H.device) if want_P else None
+        else:
+            P, P1 = out
+        nbytes = self.workspace_size(n, k, opts)
+        if nbytes == 0:
+            raise DmptError(1, "invalid sizes or options")
+        ws_ptr, ws_len = self.workspace(nbytes)
+        info = DmptInfo()
+        s = stream if stream is not None else torch.cuda.current_stream(H.device)
+        st = self.lib.dmpt_sp2_response(
+            self.h, H.data_ptr(), H1.data_ptr(), k, n, n, int(n_occ), ctypes.byref(opts),
+            P.data_ptr() if P is not None else None, P1.data_ptr(), ctypes.byref(info),
+            ctypes.c_void_p(ws_ptr), ws_len, ctypes.c_void_p(s.cuda_stream))
+        inf = Info.from_c(info, k)
+        if st != 0 and raise_on_error:
+            self._check(st)
+        return P, P1, inf
+
+    def sp2_response_host(self, H_host, H1_host, n_occ: int, precision="dual_fp16",
+                          stream=None, **kw):
+        """End-to-end call from host (pinned CPU) tensors: copy in, solve, copy out."""
+        import torch
+        dev = torch.device(f"cuda:{self.device}")
+        H = H_host.to(dev, non_blocking=True)
+        H1 = H1_host.to(dev, non_blocking=True)
+        P, P1, inf = self.sp2_response(H, H1, n_occ, precision=precision, stream=stream, **kw)
+        return (P.to("cpu") if P is not None else None), P1.to("cpu"), inf
+
+
+_default_ctx: Optional[Context] = None
+
+
+def context(device: int = 0) -> Context:
+    global _default_ctx
+    if _default_ctx is None or _default_ctx.device != device:
+        _default_ctx = Context(device)
+    return _default_ctx
+
+
+def sp2_response(H, H1, n_occ, precision="dual_fp16", **kw):
+    """Module-level convenience wrapper around Context.sp2_response."""
+    return context(H.device.index or 0).sp2_response(H, H1, n_occ, precision=precision, **kw)
+
+
+def bounds(H):
+    return context(H.device.index or 0).bounds(H)

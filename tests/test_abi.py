@@ -1,0 +1,88 @@
+"""The C ABI library builds, loads without a GPU and exports what dmpt.h declares."""
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from tests.conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "dmpt.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2203_09621_gb300.build import build_library
+    from paper_2203_09621_gb300 import dmpt
+
+    build_library()
+    return dmpt.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_]+\*?\s+\**(dmpt_[a-z0-9_]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("dmpt_bounds", "dmpt_sp2_response", "dmpt_create", "dmpt_workspace_size"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib._name], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r" T (dmpt_[a-z0-9_]+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        assert hasattr(lib, n)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    from paper_2203_09621_gb300 import dmpt
+
+    src = tmp_path / "sz.c"
+    src.write_text('#include "dmpt.h"\n#include <stdio.h>\n#include <stddef.h>\n'
+                   'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(dmpt_options), '
+                   'sizeof(dmpt_info), offsetof(dmpt_info, sigma), offsetof(dmpt_options, timeout_s));'
+                   'return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    so, si, osig, oto = map(int, subprocess.run([str(exe)], capture_output=True, text=True).stdout.split())
+    assert so == ctypes.sizeof(dmpt.DmptOptions)
+    assert si == ctypes.sizeof(dmpt.DmptInfo)
+    assert osig == dmpt.DmptInfo.sigma.offset
+    assert oto == dmpt.DmptOptions.timeout_s.offset
+
+
+def test_host_only_calls(lib):
+    from paper_2203_09621_gb300 import dmpt
+
+    o = dmpt.DmptOptions()
+    lib.dmpt_default_options(ctypes.byref(o))
+    assert (o.precision, o.max_layers, o.c_pt, o.c_d0) == (2, 100, 9.0, 4.5)
+    assert lib.dmpt_status_string(0) == b"DMPT_OK"
+    # workspace grows with n and k, is 0 for invalid arguments
+    w1 = lib.dmpt_workspace_size(1000, 1, ctypes.byref(o))
+    w3 = lib.dmpt_workspace_size(1000, 3, ctypes.byref(o))
+    assert 0 < w1 < w3
+    assert lib.dmpt_workspace_size(0, 1, ctypes.byref(o)) == 0
+    assert lib.dmpt_workspace_size(100, 0, ctypes.byref(o)) == 0
+    assert lib.dmpt_workspace_size(100, 9, ctypes.byref(o)) == 0
+    bad = dmpt.DmptOptions()
+    lib.dmpt_default_options(ctypes.byref(bad))
+    bad.precision = 9
+    assert lib.dmpt_workspace_size(100, 1, ctypes.byref(bad)) == 0
+    # n = 8192, k = 3, dual: 2 x 4 FP32 masters + 2 x 4 x 2 16-bit halves of 8192^2
+    big = lib.dmpt_workspace_size(8192, 3, ctypes.byref(o))
+    assert big >= (2 * 4 * 4 + 2 * 4 * 2 * 2) * 8192 * 8192
+    # null handle / null pointer paths need no device
+    assert lib.dmpt_sp2_response(None, None, None, 1, 4, 4, 2, None, None, None, None, None, 0,
+                                 None) == 1
+    assert lib.dmpt_destroy(None) == 1
