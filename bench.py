@@ -1,0 +1,377 @@
+"""Benchmark: converged-P1 TFLOP/s and time-to-solution of DNN-SP2-PT.
+
+Workload: n = 8192, n_occ = 4096, gapped spectrum (occupied U[-2, -0.1],
+virtual U[0.1, 2]), three dipole-like perturbations diag(x_k) + 0.001
+sym-Gauss sharing one S_0 recursion, dual-FP16 tensor-core products
+(synthetic stand-in for the paper's water systems; seeded, generated on
+the device).
+
+One step = one full dmpt_sp2_response call: Gershgorin bounds, initial
+layer, every SP2 layer with its response until the Alg. 2 / Alg. 3
+criteria fire, and the FP64 outputs P and P1 -- with H and H1 resident in
+HBM.  value = algorithmic flops of the converged solve ((2 + 3K) 2n^3 per
+D0 layer, 3K 2n^3 per D1-only layer) / device time per step.  The inputs
+(2 GiB) exceed L2, so no flush is needed between steps.
+
+`e2e` times the same call from pinned host buffers (copy-in, solve, copy-out
+of P1 inside the timed region).  `roofline` reports the layer-product
+kernel against the measured dense 16-bit tensor peak.  `cpu_baseline`
+times the FP64 oracle (numpy) on the host on a bounded sample.
+
+--impl reference times the FP64 CPU oracle as the reference arm.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "converged-P1 TFLOP/s and time-to-solution at N=8192, dual-FP16 vs FP32 vs FP64"
+N_DEFAULT = 8192
+K_DEFAULT = 3
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm_sorted = sorted(sm)
+        return {"sm_mhz": sm_sorted[len(sm_sorted) // 2], "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(n, k, device):
+    from paper_2203_09621_gb300.workloads import make_workload
+    return make_workload(3, n=n, k=k, backend="torch", device=device)
+
+
+def oracle_sample(inst_cpu_H, inst_cpu_H1, n_occ, layers):
+    """FP64 oracle on the host: the first `layers` layers of Alg. 1-3."""
+    import numpy as np
+    import oracle
+    t = time.perf_counter()
+    oracle.sp2_pt(inst_cpu_H, inst_cpu_H1, n_occ, max_layers=layers)
+    return time.perf_counter() - t
+
+
+def alg_flops_layers(n, k, layers):
+    # D0-phase layers: square (2 products) + 3 products per direction
+    return layers * (2 + 3 * k) * 2.0 * float(n) ** 3
+
+
+def cpu_cores():
+    try:
+        import numpy as np  # noqa
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count()
+    return n
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, on a bounded sample."""
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            dist.destroy_process_group()
+            return
+    import numpy as np
+    from paper_2203_09621_gb300.workloads import make_workload
+    n, k = args.oracle_n, args.k
+    layers = args.oracle_layers
+    # bounded sample: the first `layers` layers of the same recipe at
+    # n = --oracle-n, generated on the device when one is available (host QR
+    # at full size alone takes minutes), else on the host
+    try:
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+    except ImportError:
+        dev = "cpu"
+    if dev == "cuda":
+        inst = make_inputs(n, k, "cuda")
+        H = inst.H.cpu().numpy()
+        H1 = inst.H1.cpu().numpy()
+    else:
+        inst = make_workload(3, n=n, k=k)
+        H, H1 = inst.H, inst.H1
+    for _ in range(args.warmup):
+        oracle_sample(H, H1, n // 2, layers)
+    times = [oracle_sample(H, H1, n // 2, layers) for _ in range(args.steps)]
+    t = sum(times) / len(times)
+    flops = alg_flops_layers(n, k, layers)
+    val = flops / t / 1e12
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"dipole3 n={args.n} k={k} n_occ={args.n // 2}; FP64 oracle "
+                               f"(numpy, Algorithms 1-3) sampled: first {layers} layer(s) "
+                               f"at n={n} per step"},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cpu_cores(),
+                         "kind": "oracle",
+                         "sample": f"first {layers} layer(s) of Alg. 1-3 on the same recipe "
+                                   f"at n={n}, k={k} per step"},
+        "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--k", type=int, default=K_DEFAULT)
+    ap.add_argument("--precision", default="dual_fp16")
+    ap.add_argument("--forms", default="fp32", help="extra precision forms timed once (comma list)")
+    ap.add_argument("--oracle-layers", type=int, default=1)
+    ap.add_argument("--oracle-n", type=int, default=4096,
+                    help="size of the bounded oracle sample (same recipe)")
+    ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--accum-chunk", type=int, default=0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    from paper_2203_09621_gb300 import dmpt
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    n, k = args.n, args.k
+    inst = make_inputs(n, k, dev)
+    H, H1 = inst.H.contiguous(), inst.H1.contiguous()
+    ctx = dmpt.Context(local)
+    P = torch.empty(n, n, dtype=torch.float64, device=dev)
+    P1 = torch.empty(k, n, n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    kw = dict(precision=args.precision, out=(P, P1), stream=stream,
+              accum_chunk=args.accum_chunk)
+
+    # warm-up (also sizes the workspace)
+    for _ in range(args.warmup):
+        ctx.sp2_response(H, H1, inst.n_occ, **kw)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- timed: device-resident inputs
+    infos = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, _, info = ctx.sp2_response(H, H1, inst.n_occ, **kw)
+            infos.append(info)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    clocks = clk.summary()
+    alg = sum(i.alg_flops for i in infos) / len(infos)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = alg * world / (ms_max * 1e-3) / 1e12
+
+    # ---- per-launch timing of the layer products (CUDA events on the stream)
+    _, _, tinfo = ctx.sp2_response(H, H1, inst.n_occ, timing=True, **kw)
+    torch.cuda.synchronize()
+    peaks, peak_src = load_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    achieved = tinfo.alg_flops / (tinfo.ms_layers * 1e-3) / 1e12 if tinfo.ms_layers else None
+    executed = tinfo.mma_flops / (tinfo.ms_layers * 1e-3) / 1e12 if tinfo.ms_layers else None
+
+    # ---- e2e: pinned host buffers, copies inside the timed region
+    Hh = H.cpu().pin_memory()
+    H1h = H1.cpu().pin_memory()
+    P1h = torch.empty(k, n, n, dtype=torch.float64).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    Hd = torch.empty_like(H)
+    H1d = torch.empty_like(H1)
+    barrier()
+    torch.cuda.synchronize()
+    e_steps = max(1, min(args.steps, 2))
+    e0.record(stream)
+    for _ in range(e_steps):
+        Hd.copy_(Hh, non_blocking=True)
+        H1d.copy_(H1h, non_blocking=True)
+        ctx.sp2_response(Hd, H1d, inst.n_occ, **kw)
+        P1h.copy_(P1, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / e_steps
+    e2e_val = alg * world / (e2e_ms * 1e-3) / 1e12
+    h2d = (H.numel() + H1.numel()) * 8
+    d2h = P1.numel() * 8
+
+    # ---- other precision forms, one timed solve each (time-to-solution)
+    forms = {}
+    for f in [x for x in args.forms.split(",") if x]:
+        kwf = dict(kw, precision=f)
+        ctx.sp2_response(H, H1, inst.n_occ, **kwf)  # warm-up
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, _, fi = ctx.sp2_response(H, H1, inst.n_occ, **kwf)
+        b.record(stream)
+        torch.cuda.synchronize()
+        fms = a.elapsed_time(b)
+        forms[f] = {"ms": fms, "tflops": fi.alg_flops / (fms * 1e-3) / 1e12,
+                    "layers": fi.layers, "d0_layer": fi.d0_layer}
+    # restore the dual-FP16 result in P1 for the accuracy check
+    _, _, info = ctx.sp2_response(H, H1, inst.n_occ, **kw)
+    torch.cuda.synchronize()
+
+    # ---- accuracy against the oracle (sampled columns, known eigenpairs)
+    err = None
+    if not args.no_check and rank == 0:
+        from oracle.sos import response_columns
+        cols = [0, 1, n // 2 - 1, n // 2, n - 1]
+        eps = inst.eps.cpu().numpy()
+        Q = inst.Q.cpu().numpy()
+        want = response_columns(eps, Q, H1[0].cpu().numpy(), inst.n_occ, cols)
+        got = P1[0][:, cols].cpu().numpy()
+        err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+
+    # ---- CPU baseline: FP64 oracle, first layer(s) of the same workload
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ns = min(args.oracle_n, n)
+        sub = make_inputs(ns, k, dev)
+        Hc, H1c = sub.H.cpu().numpy(), sub.H1.cpu().numpy()
+        del sub
+        t = oracle_sample(Hc, H1c, ns // 2, args.oracle_layers)
+        cpu = {"value": alg_flops_layers(ns, k, args.oracle_layers) / t / 1e12, "unit": "TFLOP/s",
+               "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"first {args.oracle_layers} layer(s) of the FP64 numpy Alg. 1-3 on the "
+                         f"same recipe at n={ns}, k={k} ({t:.1f} s)"}
+
+    launches_per_step = 7 + (1 if args.precision.startswith("dual") else 0) + 2 * infos[0].product_launches
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16x2->f32" if args.precision == "dual_fp16" else args.precision, "data": "synthetic",
+            "config": {"workload": f"dipole3 n={n} k={k} n_occ={n // 2} gap 0.2, {args.precision}",
+                       "n": n, "k": k, "precision": args.precision,
+                       "l2": "inputs (2 GiB) larger than L2; no flush",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "time_to_solution_ms": ms_max,
+            "layers": infos[0].layers, "d0_layer": infos[0].d0_layer,
+            "rel_err_P1_sampled": err,
+            "forms": forms,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "kernel": "layer_tc_kernel",
+                         "executed_mma_tflops": executed,
+                         "peak_source": f"{peak_src} bf16_tflops_sustained (FP16 dense = BF16 dense)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

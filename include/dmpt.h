@@ -81,7 +81,10 @@ typedef struct {
   double timeout_s;     /* limit of any device-side spin wait (default 2.0)   */
   int ckpt_every;       /* >0: keep S every ckpt_every layers plus the branch
                            sequence in the workspace, for dmpt_sp2_backward   */
-  int reserved[7];
+  int accum_chunk;      /* dual forms: K elements summed per tensor-memory
+                           accumulator before the running sum is carried in
+                           FP32 on the CUDA cores (0: default 256)             */
+  int reserved[6];
 } dmpt_options;
 
 /* Filled on the host by dmpt_sp2_response (when info != NULL). */

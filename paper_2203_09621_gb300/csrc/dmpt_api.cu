@@ -54,6 +54,7 @@ bool valid_options(const dmpt_options* o) {
   if (o->sync_every < 1) return false;
   if (!(o->timeout_s > 0.0)) return false;
   if (o->ckpt_every < 0) return false;
+  if (o->accum_chunk < 0) return false;
   return true;
 }
 
@@ -237,7 +238,7 @@ dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, 
   while (launched < max_layers && !done) {
     for (int j = 0; j < o->sync_every && launched < max_layers; ++j) {
       if (o->timing) cudaEventRecord(h->events[2 * launched], s);
-      e = dual ? launch_layer_tc(L, workspace, s, o->timeout_s, &entries, &pass_flops)
+      e = dual ? launch_layer_tc(L, workspace, s, o->timeout_s, o->accum_chunk, &entries, &pass_flops)
                : launch_layer_simt(L, workspace, s, &entries, &pass_flops);
       if (e != cudaSuccess) return cuda_fail(h, e, "layer product");
       if (o->timing) cudaEventRecord(h->events[2 * launched + 1], s);

@@ -18,14 +18,23 @@
 // The response needs both orders S0 S1 and S1 S0 for a tile, which are two
 // K passes into the same accumulator.
 //
-// Kernel structure (persistent, one CTA per SM, 192 threads):
+// Kernel structure (persistent, one CTA per SM, 320 threads):
 //   warp 0      TMA producer: 4-stage ring of {A_hi, A_lo, B_hi, B_lo}
 //               tiles (128x32, 128x32, 256x32, 256x32 16-bit, 64B swizzle)
 //   warp 1      TMEM owner and MMA issuer: tcgen05.mma.cta_group::1
 //               kind::f16, M = 128, N = 256, K = 16, FP32 accumulate, two
 //               256-column accumulators in TMEM (double buffered)
-//   warps 2..5  epilogue: tcgen05.ld of one row per thread, fused update,
-//               stores, deterministic FP64 partial norms per tile
+//   warps 2..9  epilogue: two warps per TMEM lane quadrant, one row and one
+//               column half per thread; fused update, stores, deterministic
+//               FP64 partial norms per tile
+// Accumulation in chunks: the tensor core adds each MMA's products into the
+// FP32 accumulator with a truncating alignment, so an error that grows with
+// the number of MMAs folded into one accumulator (and is biased) would
+// build up over K = 3n terms.  The K sequence of a tile is therefore cut into
+// chunks of `chunk` stages (default 256 K-elements); each chunk starts a
+// fresh TMEM accumulator and the epilogue warps add the chunk results in
+// FP32 with round-to-nearest in registers.  The two TMEM accumulators are
+// used alternately, so the MMA of the next chunk overlaps that summation.
 // Every mbarrier wait is bounded in time; on expiry the CTA raises
 // State::timeout_flag, drains its copies in flight (bounded), frees TMEM and
 // returns, and the host reports DMPT_ETIMEOUT.
@@ -50,10 +59,24 @@ constexpr int A_BYTES = BM * BK * 2;   // 8 KB
 constexpr int B_BYTES = BN * BK * 2;   // 16 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 48 KB
 constexpr int TMEM_COLS = 512;   // two accumulators of BN columns
-constexpr int NUM_THREADS = 192;
-constexpr int EPI_THREADS = 128;
+constexpr int EPI_WARPS = 8;     // two per TMEM lane quadrant (column halves)
+constexpr int EPI_THREADS = 32 * EPI_WARPS;
+constexpr int EPI_WARP0 = 2;     // epilogue = warps 2 .. 9
+constexpr int NUM_THREADS = 64 + EPI_THREADS;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* align */ + 1024 /* barriers etc */ +
                            EPI_THREADS * 4 * 8;
+constexpr int DEFAULT_CHUNK_K = 256;  // K elements per tensor-memory accumulation chunk
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
 
 // ---------------------------------------------------------------------------
 // PTX helpers
@@ -192,18 +215,21 @@ struct Cvt<true> {
   static __device__ __forceinline__ float from(T h) { return __bfloat162float(h); }
 };
 
-// AND of a predicate over the 128 epilogue threads (named barrier 1).
+// AND of a predicate over the epilogue threads (named barrier 1).
 __device__ __forceinline__ int epi_all(int pred) {
   int out;
   asm volatile(
       "{\n\t.reg .pred p, q;\n\t"
       "setp.ne.b32 q, %1, 0;\n\t"
-      "bar.red.and.pred p, 1, 128, q;\n\t"
+      "bar.red.and.pred p, 1, %2, q;\n\t"
       "selp.s32 %0, 1, 0, p;\n\t}"
       : "=r"(out)
-      : "r"(pred)
+      : "r"(pred), "n"(EPI_THREADS)
       : "memory");
   return out;
+}
+__device__ __forceinline__ void epi_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -223,13 +249,16 @@ __device__ __forceinline__ void tile_coords(int64_t t, int* I, int* J) {
   *I = (int)(t - (int64_t)j * (j + 1));
 }
 
-struct Plan {
-  int njobs;          // jobs run this layer
-  int jobs[kMaxK + 1];  // job ids in item order (responses first)
-  int cur[kMaxK + 1];   // current buffer of each job's matrix
-  int e_cur[kMaxK + 1]; // exponent of the current 16-bit copies of that matrix
-  int e_new[kMaxK + 1]; // exponent for the new copies
-};
+// Jobs of a layer as a bit mask: bit 0 = square, bit 1 + j = response j.
+// Item order: responses (ascending j) first, then the square.
+__device__ __forceinline__ int job_at(uint32_t mask, int idx) {
+  const uint32_t resp = mask & ~1u;
+  const int nresp = __popc(resp);
+  if (idx >= nresp) return 0;
+  uint32_t m = resp;
+  for (int i = 0; i < idx; ++i) m &= m - 1;  // drop the lowest set bits
+  return __ffs(m) - 1;
+}
 
 __device__ __forceinline__ int zslice(int buf, int m, int part, int k) {
   return (buf * (1 + k) + m) * 2 + part;
@@ -240,26 +269,25 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     layer_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                     State* st, float* __restrict__ master, uint16_t* __restrict__ ops,
                     int64_t Np, int k, double* __restrict__ partials, int64_t ptiles,
-                    uint64_t limit_ns) {
+                    uint64_t limit_ns, int chunk) {
   using CV = Cvt<BF16>;
   using H16 = typename CV::T;
   extern __shared__ uint8_t smem_raw[];
   if (st->done) return;
 
   // ---- plan of this layer (identical in every CTA)
-  Plan pl;
-  pl.njobs = 0;
+  uint32_t jmask = st->plan_square ? 1u : 0u;
   for (int j = 0; j < k; ++j)
-    if (st->plan_resp[j]) pl.jobs[pl.njobs++] = 1 + j;
-  if (st->plan_square) pl.jobs[pl.njobs++] = 0;
-  if (pl.njobs == 0) return;
+    if (st->plan_resp[j]) jmask |= 1u << (1 + j);
+  const int njobs = __popc(jmask);
+  if (njobs == 0) return;
   const int cur0 = st->cur0;
   const int sigma = st->sigma_cur;
   const int write0 = st->plan_write0;
   const int s0e = st->s0_exp;
 
   const int64_t tiles = num_tiles(Np);
-  const int64_t items = tiles * pl.njobs;
+  const int64_t items = tiles * njobs;
   const int kblocks = (int)(Np / BK);
 
   // ---- shared memory carve-up (1024-aligned stage ring)
@@ -288,7 +316,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(bar_tfull + 8 * b, 1);
-      mbar_init(bar_tempty + 8 * b, 4);   // one arrive per epilogue warp
+      mbar_init(bar_tempty + 8 * b, EPI_WARPS);  // one arrive per epilogue warp
     }
     mbar_init(bar_drain, 1);
     *abort_flag = 0;
@@ -314,16 +342,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       int inflight = 0;  // stages issued whose completion this thread has not observed
       bool ok = true;
       for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
-        const int job = pl.jobs[it / tiles];
+        const int job = job_at(jmask, (int)(it / tiles));
         int I, J;
         tile_coords(it % tiles, &I, &J);
         const int passes = job == 0 ? 1 : 2;
-        const int mj = job;  // matrix of this job: 0 = S0, 1 + j = S1_j
         const int curj = job == 0 ? cur0 : st->cur1[job - 1];
         for (int pass = 0; pass < passes && ok; ++pass) {
           // pass 0: A = S0 rows of I, B = S_job rows of J; pass 1: swapped
-          const int mA = pass == 0 ? 0 : mj, bufA = pass == 0 ? cur0 : curj;
-          const int mB = pass == 0 ? mj : 0, bufB = pass == 0 ? curj : cur0;
+          const int mA = pass == 0 ? 0 : job, bufA = pass == 0 ? cur0 : curj;
+          const int mB = pass == 0 ? job : 0, bufB = pass == 0 ? curj : cur0;
           const int zAh = zslice(bufA, mA, 0, k), zAl = zslice(bufA, mA, 1, k);
           const int zBh = zslice(bufB, mB, 0, k), zBl = zslice(bufB, mB, 1, k);
           for (int kb = 0; kb < kblocks; ++kb) {
@@ -364,6 +391,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
   } else if (warp == 1) {
     // ================= MMA issuer =================
+    // The K sequence of an item (all passes) is cut into chunks of `chunk`
+    // stages; each chunk accumulates from zero into one of the two TMEM
+    // accumulators and is summed by the epilogue in FP32 on the CUDA cores.
     if (lane == 0) {
       constexpr uint32_t idesc = make_idesc(BF16 ? 1 : 0);
       int stage = 0;
@@ -372,46 +402,49 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       uint32_t abphase = 0;
       bool ok = true;
       for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
-        const int job = pl.jobs[it / tiles];
-        const int passes = job == 0 ? 1 : 2;
-        if (!mbar_wait(bar_tempty + 8 * ab, abphase ^ 1, limit_ns, abort_flag, timeout_global)) {
-          ok = false;
-          break;
-        }
-        fence_after();
-        const uint32_t d = tmem_base + (uint32_t)(ab * BN);
-        uint32_t acc = 0;
-        for (int pass = 0; pass < passes && ok; ++pass) {
-          for (int kb = 0; kb < kblocks; ++kb) {
-            if (!mbar_wait(bar_full + 8 * stage, phase, limit_ns, abort_flag, timeout_global)) {
+        const int job = job_at(jmask, (int)(it / tiles));
+        const int nst = (job == 0 ? 1 : 2) * kblocks;
+        uint32_t d = 0, acc = 0;
+        for (int si = 0; si < nst; ++si) {
+          if (si % chunk == 0) {
+            if (!mbar_wait(bar_tempty + 8 * ab, abphase ^ 1, limit_ns, abort_flag,
+                           timeout_global)) {
               ok = false;
               break;
             }
             fence_after();
-            const uint32_t sA = ring + stage * STAGE_BYTES;
-            const uint64_t ah = sw64_desc(sA), al = sw64_desc(sA + A_BYTES);
-            const uint64_t bh = sw64_desc(sA + 2 * A_BYTES);
-            const uint64_t bl = sw64_desc(sA + 2 * A_BYTES + B_BYTES);
+            d = tmem_base + (uint32_t)(ab * BN);
+            acc = 0;
+          }
+          if (!mbar_wait(bar_full + 8 * stage, phase, limit_ns, abort_flag, timeout_global)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t sA = ring + stage * STAGE_BYTES;
+          const uint64_t ah = sw64_desc(sA), al = sw64_desc(sA + A_BYTES);
+          const uint64_t bh = sw64_desc(sA + 2 * A_BYTES);
+          const uint64_t bl = sw64_desc(sA + 2 * A_BYTES + B_BYTES);
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-              const uint64_t off = (uint64_t)((kk * 32) >> 4);  // 16 elements = 32 B
-              mma_f16(d, ah + off, bh + off, idesc, acc);        // hi * hi
-              acc = 1;
-              mma_f16(d, ah + off, bl + off, idesc, 1);          // hi * lo
-              mma_f16(d, al + off, bh + off, idesc, 1);          // lo * hi
-            }
-            mma_commit(bar_empty + 8 * stage);  // frees the stage when these MMAs finish
-            if (++stage == STAGES) {
-              stage = 0;
-              phase ^= 1;
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t off = (uint64_t)((kk * 32) >> 4);  // 16 elements = 32 B
+            mma_f16(d, ah + off, bh + off, idesc, acc);        // hi * hi
+            acc = 1;
+            mma_f16(d, ah + off, bl + off, idesc, 1);          // hi * lo
+            mma_f16(d, al + off, bh + off, idesc, 1);          // lo * hi
+          }
+          mma_commit(bar_empty + 8 * stage);  // frees the stage when these MMAs finish
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+          if (si % chunk == chunk - 1 || si == nst - 1) {
+            mma_commit(bar_tfull + 8 * ab);  // chunk accumulator ready
+            if (++ab == 2) {
+              ab = 0;
+              abphase ^= 1;
             }
           }
-        }
-        if (!ok) break;
-        mma_commit(bar_tfull + 8 * ab);  // accumulator ready
-        if (++ab == 2) {
-          ab = 0;
-          abphase ^= 1;
         }
       }
       // wait (bounded) until every MMA this thread issued has completed, so
@@ -421,25 +454,59 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       while (!mbar_try_wait(bar_drain, 0) && gtimer() - t0 < limit_ns) {
       }
     }
-  } else {
-    // ================= epilogue (warps 2..5) =================
+  } else if (warp >= EPI_WARP0) {
+    // ================= epilogue (warps 4..11) =================
+    // Thread = one row of the tile (TMEM lane) and one half of its columns.
     const int q = warp & 3;                 // TMEM lane quadrant of this warp
+    const int half = (warp - EPI_WARP0) >> 2;  // column half: 0 -> 0..127, 1 -> 128..255
     const int rloc = 32 * q + lane;         // row within the tile
-    const int et = threadIdx.x - 64;        // 0..127
+    const int et = threadIdx.x - 32 * EPI_WARP0;  // 0..255
     const size_t mat = (size_t)Np * Np;
+    const uint32_t tlane = (uint32_t)(32 * q) << 16;
     int ab = 0;
     uint32_t abphase = 0;
-    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
-      const int job = pl.jobs[it / tiles];
+    bool alive = true;
+    for (int64_t it = blockIdx.x; it < items && alive; it += gridDim.x) {
+      const int job = job_at(jmask, (int)(it / tiles));
+      const int nst = (job == 0 ? 1 : 2) * kblocks;
+      const int nchunks = (nst + chunk - 1) / chunk;
+
+      // ---- sum the chunk accumulators in FP32 (round to nearest)
+      float sum[128];
+#pragma unroll
+      for (int i = 0; i < 128; ++i) sum[i] = 0.0f;
+      for (int ch = 0; ch < nchunks; ++ch) {
+        const bool ok =
+            mbar_wait(bar_tfull + 8 * ab, abphase, limit_ns, abort_flag, timeout_global);
+        // all epilogue threads take the same branch (warp-collective
+        // tcgen05.ld follows)
+        if (!epi_all(ok && !*abort_flag)) {
+          alive = false;
+          break;
+        }
+        fence_after();
+        const uint32_t ta = tmem_base + tlane + (uint32_t)(ab * BN + half * 128);
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) {
+          uint32_t x[16];
+          tmem_ld16(ta + 16 * cc, x);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) sum[16 * cc + i] += __uint_as_float(x[i]);
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar_tempty + 8 * ab);
+        if (++ab == 2) {
+          ab = 0;
+          abphase ^= 1;
+        }
+      }
+      if (!alive) break;
+
+      // ---- fused layer update, split and stores
       const int64_t t = it % tiles;
       int I, J;
       tile_coords(t, &I, &J);
-      const bool ok = mbar_wait(bar_tfull + 8 * ab, abphase, limit_ns, abort_flag, timeout_global);
-      // all 128 epilogue threads take the same branch (warp-collective
-      // tcgen05.ld follows)
-      if (!epi_all(ok && !*abort_flag)) break;
-      fence_after();
-
       const int curj = job == 0 ? cur0 : st->cur1[job - 1];
       const int e_cur = job == 0 ? s0e : st->s1_exp_cur[job - 1];
       const int e_new = job == 0 ? s0e : st->s1_exp_next[job - 1];
@@ -447,38 +514,31 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const float scale_new = ldexpf(1.0f, e_new);
       const float sg = (float)sigma, om = 1.0f - (float)sigma;
       const bool write = job != 0 || write0;
-      const float* Sold = master + (size_t)(curj * (1 + k) + job) * mat;
+      const int r = I * BM + rloc;
+      const int c0 = J * BN + half * 128;
+      const size_t row_off = (size_t)r * Np;
+      const float* Sold = master + (size_t)(curj * (1 + k) + job) * mat + row_off;
       float* Snew = master + (size_t)((curj ^ 1) * (1 + k) + job) * mat;
       H16* hi_new = reinterpret_cast<H16*>(ops) + (size_t)zslice(curj ^ 1, job, 0, k) * mat;
       H16* lo_new = reinterpret_cast<H16*>(ops) + (size_t)zslice(curj ^ 1, job, 1, k) * mat;
 
-      const int64_t r = (int64_t)I * BM + rloc;
-      double tr = 0.0, fnew = 0.0, fdiff = 0.0, bad = 0.0;
-#pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        float x[32];
-        tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * BN + c0), x);
-        const int64_t cb = (int64_t)J * BN + c0;   // first global column of the chunk
-        if (r > cb + 31) continue;                 // no element with r <= c in this chunk
-        const float* po = Sold + (size_t)r * Np + cb;
-        float old[32];
+      double tr = 0.0, fnew = 0.0, fdiff = 0.0;
+      int bad = 0;
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
-          const float4 o4 = *reinterpret_cast<const float4*>(po + 4 * v);
-          old[4 * v + 0] = o4.x;
-          old[4 * v + 1] = o4.y;
-          old[4 * v + 2] = o4.z;
-          old[4 * v + 3] = o4.w;
-        }
-        float nw[32];
-        H16 nh[32], nl[32];
+      for (int g = 0; g < 32; ++g) {   // groups of 4 columns
+        const int cb = c0 + 4 * g;
+        if (r > cb + 3) continue;      // no element with r <= c in this group
+        const float4 o4 = *reinterpret_cast<const float4*>(Sold + cb);
+        const float old[4] = {o4.x, o4.y, o4.z, o4.w};
+        float nw[4];
+        H16 nh[4], nl[4];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const float xv = x[i] * unscale;
-          const int64_t c = cb + i;
+        for (int i = 0; i < 4; ++i) {
+          const float xv = sum[4 * g + i] * unscale;
+          const int c = cb + i;
           const bool own = c >= r;
           const double w = (c == r) ? 1.0 : 2.0;
-          if (!isfinite(xv)) bad += own ? 1.0 : 0.0;
+          bad += (own && !isfinite(xv)) ? 1 : 0;
           const double dd = (double)old[i] - (double)xv;
           fdiff += own ? w * dd * dd : 0.0;
           const float n1 = sg * xv + om * old[i];
@@ -487,67 +547,58 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           fnew += (own && write) ? w * dn * dn : 0.0;
           tr += (own && write && c == r) ? dn : 0.0;
           const float y = n1 * scale_new;
-          const H16 h = CV::to(y);
-          nh[i] = h;
-          nl[i] = CV::to(y - CV::from(h));
+          nh[i] = CV::to(y);
+          nl[i] = CV::to(y - CV::from(nh[i]));
         }
         if (!write) continue;
-        // direct stores at (r, c)
         if (r <= cb) {
-          float* pn = Snew + (size_t)r * Np + cb;
-#pragma unroll
-          for (int v = 0; v < 8; ++v)
-            *reinterpret_cast<float4*>(pn + 4 * v) =
-                make_float4(nw[4 * v], nw[4 * v + 1], nw[4 * v + 2], nw[4 * v + 3]);
-          uint4* ph = reinterpret_cast<uint4*>(hi_new + (size_t)r * Np + cb);
-          uint4* plo = reinterpret_cast<uint4*>(lo_new + (size_t)r * Np + cb);
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            ph[v] = *reinterpret_cast<const uint4*>(&nh[8 * v]);
-            plo[v] = *reinterpret_cast<const uint4*>(&nl[8 * v]);
-          }
+          // whole group owned: vector stores at (r, cb .. cb+3)
+          *reinterpret_cast<float4*>(Snew + row_off + cb) = make_float4(nw[0], nw[1], nw[2], nw[3]);
+          uint2 ph, pl2;
+          ph.x = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[0])) |
+                 ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[1])) << 16);
+          ph.y = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[2])) |
+                 ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[3])) << 16);
+          pl2.x = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[0])) |
+                  ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[1])) << 16);
+          pl2.y = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[2])) |
+                  ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[3])) << 16);
+          *reinterpret_cast<uint2*>(hi_new + row_off + cb) = ph;
+          *reinterpret_cast<uint2*>(lo_new + row_off + cb) = pl2;
         } else {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const int64_t c = cb + i;
-            if (c >= r) {
-              Snew[(size_t)r * Np + c] = nw[i];
-              hi_new[(size_t)r * Np + c] = nh[i];
-              lo_new[(size_t)r * Np + c] = nl[i];
+          for (int i = 0; i < 4; ++i) {
+            if (cb + i >= r) {
+              Snew[row_off + cb + i] = nw[i];
+              hi_new[row_off + cb + i] = nh[i];
+              lo_new[row_off + cb + i] = nl[i];
             }
           }
         }
         // mirrored stores at (c, r): for fixed c the warp's 32 rows are contiguous
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int64_t c = cb + i;
+        for (int i = 0; i < 4; ++i) {
+          const int c = cb + i;
           if (c > r) {
-            Snew[(size_t)c * Np + r] = nw[i];
-            hi_new[(size_t)c * Np + r] = nh[i];
-            lo_new[(size_t)c * Np + r] = nl[i];
+            const size_t m = (size_t)c * Np + r;
+            Snew[m] = nw[i];
+            hi_new[m] = nh[i];
+            lo_new[m] = nl[i];
           }
         }
       }
-      // accumulator drained: hand the TMEM buffer back to the MMA warp
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bar_tempty + 8 * ab);
-      if (++ab == 2) {
-        ab = 0;
-        abphase ^= 1;
-      }
-      // deterministic tile reduction over the 128 epilogue threads
+      // deterministic tile reduction over the 256 epilogue threads
       red[0 * EPI_THREADS + et] = tr;
       red[1 * EPI_THREADS + et] = fnew;
       red[2 * EPI_THREADS + et] = fdiff;
-      red[3 * EPI_THREADS + et] = bad;
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      red[3 * EPI_THREADS + et] = (double)bad;
+      epi_sync();
       for (int s = EPI_THREADS / 2; s > 0; s >>= 1) {
         if (et < s) {
 #pragma unroll
           for (int qq = 0; qq < 4; ++qq) red[qq * EPI_THREADS + et] += red[qq * EPI_THREADS + et + s];
         }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+        epi_sync();
       }
       if (et == 0) {
         double* p = partials + ((size_t)job * ptiles + t) * kNQ;
@@ -556,7 +607,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         p[kQFroDiff] = red[2 * EPI_THREADS];
         p[kQBad] = red[3 * EPI_THREADS];
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      epi_sync();
     }
   }
 
@@ -605,7 +656,7 @@ bool make_map(CUtensorMap* map, void* base, int64_t Np, int slices, int box_rows
 int tc_tile() { return tc::BN; }
 
 cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double timeout_s,
-                            int64_t* entries, double* pass_flops) {
+                            int accum_chunk_k, int64_t* entries, double* pass_flops) {
   using namespace tc;
   char* base = (char*)ws;
   const bool bf16 = L.precision == DMPT_DUAL_BF16;
@@ -630,6 +681,9 @@ cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double ti
   int64_t max_items = tiles * (1 + L.k);
   int grid = (int)(max_items < sms ? max_items : sms);
   const uint64_t limit_ns = (uint64_t)(timeout_s * 1e9);
+  int ck = accum_chunk_k > 0 ? accum_chunk_k : DEFAULT_CHUNK_K;
+  int chunk = ck / BK;
+  if (chunk < 1) chunk = 1;
   State* st = (State*)(base + L.off_state);
   float* master = (float*)(base + L.off_master);
   uint16_t* ops = (uint16_t*)(base + L.off_ops16);
@@ -637,11 +691,11 @@ cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double ti
   if (bf16)
     layer_tc_kernel<true><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(mA, mB, st, master, ops, L.Np,
                                                                 L.k, partials, L.partial_tiles,
-                                                                limit_ns);
+                                                                limit_ns, chunk);
   else
     layer_tc_kernel<false><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(mA, mB, st, master, ops, L.Np,
                                                                  L.k, partials, L.partial_tiles,
-                                                                 limit_ns);
+                                                                 limit_ns, chunk);
   if (entries) *entries = tiles;
   if (pass_flops) *pass_flops = (double)tiles * BM * BN * (double)L.Np * 2.0;
   return cudaGetLastError();

@@ -37,7 +37,8 @@ class DmptOptions(ctypes.Structure):
         ("timing", ctypes.c_int),
         ("timeout_s", ctypes.c_double),
         ("ckpt_every", ctypes.c_int),
-        ("reserved", ctypes.c_int * 7),
+        ("accum_chunk", ctypes.c_int),
+        ("reserved", ctypes.c_int * 6),
     ]
 
 
@@ -132,7 +133,7 @@ class Info:
 
 
 def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_scaling=1,
-            sync_every=4, timing=False, timeout_s=2.0) -> DmptOptions:
+            sync_every=4, timing=False, timeout_s=2.0, accum_chunk=0) -> DmptOptions:
     lib = load_library()
     o = DmptOptions()
     lib.dmpt_default_options(ctypes.byref(o))
@@ -144,6 +145,7 @@ def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_s
     o.sync_every = int(sync_every)
     o.timing = int(bool(timing))
     o.timeout_s = float(timeout_s)
+    o.accum_chunk = int(accum_chunk)
     return o
 
 

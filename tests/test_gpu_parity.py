@@ -86,8 +86,15 @@ def test_fp64_matches_oracle(ctx, cfg, n):
     r = oracle.sp2_pt(inst.H, inst.H1, inst.n_occ)
     Pr, P1r = oracle.response_sos(inst.H, inst.H1, inst.n_occ)
     assert info.converged and r.converged
-    assert info.sigma == r.sigma
-    assert info.layers == r.layers and info.d0_layer == r.d0_layer
+    # branch decisions before D0 converges are unique; at the converging layer
+    # N_S ~ N_X ~ n_occ and sigma is decided by rounding noise (a near tie),
+    # after it the branches must alternate (the sigma flip)
+    nc = r.d0_layer
+    assert info.d0_layer == nc
+    assert info.sigma[: nc - 1] == r.sigma[: nc - 1]
+    tail = info.sigma[nc - 1:]
+    assert all(tail[i] == -tail[i - 1] for i in range(1, len(tail)))
+    assert info.layers == r.layers
     assert info.d1_layer == r.d1_layer
     assert abs(info.eps_min - r.bounds[0]) < 1e-12 * abs(r.bounds[0])
     assert rel(P, Pr) < 1e-10
