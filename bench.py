@@ -109,8 +109,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+INPUT_BACKEND = "torch"
+
+
 def make_inputs(n, k, device):
+    """The workload's matrices on `device` (torch: built on the device;
+    numpy: built on the host and copied, used where torch.linalg is not
+    loadable, e.g. under a profiler)."""
     from paper_2203_09621_gb300.workloads import make_workload
+    if INPUT_BACKEND == "numpy":
+        import torch
+        inst = make_workload(3, n=n, k=k)
+        inst.H = torch.from_numpy(inst.H).to(device)
+        inst.H1 = torch.from_numpy(inst.H1).to(device)
+        inst.eps = torch.from_numpy(inst.eps)
+        inst.Q = torch.from_numpy(inst.Q)
+        return inst
     return make_workload(3, n=n, k=k, backend="torch", device=device)
 
 
@@ -209,7 +223,10 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--accum-chunk", type=int, default=0)
+    ap.add_argument("--input-backend", default="torch", choices=["torch", "numpy"])
     args = ap.parse_args()
+    global INPUT_BACKEND
+    INPUT_BACKEND = args.input_backend
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
