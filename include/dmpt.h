@@ -156,6 +156,30 @@ dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1,
                               dmpt_info* info, void* workspace, size_t ws_bytes,
                               void* stream);
 
+/* Static-scratch variant of dmpt_sp2_response for callers that cannot
+ * allocate device memory (a host framework that owns every allocation, code
+ * that must not allocate after start-up, plug-ins that only get input and
+ * output pointers).  The paper has no counterpart; this is a library
+ * convenience.
+ *   Same arguments and results as dmpt_sp2_response, without the workspace:
+ *   scratch comes from one fixed device array of DMPT_STATIC_SCRATCH_BYTES
+ *   inside the library, resident on every GPU that loads it until exit.
+ *   Limits: n <= DMPT_STATIC_MAX_N, k <= DMPT_STATIC_MAX_K; larger sizes
+ *   return DMPT_EINVAL with a message on stderr.  o->timing = 1 returns
+ *   DMPT_EUNSUPPORTED (timing creates CUDA events).
+ *   The first call on a device looks up the array's device address (with
+ *   that device current); make that first call before any stream capture.
+ *   All calls share the array and it keeps the last call's contents; calls
+ *   that overlap on the GPU race on it and must be serialised by the caller.
+ *   Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
+#define DMPT_STATIC_MAX_N 512
+#define DMPT_STATIC_MAX_K 1
+#define DMPT_STATIC_SCRATCH_BYTES (8912896) /* 8.5 MiB */
+dmpt_status dmpt_sp2_response_static(dmpt_handle h, const double* H, const double* H1,
+                                     int k, int64_t n, int64_t ld, int64_t n_occ,
+                                     const dmpt_options* o, double* P, double* P1,
+                                     dmpt_info* info, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,6 +1,6 @@
 """Build libdmpt.so in-tree with nvcc for sm_103a (GB300).
 
-Three translation units are compiled in parallel and linked into one
+Four translation units are compiled in parallel and linked into one
 shared library with the static CUDA runtime, so the library loads without
 a GPU and without libcudart on the library path.  The driver API entry
 point it needs (cuTensorMapEncodeTiled) is looked up at run time.
@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdmpt.so")
 
-SOURCES = ["dmpt_api.cu", "kernels_simt.cu", "kernels_tc.cu"]
+SOURCES = ["dmpt_api.cu", "kernels_simt.cu", "kernels_tc.cu", "dmpt_static.cu"]
 HEADERS = [os.path.join(CSRC, "dmpt_internal.cuh"), os.path.join(INCLUDE, "dmpt.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE,

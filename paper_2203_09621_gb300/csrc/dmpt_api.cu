@@ -89,6 +89,10 @@ double layer_mma_flops(const Layout& L, double per /* one full-K single-term pas
 
 }  // namespace
 
+namespace dmpt {
+int handle_device(dmpt_handle h) { return h ? h->device : -1; }
+}  // namespace dmpt
+
 extern "C" {
 
 void dmpt_default_options(dmpt_options* o) {

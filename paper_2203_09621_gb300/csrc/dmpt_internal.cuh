@@ -106,6 +106,9 @@ int tc_tile();
 
 enum DecideMode { kDecideInit = 0, kDecideLayer = 1 };
 
+// CUDA device of a handle (-1 for NULL).
+int handle_device(dmpt_handle h);
+
 // State-dependent exponent for the 16-bit copies of S1: chosen so that a
 // bound of the largest element maps to <= 2^14 (FP16 max is 65504).
 constexpr int kFp16TargetExp = 14;

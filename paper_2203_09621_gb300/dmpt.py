@@ -93,6 +93,10 @@ def load_library(path: str = LIB_PATH):
                                       ctypes.POINTER(DmptOptions), vp, vp,
                                       ctypes.POINTER(DmptInfo), vp, ctypes.c_size_t, vp]
     lib.dmpt_sp2_response.restype = c_int
+    lib.dmpt_sp2_response_static.argtypes = [vp, vp, vp, c_int, i64, i64, i64,
+                                             ctypes.POINTER(DmptOptions), vp, vp,
+                                             ctypes.POINTER(DmptInfo), vp]
+    lib.dmpt_sp2_response_static.restype = c_int
     _lib = lib
     return lib
 
