@@ -522,7 +522,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       H16* hi_new = reinterpret_cast<H16*>(ops) + (size_t)zslice(curj ^ 1, job, 0, k) * mat;
       H16* lo_new = reinterpret_cast<H16*>(ops) + (size_t)zslice(curj ^ 1, job, 1, k) * mat;
 
-      double tr = 0.0, fnew = 0.0, fdiff = 0.0;
+      // Partial norms in FP32 with compensation (GB300's FP64 rate is a small
+      // fraction of its FP32 rate): ||S_new||^2 feeds the Alg. 2 test, so its
+      // products are split exactly (FMA) and summed with TwoSum; the
+      // FroErr sums only enter ratio tests and use plain FP32.
+      float fn_s = 0.0f, fn_c = 0.0f, fd = 0.0f, trf = 0.0f;
       int bad = 0;
 #pragma unroll
       for (int g = 0; g < 32; ++g) {   // groups of 4 columns
@@ -537,15 +541,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const float xv = sum[4 * g + i] * unscale;
           const int c = cb + i;
           const bool own = c >= r;
-          const double w = (c == r) ? 1.0 : 2.0;
+          const float w = (c == r) ? 1.0f : 2.0f;
           bad += (own && !isfinite(xv)) ? 1 : 0;
-          const double dd = (double)old[i] - (double)xv;
-          fdiff += own ? w * dd * dd : 0.0;
+          const float dd = old[i] - xv;
+          fd = own ? fmaf(w * dd, dd, fd) : fd;
           const float n1 = sg * xv + om * old[i];
           nw[i] = n1;
-          const double dn = (double)n1;
-          fnew += (own && write) ? w * dn * dn : 0.0;
-          tr += (own && write && c == r) ? dn : 0.0;
+          if (own && write) {
+            const float p = w * n1 * n1;                // w in {1, 2}: exact scaling
+            const float e = w * fmaf(n1, n1, -n1 * n1);  // exact product error
+            const float t = fn_s + p;                    // TwoSum(fn_s, p)
+            const float bp = t - fn_s;
+            fn_c += (fn_s - (t - bp)) + (p - bp) + e;
+            fn_s = t;
+            if (c == r) trf += n1;                       // at most one per thread
+          }
           const float y = n1 * scale_new;
           nh[i] = CV::to(y);
           nl[i] = CV::to(y - CV::from(nh[i]));
@@ -587,10 +597,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           }
         }
       }
-      // deterministic tile reduction over the 256 epilogue threads
-      red[0 * EPI_THREADS + et] = tr;
-      red[1 * EPI_THREADS + et] = fnew;
-      red[2 * EPI_THREADS + et] = fdiff;
+      // deterministic tile reduction over the 256 epilogue threads (FP64)
+      red[0 * EPI_THREADS + et] = (double)trf;
+      red[1 * EPI_THREADS + et] = (double)fn_s + (double)fn_c;
+      red[2 * EPI_THREADS + et] = (double)fd;
       red[3 * EPI_THREADS + et] = (double)bad;
       epi_sync();
       for (int s = EPI_THREADS / 2; s > 0; s >>= 1) {
