@@ -142,6 +142,27 @@ def alg_flops_layers(n, k, layers):
     return layers * (2 + 3 * k) * 2.0 * float(n) ** 3
 
 
+def aggregate(ms_local, units_local, world):
+    """Whole-job rate over replicas: max step time over ranks, units summed.
+
+    Each rank solves its own replica of the workload (the path shards only
+    as independent problems), so the job processes world * units per step in
+    the time of the slowest rank.  Returns (ms_max, value in units / s).
+    """
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64)
+    u = torch.tensor([float(units_local)], dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+        dev = torch.device("cuda", torch.cuda.current_device()) \
+            if dist.get_backend() == "nccl" else torch.device("cpu")
+        t, u = t.to(dev), u.to(dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    return ms_max, float(u.item()) / (ms_max * 1e-3)
+
+
 def cpu_cores():
     try:
         import numpy as np  # noqa
@@ -278,11 +299,8 @@ def main():
     ms = ev0.elapsed_time(ev1) / args.steps
     clocks = clk.summary()
     alg = sum(i.alg_flops for i in infos) / len(infos)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = alg * world / (ms_max * 1e-3) / 1e12
+    ms_max, rate = aggregate(ms, alg, world)
+    value = rate / 1e12
 
     # ---- per-launch timing of the layer products (CUDA events on the stream)
     _, _, tinfo = ctx.sp2_response(H, H1, inst.n_occ, timing=True, **kw)
@@ -311,8 +329,8 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    e2e_ms = e0.elapsed_time(e1) / e_steps
-    e2e_val = alg * world / (e2e_ms * 1e-3) / 1e12
+    e2e_ms, e2e_rate = aggregate(e0.elapsed_time(e1) / e_steps, alg, world)
+    e2e_val = e2e_rate / 1e12
     h2d = (H.numel() + H1.numel()) * 8
     d2h = P1.numel() * 8
 
