@@ -245,6 +245,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--accum-chunk", type=int, default=0)
     ap.add_argument("--input-backend", default="torch", choices=["torch", "numpy"])
+    ap.add_argument("--cta-pair", type=int, default=1, choices=[0, 1])
     args = ap.parse_args()
     global INPUT_BACKEND
     INPUT_BACKEND = args.input_backend
@@ -272,7 +273,7 @@ def main():
     P1 = torch.empty(k, n, n, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     kw = dict(precision=args.precision, out=(P, P1), stream=stream,
-              accum_chunk=args.accum_chunk)
+              accum_chunk=args.accum_chunk, cta_pair=args.cta_pair)
 
     # warm-up (also sizes the workspace)
     for _ in range(args.warmup):
@@ -384,7 +385,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f16x2->f32" if args.precision == "dual_fp16" else args.precision, "data": "synthetic",
             "config": {"workload": f"dipole3 n={n} k={k} n_occ={n // 2} gap 0.2, {args.precision}",
-                       "n": n, "k": k, "precision": args.precision,
+                       "n": n, "k": k, "precision": args.precision, "cta_pair": args.cta_pair,
                        "l2": "inputs (2 GiB) larger than L2; no flush",
                        "parallelism": "replicas" if world > 1 else "single"},
             "time_to_solution_ms": ms_max,
@@ -393,7 +394,7 @@ def main():
             "forms": forms,
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": None,
-                         "kernel": "layer_tc_kernel",
+                         "kernel": "layer_tc2_kernel" if args.cta_pair else "layer_tc_kernel",
                          "executed_mma_tflops": executed,
                          "peak_source": f"{peak_src} bf16_tflops_sustained (FP16 dense = BF16 dense)"},
             "cpu_baseline": cpu,

@@ -84,7 +84,10 @@ typedef struct {
   int accum_chunk;      /* dual forms: K elements summed per tensor-memory
                            accumulator before the running sum is carried in
                            FP32 on the CUDA cores (0: default 256)             */
-  int reserved[6];
+  int cta_pair;         /* dual forms: 1 = products on CTA pairs (cta_group::2,
+                           256 x 256 tiles, default), 0 = one CTA per
+                           128 x 256 tile                                      */
+  int reserved[5];
 } dmpt_options;
 
 /* Filled on the host by dmpt_sp2_response (when info != NULL). */

@@ -55,6 +55,7 @@ bool valid_options(const dmpt_options* o) {
   if (!(o->timeout_s > 0.0)) return false;
   if (o->ckpt_every < 0) return false;
   if (o->accum_chunk < 0) return false;
+  if (o->cta_pair < 0 || o->cta_pair > 1) return false;
   return true;
 }
 
@@ -107,6 +108,8 @@ void dmpt_default_options(dmpt_options* o) {
   o->timing = 0;
   o->timeout_s = 2.0;
   o->ckpt_every = 0;
+  o->accum_chunk = 0;
+  o->cta_pair = 1;
 }
 
 const char* dmpt_status_string(dmpt_status s) {
@@ -242,7 +245,8 @@ dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, 
   while (launched < max_layers && !done) {
     for (int j = 0; j < o->sync_every && launched < max_layers; ++j) {
       if (o->timing) cudaEventRecord(h->events[2 * launched], s);
-      e = dual ? launch_layer_tc(L, workspace, s, o->timeout_s, o->accum_chunk, &entries, &pass_flops)
+      e = dual ? launch_layer_tc(L, workspace, s, o->timeout_s, o->accum_chunk, o->cta_pair,
+                                 &entries, &pass_flops)
                : launch_layer_simt(L, workspace, s, &entries, &pass_flops);
       if (e != cudaSuccess) return cuda_fail(h, e, "layer product");
       if (o->timing) cudaEventRecord(h->events[2 * launched + 1], s);

@@ -632,6 +632,436 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
+// CTA-pair variant (cta_group::2).  A cluster of two CTAs computes a
+// 256 x 256 tile: CTA r holds rows 128 r .. 128 r + 127 of A and B rows
+// (output columns) 128 r .. 128 r + 127; the leader (rank 0) issues
+// M = 256, N = 256 MMAs that read A from each CTA's own shared memory and B
+// from both, and each CTA's tensor memory receives its 128 rows of the
+// accumulator.  Per SM this halves the operand bytes loaded per MMA
+// (32 KB per 6 MMAs instead of 48 KB).
+//   full[s]   leader only: leader producer's expect_tx(64 KB); both CTAs'
+//             TMA loads complete their bytes on it
+//   empty[s]  each CTA: the leader's MMA commit arrives on both (multicast)
+//   tfull[b]  each CTA: leader's commit, multicast
+//   tempty[b] leader only: 16 arrivals (8 epilogue warps per CTA)
+
+constexpr int P_STAGES = 6;
+constexpr int P_STAGE_BYTES = 2 * A_BYTES + 2 * A_BYTES;   // A hi/lo + B-half hi/lo: 32 KB
+constexpr int P_SMEM_BYTES = P_STAGES * P_STAGE_BYTES + 1024 + 1024 + EPI_THREADS * 4 * 8;
+
+__host__ __device__ inline int64_t num_pair_tiles(int64_t Np) {
+  const int64_t tj = Np / BN;
+  return tj * (tj + 1) / 2;
+}
+// pair tile t -> (I2, J), I2 <= J, J-major
+__device__ __forceinline__ void pair_tile_coords(int64_t t, int* I2, int* J) {
+  int j = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while ((int64_t)(j + 1) * (j + 2) / 2 <= t) ++j;
+  while ((int64_t)j * (j + 1) / 2 > t) --j;
+  *J = j;
+  *I2 = (int)(t - (int64_t)j * (j + 1) / 2);
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t addr, uint32_t rank) {
+  uint32_t out;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(addr), "r"(rank));
+  return out;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                                 int z, uint32_t leader_bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(leader_bar)
+      : "memory");
+}
+__device__ __forceinline__ void mma_f16_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                             uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
+  const uint16_t mask = 0x3;
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(bar), "h"(mask)
+      : "memory");
+}
+__host__ __device__ constexpr uint32_t make_idesc_m256(int ab_type) {
+  return (1u << 4) | ((uint32_t)ab_type << 7) | ((uint32_t)ab_type << 10) |
+         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
+}
+
+template <bool BF16>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
+    layer_tc2_kernel(const __grid_constant__ CUtensorMap mapA, State* st, float* __restrict__ master,
+                     uint16_t* __restrict__ ops, int64_t Np, int k, double* __restrict__ partials,
+                     int64_t ptiles, uint64_t limit_ns, int chunk) {
+  using CV = Cvt<BF16>;
+  using H16 = typename CV::T;
+  extern __shared__ uint8_t smem_raw[];
+  // every CTA takes the same early exits (state is read before any cluster
+  // barrier, and both CTAs of a pair see the same values)
+  if (st->done) return;
+  uint32_t jmask = st->plan_square ? 1u : 0u;
+  for (int j = 0; j < k; ++j)
+    if (st->plan_resp[j]) jmask |= 1u << (1 + j);
+  const int njobs = __popc(jmask);
+  if (njobs == 0) return;
+  const int cur0 = st->cur0;
+  const int sigma = st->sigma_cur;
+  const int write0 = st->plan_write0;
+  const int s0e = st->s0_exp;
+
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const int64_t pair = blockIdx.x >> 1;
+  const int64_t npairs = gridDim.x >> 1;
+  const int64_t tiles = num_pair_tiles(Np);
+  const int64_t items = tiles * njobs;
+  const int kblocks = (int)(Np / BK);
+
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw);
+  const uint32_t ring = base;
+  uint8_t* misc = gbase + P_STAGES * P_STAGE_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(misc);
+  const uint32_t bar_full = smem_u32(bars);
+  const uint32_t bar_empty = bar_full + 8 * P_STAGES;
+  const uint32_t bar_tfull = bar_empty + 8 * P_STAGES;
+  const uint32_t bar_tempty = bar_tfull + 8 * 2;
+  const uint32_t bar_drain = bar_tempty + 8 * 2;
+  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(misc + 256);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(misc + 264);
+  double* red = reinterpret_cast<double*>(misc + 1024);
+  const uint32_t lead_full = map_to_rank(bar_full, 0);
+  const uint32_t lead_tempty = map_to_rank(bar_tempty, 0);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P_STAGES; ++s) {
+      mbar_init(bar_full + 8 * s, 1);
+      mbar_init(bar_empty + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bar_tfull + 8 * b, 1);
+      mbar_init(bar_tempty + 8 * b, 2 * EPI_WARPS);
+    }
+    mbar_init(bar_drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32((const void*)tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+  }
+  fence_before();
+  cluster_sync_all();   // barriers of both CTAs initialised, TMEM allocated
+  fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  int* timeout_global = &st->timeout_flag;
+
+  if (warp == 0) {
+    // ================= TMA producer (both CTAs load their own halves) ======
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int64_t it = pair; it < items && ok; it += npairs) {
+        const int job = job_at(jmask, (int)(it / tiles));
+        int I2, J;
+        pair_tile_coords(it % tiles, &I2, &J);
+        const int passes = job == 0 ? 1 : 2;
+        const int curj = job == 0 ? cur0 : st->cur1[job - 1];
+        const int rowA = I2 * 2 * BM + (int)rank * BM;
+        const int rowB = J * BN + (int)rank * BM;
+        for (int pass = 0; pass < passes && ok; ++pass) {
+          const int mA = pass == 0 ? 0 : job, bufA = pass == 0 ? cur0 : curj;
+          const int mB = pass == 0 ? job : 0, bufB = pass == 0 ? curj : cur0;
+          const int zAh = zslice(bufA, mA, 0, k), zAl = zslice(bufA, mA, 1, k);
+          const int zBh = zslice(bufB, mB, 0, k), zBl = zslice(bufB, mB, 1, k);
+          for (int kb = 0; kb < kblocks; ++kb) {
+            if (!mbar_wait(bar_empty + 8 * stage, phase ^ 1, limit_ns, abort_flag,
+                           timeout_global)) {
+              ok = false;
+              break;
+            }
+            const uint32_t sA = ring + stage * P_STAGE_BYTES;
+            if (leader) mbar_expect_tx(bar_full + 8 * stage, 2 * P_STAGE_BYTES);
+            const uint32_t fb = lead_full + 8 * stage;
+            tma_load_3d_pair(sA, &mapA, kb * BK, rowA, zAh, fb);
+            tma_load_3d_pair(sA + A_BYTES, &mapA, kb * BK, rowA, zAl, fb);
+            tma_load_3d_pair(sA + 2 * A_BYTES, &mapA, kb * BK, rowB, zBh, fb);
+            tma_load_3d_pair(sA + 3 * A_BYTES, &mapA, kb * BK, rowB, zBl, fb);
+            if (++stage == P_STAGES) {
+              stage = 0;
+              phase ^= 1;
+            }
+          }
+        }
+      }
+      // wait (bounded) for this CTA's copies to land before the CTA may exit:
+      // the last P_STAGES stages were released by MMA commits or are pending
+      for (int i = 0; i < P_STAGES; ++i) {
+        const uint64_t t0 = gtimer();
+        while (!mbar_try_wait(bar_empty + 8 * stage, phase ^ 1) && gtimer() - t0 < limit_ns) {
+        }
+        if (++stage == P_STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ================= MMA issuer (leader CTA only) =================
+    if (leader && lane == 0) {
+      constexpr uint32_t idesc = make_idesc_m256(BF16 ? 1 : 0);
+      int stage = 0;
+      uint32_t phase = 0;
+      int ab = 0;
+      uint32_t abphase = 0;
+      bool ok = true;
+      for (int64_t it = pair; it < items && ok; it += npairs) {
+        const int job = job_at(jmask, (int)(it / tiles));
+        const int nst = (job == 0 ? 1 : 2) * kblocks;
+        uint32_t d = 0, acc = 0;
+        for (int si = 0; si < nst; ++si) {
+          if (si % chunk == 0) {
+            if (!mbar_wait(bar_tempty + 8 * ab, abphase ^ 1, limit_ns, abort_flag,
+                           timeout_global)) {
+              ok = false;
+              break;
+            }
+            fence_after();
+            d = tmem_base + (uint32_t)(ab * BN);
+            acc = 0;
+          }
+          if (!mbar_wait(bar_full + 8 * stage, phase, limit_ns, abort_flag, timeout_global)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t sA = ring + stage * P_STAGE_BYTES;
+          const uint64_t ah = sw64_desc(sA), al = sw64_desc(sA + A_BYTES);
+          const uint64_t bh = sw64_desc(sA + 2 * A_BYTES);
+          const uint64_t bl = sw64_desc(sA + 3 * A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t off = (uint64_t)((kk * 32) >> 4);
+            mma_f16_pair(d, ah + off, bh + off, idesc, acc);   // hi * hi
+            acc = 1;
+            mma_f16_pair(d, ah + off, bl + off, idesc, 1);     // hi * lo
+            mma_f16_pair(d, al + off, bh + off, idesc, 1);     // lo * hi
+          }
+          mma_commit_pair(bar_empty + 8 * stage);   // frees the stage in both CTAs
+          if (++stage == P_STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+          if (si % chunk == chunk - 1 || si == nst - 1) {
+            mma_commit_pair(bar_tfull + 8 * ab);    // chunk ready in both CTAs
+            if (++ab == 2) {
+              ab = 0;
+              abphase ^= 1;
+            }
+          }
+        }
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              bar_drain)
+          : "memory");
+      const uint64_t t0 = gtimer();
+      while (!mbar_try_wait(bar_drain, 0) && gtimer() - t0 < limit_ns) {
+      }
+    }
+  } else if (warp >= EPI_WARP0) {
+    // ================= epilogue (both CTAs, own 128 rows) =================
+    const int q = warp & 3;
+    const int half = (warp - EPI_WARP0) >> 2;
+    const int rloc = 32 * q + lane;
+    const int et = threadIdx.x - 32 * EPI_WARP0;
+    const size_t mat = (size_t)Np * Np;
+    const uint32_t tlane = (uint32_t)(32 * q) << 16;
+    int ab = 0;
+    uint32_t abphase = 0;
+    bool alive = true;
+    for (int64_t it = pair; it < items && alive; it += npairs) {
+      const int job = job_at(jmask, (int)(it / tiles));
+      const int nst = (job == 0 ? 1 : 2) * kblocks;
+      const int nchunks = (nst + chunk - 1) / chunk;
+      float sum[128];
+#pragma unroll
+      for (int i = 0; i < 128; ++i) sum[i] = 0.0f;
+      for (int ch = 0; ch < nchunks; ++ch) {
+        const bool ok =
+            mbar_wait(bar_tfull + 8 * ab, abphase, limit_ns, abort_flag, timeout_global);
+        if (!epi_all(ok && !*abort_flag)) {
+          alive = false;
+          break;
+        }
+        fence_after();
+        const uint32_t ta = tmem_base + tlane + (uint32_t)(ab * BN + half * 128);
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) {
+          uint32_t x[16];
+          tmem_ld16(ta + 16 * cc, x);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) sum[16 * cc + i] += __uint_as_float(x[i]);
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(lead_tempty + 8 * ab);
+        if (++ab == 2) {
+          ab = 0;
+          abphase ^= 1;
+        }
+      }
+      if (!alive) break;
+
+      const int64_t t = it % tiles;
+      int I2, J;
+      pair_tile_coords(t, &I2, &J);
+      const int curj = job == 0 ? cur0 : st->cur1[job - 1];
+      const int e_cur = job == 0 ? s0e : st->s1_exp_cur[job - 1];
+      const int e_new = job == 0 ? s0e : st->s1_exp_next[job - 1];
+      const float unscale = ldexpf(1.0f, -(s0e + e_cur));
+      const float scale_new = ldexpf(1.0f, e_new);
+      const float sg = (float)sigma, om = 1.0f - (float)sigma;
+      const bool write = job != 0 || write0;
+      const int r = I2 * 2 * BM + (int)rank * BM + rloc;
+      const int c0 = J * BN + half * 128;
+      const size_t row_off = (size_t)r * Np;
+      const float* Sold = master + (size_t)(curj * (1 + k) + job) * mat + row_off;
+      float* Snew = master + (size_t)((curj ^ 1) * (1 + k) + job) * mat;
+      H16* hi_new = reinterpret_cast<H16*>(ops) + (size_t)zslice(curj ^ 1, job, 0, k) * mat;
+      H16* lo_new = reinterpret_cast<H16*>(ops) + (size_t)zslice(curj ^ 1, job, 1, k) * mat;
+
+      float fn_s = 0.0f, fn_c = 0.0f, fd = 0.0f, trf = 0.0f;
+      int bad = 0;
+#pragma unroll
+      for (int g = 0; g < 32; ++g) {
+        const int cb = c0 + 4 * g;
+        if (r > cb + 3) continue;
+        const float4 o4 = *reinterpret_cast<const float4*>(Sold + cb);
+        const float old[4] = {o4.x, o4.y, o4.z, o4.w};
+        float nw[4];
+        H16 nh[4], nl[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float xv = sum[4 * g + i] * unscale;
+          const int c = cb + i;
+          const bool own = c >= r;
+          const float w = (c == r) ? 1.0f : 2.0f;
+          bad += (own && !isfinite(xv)) ? 1 : 0;
+          const float dd = old[i] - xv;
+          fd = own ? fmaf(w * dd, dd, fd) : fd;
+          const float n1 = sg * xv + om * old[i];
+          nw[i] = n1;
+          if (own && write) {
+            const float p = w * n1 * n1;
+            const float e = w * fmaf(n1, n1, -n1 * n1);
+            const float tt = fn_s + p;
+            const float bp = tt - fn_s;
+            fn_c += (fn_s - (tt - bp)) + (p - bp) + e;
+            fn_s = tt;
+            if (c == r) trf += n1;
+          }
+          const float y = n1 * scale_new;
+          nh[i] = CV::to(y);
+          nl[i] = CV::to(y - CV::from(nh[i]));
+        }
+        if (!write) continue;
+        if (r <= cb) {
+          *reinterpret_cast<float4*>(Snew + row_off + cb) = make_float4(nw[0], nw[1], nw[2], nw[3]);
+          uint2 ph, pl2;
+          ph.x = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[0])) |
+                 ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[1])) << 16);
+          ph.y = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[2])) |
+                 ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[3])) << 16);
+          pl2.x = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[0])) |
+                  ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[1])) << 16);
+          pl2.y = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[2])) |
+                  ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[3])) << 16);
+          *reinterpret_cast<uint2*>(hi_new + row_off + cb) = ph;
+          *reinterpret_cast<uint2*>(lo_new + row_off + cb) = pl2;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            if (cb + i >= r) {
+              Snew[row_off + cb + i] = nw[i];
+              hi_new[row_off + cb + i] = nh[i];
+              lo_new[row_off + cb + i] = nl[i];
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int c = cb + i;
+          if (c > r) {
+            const size_t m = (size_t)c * Np + r;
+            Snew[m] = nw[i];
+            hi_new[m] = nh[i];
+            lo_new[m] = nl[i];
+          }
+        }
+      }
+      red[0 * EPI_THREADS + et] = (double)trf;
+      red[1 * EPI_THREADS + et] = (double)fn_s + (double)fn_c;
+      red[2 * EPI_THREADS + et] = (double)fd;
+      red[3 * EPI_THREADS + et] = (double)bad;
+      epi_sync();
+      for (int s2 = EPI_THREADS / 2; s2 > 0; s2 >>= 1) {
+        if (et < s2) {
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) red[qq * EPI_THREADS + et] += red[qq * EPI_THREADS + et + s2];
+        }
+        epi_sync();
+      }
+      if (et == 0) {
+        double* pp = partials + ((size_t)job * ptiles + 2 * t + rank) * kNQ;
+        pp[kQTrace] = red[0];
+        pp[kQFroNew] = red[EPI_THREADS];
+        pp[kQFroDiff] = red[2 * EPI_THREADS];
+        pp[kQBad] = red[3 * EPI_THREADS];
+      }
+      epi_sync();
+    }
+  }
+
+  // ---- teardown: both CTAs done (or aborted); free TMEM of the pair
+  fence_before();
+  __syncthreads();
+  cluster_sync_all();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(TMEM_COLS));
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
@@ -666,7 +1096,7 @@ bool make_map(CUtensorMap* map, void* base, int64_t Np, int slices, int box_rows
 int tc_tile() { return tc::BN; }
 
 cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double timeout_s,
-                            int accum_chunk_k, int64_t* entries, double* pass_flops) {
+                            int accum_chunk_k, int cta_pair, int64_t* entries, double* pass_flops) {
   using namespace tc;
   char* base = (char*)ws;
   const bool bf16 = L.precision == DMPT_DUAL_BF16;
@@ -684,12 +1114,11 @@ cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double ti
                          SMEM_BYTES);
     cudaFuncSetAttribute(layer_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          SMEM_BYTES);
+    cudaFuncSetAttribute(layer_tc2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         P_SMEM_BYTES);
+    cudaFuncSetAttribute(layer_tc2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         P_SMEM_BYTES);
   }
-  const int64_t tiles = num_tiles(L.Np);
-  // the number of jobs is only known on the device; size the grid for the
-  // largest case and let surplus CTAs exit
-  int64_t max_items = tiles * (1 + L.k);
-  int grid = (int)(max_items < sms ? max_items : sms);
   const uint64_t limit_ns = (uint64_t)(timeout_s * 1e9);
   int ck = accum_chunk_k > 0 ? accum_chunk_k : DEFAULT_CHUNK_K;
   int chunk = ck / BK;
@@ -698,6 +1127,27 @@ cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double ti
   float* master = (float*)(base + L.off_master);
   uint16_t* ops = (uint16_t*)(base + L.off_ops16);
   double* partials = (double*)(base + L.off_partials);
+  if (cta_pair) {
+    const int64_t tiles = num_pair_tiles(L.Np);
+    const int64_t max_items = tiles * (1 + L.k);
+    int64_t pairs = sms / 2;
+    if (pairs > max_items) pairs = max_items;
+    const int grid = (int)(2 * pairs);
+    if (bf16)
+      layer_tc2_kernel<true><<<grid, NUM_THREADS, P_SMEM_BYTES, s>>>(
+          mA, st, master, ops, L.Np, L.k, partials, L.partial_tiles, limit_ns, chunk);
+    else
+      layer_tc2_kernel<false><<<grid, NUM_THREADS, P_SMEM_BYTES, s>>>(
+          mA, st, master, ops, L.Np, L.k, partials, L.partial_tiles, limit_ns, chunk);
+    if (entries) *entries = 2 * tiles;
+    if (pass_flops) *pass_flops = (double)tiles * 2 * BM * BN * (double)L.Np * 2.0;
+    return cudaGetLastError();
+  }
+  const int64_t tiles = num_tiles(L.Np);
+  // the number of jobs is only known on the device; size the grid for the
+  // largest case and let surplus CTAs exit
+  int64_t max_items = tiles * (1 + L.k);
+  int grid = (int)(max_items < sms ? max_items : sms);
   if (bf16)
     layer_tc_kernel<true><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(mA, mB, st, master, ops, L.Np,
                                                                 L.k, partials, L.partial_tiles,

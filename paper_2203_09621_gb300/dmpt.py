@@ -38,7 +38,8 @@ class DmptOptions(ctypes.Structure):
         ("timeout_s", ctypes.c_double),
         ("ckpt_every", ctypes.c_int),
         ("accum_chunk", ctypes.c_int),
-        ("reserved", ctypes.c_int * 6),
+        ("cta_pair", ctypes.c_int),
+        ("reserved", ctypes.c_int * 5),
     ]
 
 
@@ -137,7 +138,8 @@ class Info:
 
 
 def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_scaling=1,
-            sync_every=4, timing=False, timeout_s=2.0, accum_chunk=0) -> DmptOptions:
+            sync_every=4, timing=False, timeout_s=2.0, accum_chunk=0,
+            cta_pair=1) -> DmptOptions:
     lib = load_library()
     o = DmptOptions()
     lib.dmpt_default_options(ctypes.byref(o))
@@ -150,6 +152,7 @@ def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_s
     o.timing = int(bool(timing))
     o.timeout_s = float(timeout_s)
     o.accum_chunk = int(accum_chunk)
+    o.cta_pair = int(cta_pair)
     return o
 
 

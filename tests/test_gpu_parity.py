@@ -116,11 +116,12 @@ def test_fp32(ctx, cfg, n):
     assert rel(P, Pr) < tol and rel(P1[0], P1r[0]) < tol, (rel(P, Pr), rel(P1[0], P1r[0]), tol)
 
 
+@pytest.mark.parametrize("cta_pair", [0, 1])
 @pytest.mark.parametrize("precision", ["dual_fp16", "dual_bf16"])
 @pytest.mark.parametrize("cfg,n", [(1, None), (2, 300), (2, 1024), (3, 512)])
-def test_dual(ctx, precision, cfg, n):
+def test_dual(ctx, precision, cfg, n, cta_pair):
     inst = make_workload(cfg, n=n)
-    P, P1, info = run(ctx, inst, precision)
+    P, P1, info = run(ctx, inst, precision, cta_pair=cta_pair)
     Pr, P1r = oracle.response_sos(inst.H, inst.H1, inst.n_occ)
     assert info.converged, info
     assert rel(P, Pr) < TOL[precision]
@@ -143,11 +144,11 @@ def test_two_level_closed_form(ctx, golden, precision):
     assert info.d0_layer == g["d0_layer"] and info.converged
 
 
-@pytest.mark.parametrize("precision", ["fp32", "dual_fp16"])
-def test_deterministic(ctx, precision):
+@pytest.mark.parametrize("precision,cta_pair", [("fp32", 0), ("dual_fp16", 0), ("dual_fp16", 1)])
+def test_deterministic(ctx, precision, cta_pair):
     inst = make_workload(2, n=512)
-    a = run(ctx, inst, precision)
-    b = run(ctx, inst, precision)
+    a = run(ctx, inst, precision, cta_pair=cta_pair)
+    b = run(ctx, inst, precision, cta_pair=cta_pair)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
     assert a[2].sigma == b[2].sigma
 
