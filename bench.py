@@ -246,6 +246,7 @@ def main():
     ap.add_argument("--accum-chunk", type=int, default=0)
     ap.add_argument("--input-backend", default="torch", choices=["torch", "numpy"])
     ap.add_argument("--cta-pair", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--k-snake", type=int, default=1, choices=[0, 1])
     args = ap.parse_args()
     global INPUT_BACKEND
     INPUT_BACKEND = args.input_backend
@@ -273,7 +274,7 @@ def main():
     P1 = torch.empty(k, n, n, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     kw = dict(precision=args.precision, out=(P, P1), stream=stream,
-              accum_chunk=args.accum_chunk, cta_pair=args.cta_pair)
+              accum_chunk=args.accum_chunk, cta_pair=args.cta_pair, k_snake=args.k_snake)
 
     # warm-up (also sizes the workspace)
     for _ in range(args.warmup):

@@ -87,7 +87,9 @@ typedef struct {
   int cta_pair;         /* dual forms: 1 = products on CTA pairs (cta_group::2,
                            256 x 256 tiles, default), 0 = one CTA per
                            128 x 256 tile                                      */
-  int reserved[5];
+  int k_snake;          /* CTA-pair form: 1 = alternate the K-sweep direction
+                           between scheduling rounds for L2 reuse (default 1) */
+  int reserved[4];
 } dmpt_options;
 
 /* Filled on the host by dmpt_sp2_response (when info != NULL). */

@@ -56,6 +56,7 @@ bool valid_options(const dmpt_options* o) {
   if (o->ckpt_every < 0) return false;
   if (o->accum_chunk < 0) return false;
   if (o->cta_pair < 0 || o->cta_pair > 1) return false;
+  if (o->k_snake < 0 || o->k_snake > 1) return false;
   return true;
 }
 
@@ -110,6 +111,7 @@ void dmpt_default_options(dmpt_options* o) {
   o->ckpt_every = 0;
   o->accum_chunk = 0;
   o->cta_pair = 1;
+  o->k_snake = 1;
 }
 
 const char* dmpt_status_string(dmpt_status s) {
@@ -246,7 +248,7 @@ dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, 
     for (int j = 0; j < o->sync_every && launched < max_layers; ++j) {
       if (o->timing) cudaEventRecord(h->events[2 * launched], s);
       e = dual ? launch_layer_tc(L, workspace, s, o->timeout_s, o->accum_chunk, o->cta_pair,
-                                 &entries, &pass_flops)
+                                 o->k_snake, &entries, &pass_flops)
                : launch_layer_simt(L, workspace, s, &entries, &pass_flops);
       if (e != cudaSuccess) return cuda_fail(h, e, "layer product");
       if (o->timing) cudaEventRecord(h->events[2 * launched + 1], s);

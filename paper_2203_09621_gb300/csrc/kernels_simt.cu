@@ -139,36 +139,58 @@ __global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const d
                                                    const double* __restrict__ H1, int64_t n,
                                                    int64_t Np, int64_t ld, int k,
                                                    double* partials, int64_t ptiles) {
+  // 32 x 32 tile pairs (bi <= bj): the upper tile is read row-wise (coalesced),
+  // written in place and, through shared memory, transposed into the mirror
+  // tile, so both triangles of S come from the upper triangle of the input.
+  __shared__ double tile[32][33];
   __shared__ double red[3 * 256];
   const double e1 = st->eps1, eN = st->epsN;
   const double w = 1.0 / (eN - e1);
   const size_t mat = (size_t)Np * Np;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+  const int64_t TB = Np / 32;
+  const int64_t pairs = TB * (TB + 1) / 2;
   double tr = 0.0, f0 = 0.0, bad = 0.0;
   double f1[kMaxK];
 #pragma unroll
   for (int j = 0; j < kMaxK; ++j) f1[j] = 0.0;
-  const int64_t total = (int64_t)Np * Np;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = idx / Np, c = idx - r * Np;
-    const bool in = r < n && c < n;
-    const int64_t src = (r <= c ? r * ld + c : c * ld + r);
-    double s0 = 0.0;
-    if (in) s0 = ((r == c ? eN : 0.0) - H[src]) * w;
-    const T t0 = (T)s0;
-    master[idx] = t0;
-    const double d0 = (double)t0;
-    if (r == c) tr += d0;
-    f0 += d0 * d0;
-    if (!isfinite(d0)) bad += 1.0;
-    for (int j = 0; j < k; ++j) {
-      double s1 = 0.0;
-      if (in) s1 = -H1[(size_t)j * n * ld + src] * w;
-      const T t1 = (T)s1;
-      master[(size_t)(1 + j) * mat + idx] = t1;
-      const double d1 = (double)t1;
-      f1[j] += d1 * d1;
-      if (!isfinite(d1)) bad += 1.0;
+  for (int64_t tp = blockIdx.x; tp < pairs; tp += gridDim.x) {
+    // tile pair index -> (bi, bj), bj-major: tp = bj (bj + 1) / 2 + bi
+    int64_t bj = (int64_t)((sqrt(8.0 * (double)tp + 1.0) - 1.0) * 0.5);
+    while ((bj + 1) * (bj + 2) / 2 <= tp) ++bj;
+    while (bj * (bj + 1) / 2 > tp) --bj;
+    const int64_t bi = tp - bj * (bj + 1) / 2;
+    for (int m = 0; m <= k; ++m) {
+      const double* src = m == 0 ? H : H1 + (size_t)(m - 1) * n * ld;
+      for (int i = 0; i < 4; ++i) {
+        const int rl = ty + 8 * i;
+        const int64_t r = bi * 32 + rl, c = bj * 32 + tx;
+        double v = 0.0;
+        if (r < n && c < n) {
+          const double h = src[r * ld + c];
+          v = m == 0 ? ((r == c ? eN : 0.0) - h) * w : -h * w;
+        }
+        tile[rl][tx] = (double)(T)v;   // the stored (rounded) value
+      }
+      __syncthreads();
+      T* dst = master + (size_t)m * mat;
+      for (int i = 0; i < 4; ++i) {
+        const int rl = ty + 8 * i;
+        const int64_t r = bi * 32 + rl, c = bj * 32 + tx;
+        // diagonal tile: the lower half mirrors the upper half
+        const double v = (bi < bj || rl <= tx) ? tile[rl][tx] : tile[tx][rl];
+        dst[(size_t)r * Np + c] = (T)v;
+        const double wgt = bi < bj ? 2.0 : 1.0;   // the mirror tile holds the same values
+        if (m == 0) {
+          if (r == c) tr += v;
+          f0 += wgt * v * v;
+        } else {
+          f1[m - 1] += wgt * v * v;
+        }
+        if (!isfinite(v)) bad += 1.0;
+        if (bi < bj) dst[(size_t)(bj * 32 + rl) * Np + bi * 32 + tx] = (T)tile[tx][rl];
+      }
+      __syncthreads();
     }
   }
   // job 0: trace, fro, bad

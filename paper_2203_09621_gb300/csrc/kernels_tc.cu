@@ -676,9 +676,13 @@ __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
                    : "memory");
 }
+// Arrive on a barrier of another CTA of the cluster.  Release at CTA scope
+// only: the arrival signals that this warp's tensor-memory reads are done
+// (tcgen05.wait::ld has returned), not that its global stores are visible,
+// so no cluster-scope fence (which would wait for the previous tile's
+// stores) is needed.
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
-               : "memory");
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 __device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap* map, int x, int y,
                                                  int z, uint32_t leader_bar) {
@@ -712,7 +716,7 @@ template <bool BF16>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     layer_tc2_kernel(const __grid_constant__ CUtensorMap mapA, State* st, float* __restrict__ master,
                      uint16_t* __restrict__ ops, int64_t Np, int k, double* __restrict__ partials,
-                     int64_t ptiles, uint64_t limit_ns, int chunk) {
+                     int64_t ptiles, uint64_t limit_ns, int chunk, int k_snake) {
   using CV = Cvt<BF16>;
   using H16 = typename CV::T;
   extern __shared__ uint8_t smem_raw[];
@@ -788,7 +792,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      for (int64_t it = pair; it < items && ok; it += npairs) {
+      int64_t round = 0;
+      for (int64_t it = pair; it < items && ok; it += npairs, ++round) {
         const int job = job_at(jmask, (int)(it / tiles));
         int I2, J;
         pair_tile_coords(it % tiles, &I2, &J);
@@ -796,12 +801,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
         const int curj = job == 0 ? cur0 : st->cur1[job - 1];
         const int rowA = I2 * 2 * BM + (int)rank * BM;
         const int rowB = J * BN + (int)rank * BM;
-        for (int pass = 0; pass < passes && ok; ++pass) {
+        // all pairs move through their tiles' K ranges in near lockstep; in
+        // odd rounds the sweep runs backwards (passes and K blocks), so a
+        // round starts on the panel slices the previous round loaded last,
+        // which are still in L2
+        const bool rev = k_snake && (round & 1);
+        for (int pp = 0; pp < passes && ok; ++pp) {
+          const int pass = rev ? passes - 1 - pp : pp;
           const int mA = pass == 0 ? 0 : job, bufA = pass == 0 ? cur0 : curj;
           const int mB = pass == 0 ? job : 0, bufB = pass == 0 ? curj : cur0;
           const int zAh = zslice(bufA, mA, 0, k), zAl = zslice(bufA, mA, 1, k);
           const int zBh = zslice(bufB, mB, 0, k), zBl = zslice(bufB, mB, 1, k);
-          for (int kb = 0; kb < kblocks; ++kb) {
+          for (int kq = 0; kq < kblocks; ++kq) {
+            const int kb = rev ? kblocks - 1 - kq : kq;
             if (!mbar_wait(bar_empty + 8 * stage, phase ^ 1, limit_ns, abort_flag,
                            timeout_global)) {
               ok = false;
@@ -1096,7 +1108,8 @@ bool make_map(CUtensorMap* map, void* base, int64_t Np, int slices, int box_rows
 int tc_tile() { return tc::BN; }
 
 cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double timeout_s,
-                            int accum_chunk_k, int cta_pair, int64_t* entries, double* pass_flops) {
+                            int accum_chunk_k, int cta_pair, int k_snake, int64_t* entries,
+                            double* pass_flops) {
   using namespace tc;
   char* base = (char*)ws;
   const bool bf16 = L.precision == DMPT_DUAL_BF16;
@@ -1135,10 +1148,10 @@ cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double ti
     const int grid = (int)(2 * pairs);
     if (bf16)
       layer_tc2_kernel<true><<<grid, NUM_THREADS, P_SMEM_BYTES, s>>>(
-          mA, st, master, ops, L.Np, L.k, partials, L.partial_tiles, limit_ns, chunk);
+          mA, st, master, ops, L.Np, L.k, partials, L.partial_tiles, limit_ns, chunk, k_snake);
     else
       layer_tc2_kernel<false><<<grid, NUM_THREADS, P_SMEM_BYTES, s>>>(
-          mA, st, master, ops, L.Np, L.k, partials, L.partial_tiles, limit_ns, chunk);
+          mA, st, master, ops, L.Np, L.k, partials, L.partial_tiles, limit_ns, chunk, k_snake);
     if (entries) *entries = 2 * tiles;
     if (pass_flops) *pass_flops = (double)tiles * 2 * BM * BN * (double)L.Np * 2.0;
     return cudaGetLastError();

@@ -39,7 +39,8 @@ class DmptOptions(ctypes.Structure):
         ("ckpt_every", ctypes.c_int),
         ("accum_chunk", ctypes.c_int),
         ("cta_pair", ctypes.c_int),
-        ("reserved", ctypes.c_int * 5),
+        ("k_snake", ctypes.c_int),
+        ("reserved", ctypes.c_int * 4),
     ]
 
 
@@ -139,7 +140,7 @@ class Info:
 
 def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_scaling=1,
             sync_every=4, timing=False, timeout_s=2.0, accum_chunk=0,
-            cta_pair=1) -> DmptOptions:
+            cta_pair=1, k_snake=1) -> DmptOptions:
     lib = load_library()
     o = DmptOptions()
     lib.dmpt_default_options(ctypes.byref(o))
@@ -153,6 +154,7 @@ def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_s
     o.timeout_s = float(timeout_s)
     o.accum_chunk = int(accum_chunk)
     o.cta_pair = int(cta_pair)
+    o.k_snake = int(k_snake)
     return o
 
 
