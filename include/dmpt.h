@@ -79,8 +79,9 @@ typedef struct {
   int timing;           /* 1: time every layer-product launch with CUDA events
                            on `stream` and report it in dmpt_info             */
   double timeout_s;     /* limit of any device-side spin wait (default 2.0)   */
-  int ckpt_every;       /* >0: keep S every ckpt_every layers plus the branch
-                           sequence in the workspace, for dmpt_sp2_backward   */
+  int ckpt_every;       /* 1: keep the 16-bit copies of every S0 layer state in
+                           the workspace (dual forms) for dmpt_sp2_backward;
+                           0: none (default)                                  */
   int accum_chunk;      /* dual forms: K elements summed per tensor-memory
                            accumulator before the running sum is carried in
                            FP32 on the CUDA cores (0: default 256)             */
@@ -142,8 +143,9 @@ dmpt_status dmpt_bounds(dmpt_handle h, const double* H, int64_t n, int64_t ld,
 /* Density matrix and first-order responses by DNN-SP2-PT (Algorithms 1-3).
  *   H      device, n x n (ld), float64, symmetric.
  *   H1     device, k blocks of n x n (ld), float64, each symmetric.
- *   k      1..DMPT_MAX_K directions sharing one S_0 recursion (each has its
- *          own Alg. 3 test and stops independently).
+ *   k      0..DMPT_MAX_K directions sharing one S_0 recursion (each has its
+ *          own Alg. 3 test and stops independently); k = 0 computes P only
+ *          (H1 and P1 may then be NULL, P must not).
  *   n_occ  0..n.  n_occ = 0 or n gives P = 0 or I and P1 = 0 at once.
  *   o      options (NULL: defaults).
  *   P      device n x n (ld) output, may be NULL.
@@ -154,12 +156,38 @@ dmpt_status dmpt_bounds(dmpt_handle h, const double* H, int64_t n, int64_t ld,
  * o->sync_every layers to read the convergence flag; it returns when the
  * outputs are written.  Returns DMPT_ENOTCONV (outputs = last iterate) when
  * max_layers is reached, DMPT_ENUMERIC on non-finite values or
- * eps_N <= eps_1 for 0 < n_occ < n. */
+ * eps_N <= eps_1 for 0 < n_occ < n.  With o->ckpt_every = 1 the workspace
+ * (sized by dmpt_workspace_size with the same options) also keeps every S0
+ * layer state for dmpt_sp2_backward. */
 dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1,
                               int k, int64_t n, int64_t ld, int64_t n_occ,
                               const dmpt_options* o, double* P, double* P1,
                               dmpt_info* info, void* workspace, size_t ws_bytes,
                               void* stream);
+
+/* Adjoint of the S0 recursion: the gradient of L = Tr[G P] with respect to H
+ * for the P of the preceding dmpt_sp2_response call that used `workspace`
+ * with o->ckpt_every = 1 and a dual precision.  The paper has no backward
+ * pass; this is the reverse mode of its layer map (Sec. II B, Eq. (eq:Sn)):
+ *   Gbar_U = (G + G^T)/2,
+ *   Gbar_{m-1} = sigma_m (S_{m-1} Gbar_m + Gbar_m S_{m-1}) + (1 - sigma_m) Gbar_m
+ * over the U layers that updated S0 (newest first), each a response-type
+ * layer product on the tensor cores with the stored S_{m-1}, and
+ *   dL/dH = -Gbar_0 / (eps_N - eps_1),
+ * with the branch choices and the Gershgorin bounds held fixed (piecewise
+ * constant in H).  At convergence this equals the first-order response to
+ * the perturbation G (the Daleckii-Krein derivative is self-adjoint).
+ *   G      device n x n (ld), float64 (need not be symmetric).
+ *   o      options for the products (precision is taken from the forward).
+ *   dLdH   device n x n (ld) output, float64, symmetric.
+ * The forward's response slots are reused as scratch; the S0 tape is left
+ * intact, so several backward calls may follow one forward call.  Returns
+ * DMPT_EINVAL when the workspace holds no tape of a converged forward run of
+ * this n.  Synchronises `stream` once at entry (to read the forward state)
+ * and once at exit. */
+dmpt_status dmpt_sp2_backward(dmpt_handle h, const double* G, int64_t n, int64_t ld,
+                              const dmpt_options* o, double* dLdH, void* workspace,
+                              size_t ws_bytes, void* stream);
 
 /* Static-scratch variant of dmpt_sp2_response for callers that cannot
  * allocate device memory (a host framework that owns every allocation, code

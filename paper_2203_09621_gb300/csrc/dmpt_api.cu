@@ -53,15 +53,30 @@ bool valid_options(const dmpt_options* o) {
   if (!(o->c_pt > 0.0) || !(o->c_d0 > 0.0)) return false;
   if (o->sync_every < 1) return false;
   if (!(o->timeout_s > 0.0)) return false;
-  if (o->ckpt_every < 0) return false;
+  if (o->ckpt_every < 0 || o->ckpt_every > 1) return false;
   if (o->accum_chunk < 0) return false;
   if (o->cta_pair < 0 || o->cta_pair > 1) return false;
   if (o->k_snake < 0 || o->k_snake > 1) return false;
   return true;
 }
 
+// Workspace geometry for (n, k) under options o: response slots (at least
+// one when S0 states are kept, for the adjoint) and tape capacity.
+Layout layout_for(int64_t n, int k, const dmpt_options* o) {
+  const bool tape = o->ckpt_every == 1;
+  const int slots = (tape && k == 0) ? 1 : k;
+  return make_layout(n, slots, o->precision, tape ? o->max_layers + 2 : 0);
+}
+
 __global__ void state_init_kernel(State* st, int k, int max_layers, int precision, double n_occ,
-                                  double c_pt, double c_d0) {
+                                  double c_pt, double c_d0, int tape, int tape_base,
+                                  int tape_states, int layout_k, int64_t n) {
+  st->tape = tape;
+  st->tape_base = tape_base;
+  st->tape_states = tape_states;
+  st->layout_k = layout_k;
+  st->k_fwd = k;
+  st->n = n;
   st->n_layer = 0;
   st->done = 0;
   st->status = DMPT_OK;
@@ -75,6 +90,14 @@ __global__ void state_init_kernel(State* st, int k, int max_layers, int precisio
   st->plan_square = 0;
   st->plan_write0 = 0;
   for (int j = 0; j < kMaxK; ++j) st->plan_resp[j] = 0;
+}
+
+// Re-open a finished forward state for the adjoint run (keeps sigma, the
+// bounds, the tape geometry and the number of S0 updates).
+__global__ void adj_state_reset_kernel(State* st) {
+  st->done = 0;
+  st->status = DMPT_OK;
+  st->timeout_flag = 0;
 }
 
 double layer_alg_flops(double n, int prec, bool square, int active) {
@@ -160,8 +183,8 @@ size_t dmpt_workspace_size(int64_t n, int k, const dmpt_options* o) {
   dmpt_options d;
   dmpt_default_options(&d);
   if (!o) o = &d;
-  if (n < 1 || k < 1 || k > DMPT_MAX_K || !valid_options(o)) return 0;
-  return make_layout(n, k, o->precision).total;
+  if (n < 1 || k < 0 || k > DMPT_MAX_K || !valid_options(o)) return 0;
+  return layout_for(n, k, o).total;
 }
 
 dmpt_status dmpt_bounds(dmpt_handle h, const double* H, int64_t n, int64_t ld, double* eps,
@@ -186,13 +209,15 @@ dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, 
   dmpt_default_options(&defaults);
   if (!o) o = &defaults;
   if (info) memset(info, 0, sizeof(*info));
-  if (!H || !H1 || !P1) return fail(h, DMPT_EINVAL, "dmpt_sp2_response: null %s", "H/H1/P1");
-  if (k < 1 || k > DMPT_MAX_K) return fail(h, DMPT_EINVAL, "dmpt_sp2_response: k out of range%s");
+  if (k < 0 || k > DMPT_MAX_K) return fail(h, DMPT_EINVAL, "dmpt_sp2_response: k out of range%s");
+  if (!H || (k > 0 && (!H1 || !P1)) || (k == 0 && !P))
+    return fail(h, DMPT_EINVAL, "dmpt_sp2_response: null %s", "H/H1/P1/P");
   if (n < 1 || ld < n) return fail(h, DMPT_EINVAL, "dmpt_sp2_response: need n >= 1, ld >= n%s");
   if (n_occ < 0 || n_occ > n) return fail(h, DMPT_EINVAL, "dmpt_sp2_response: n_occ out of [0, n]%s");
   if (!valid_options(o)) return fail(h, DMPT_EINVAL, "dmpt_sp2_response: invalid options%s");
-  if (o->ckpt_every != 0)
-    return fail(h, DMPT_EUNSUPPORTED, "dmpt_sp2_response: ckpt_every is not supported%s");
+  if (o->ckpt_every != 0 && o->precision < DMPT_DUAL_FP16)
+    return fail(h, DMPT_EUNSUPPORTED,
+                "dmpt_sp2_response: the S0 tape (ckpt_every = 1) needs a dual precision%s");
   cudaStream_t s = (cudaStream_t)stream;
   DeviceGuard g(h->device);
 
@@ -207,7 +232,7 @@ dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, 
     return DMPT_OK;
   }
 
-  const Layout L = make_layout(n, k, o->precision);
+  const Layout L = layout_for(n, k, o);
   if (!workspace) return fail(h, DMPT_EWORKSPACE, "dmpt_sp2_response: null workspace%s");
   if (((uintptr_t)workspace) % 256)
     return fail(h, DMPT_EWORKSPACE, "dmpt_sp2_response: workspace not 256-byte aligned%s");
@@ -220,15 +245,16 @@ dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, 
   cudaError_t e = cudaMemsetAsync(st, 0, sizeof(State), s);
   if (e != cudaSuccess) return cuda_fail(h, e, "state reset");
   state_init_kernel<<<1, 1, 0, s>>>(st, k, o->max_layers, o->precision, (double)n_occ, o->c_pt,
-                                    o->c_d0);
+                                    o->c_d0, L.tape_states > 0 ? 1 : 0, 4 * (1 + L.k),
+                                    L.tape_states, L.k, n);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "state init");
   if ((e = launch_bounds(H, n, ld, &st->eps1, s)) != cudaSuccess) return cuda_fail(h, e, "bounds");
   const int init_blocks = 1024;
-  if ((e = launch_init(L, workspace, H, H1, ld, init_blocks, s)) != cudaSuccess)
+  if ((e = launch_init(L, workspace, H, H1, ld, k, init_blocks, s)) != cudaSuccess)
     return cuda_fail(h, e, "init");
   if ((e = launch_decide(L, workspace, kDecideInit, init_blocks, s)) != cudaSuccess)
     return cuda_fail(h, e, "decide(init)");
-  if (dual && (e = launch_split(L, workspace, s)) != cudaSuccess) return cuda_fail(h, e, "split");
+  if (dual && (e = launch_split(L, workspace, 0, s)) != cudaSuccess) return cuda_fail(h, e, "split");
 
   // events for per-launch timing of the layer products
   const int max_layers = o->max_layers;
@@ -261,7 +287,7 @@ dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, 
       return cuda_fail(h, e, "poll");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(h, e, "layer loop");
   }
-  if ((e = launch_finalize(L, workspace, P, P1, ld, s)) != cudaSuccess)
+  if ((e = launch_finalize(L, workspace, P, P1, ld, k, s)) != cudaSuccess)
     return cuda_fail(h, e, "finalize");
 
   State* host_state = new State;
@@ -321,6 +347,70 @@ dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, 
   if (status == DMPT_ENUMERIC) fail(h, status, "non-finite values or eps_N <= eps_1%s");
   if (status == DMPT_ENOTCONV) fail(h, status, "max_layers reached%s");
   return status;
+}
+
+dmpt_status dmpt_sp2_backward(dmpt_handle h, const double* G, int64_t n, int64_t ld,
+                              const dmpt_options* o, double* dLdH, void* workspace,
+                              size_t ws_bytes, void* stream) {
+  if (!h) return DMPT_EINVAL;
+  h->err[0] = 0;
+  dmpt_options defaults;
+  dmpt_default_options(&defaults);
+  if (!o) o = &defaults;
+  if (!G || !dLdH) return fail(h, DMPT_EINVAL, "dmpt_sp2_backward: null %s", "G/dLdH");
+  if (n < 1 || ld < n) return fail(h, DMPT_EINVAL, "dmpt_sp2_backward: need n >= 1, ld >= n%s");
+  if (!valid_options(o)) return fail(h, DMPT_EINVAL, "dmpt_sp2_backward: invalid options%s");
+  if (!workspace || ((uintptr_t)workspace) % 256 || ws_bytes < sizeof(State))
+    return fail(h, DMPT_EWORKSPACE, "dmpt_sp2_backward: workspace missing or misaligned%s");
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceGuard g(h->device);
+  cudaError_t e;
+  State* st = (State*)workspace;
+  State* hs = new State;
+  e = cudaMemcpyAsync(hs, st, sizeof(State), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    delete hs;
+    return cuda_fail(h, e, "dmpt_sp2_backward: state read");
+  }
+  const State fs = *hs;
+  delete hs;
+  if (fs.tape != 1 || fs.n != n || !fs.done || fs.d0_updates < 0 ||
+      fs.d0_updates + 1 > fs.tape_states ||
+      (fs.precision != DMPT_DUAL_FP16 && fs.precision != DMPT_DUAL_BF16))
+    return fail(h, DMPT_EINVAL,
+                "dmpt_sp2_backward: the workspace holds no S0 tape of a dual-precision forward "
+                "run of this n (run dmpt_sp2_response with ckpt_every = 1 first)%s");
+  if (fs.status != DMPT_OK)
+    return fail(h, DMPT_EINVAL, "dmpt_sp2_backward: the forward run did not converge%s");
+  const Layout L = make_layout(n, fs.layout_k, fs.precision, fs.tape_states);
+  if (ws_bytes < L.total) return fail(h, DMPT_EWORKSPACE, "dmpt_sp2_backward: workspace too small%s");
+
+  const int blocks = 1024;
+  adj_state_reset_kernel<<<1, 1, 0, s>>>(st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "adjoint reset");
+  if ((e = launch_adj_init(L, workspace, G, ld, blocks, s)) != cudaSuccess)
+    return cuda_fail(h, e, "adjoint init");
+  if ((e = launch_decide(L, workspace, kDecideAdjInit, blocks, s)) != cudaSuccess)
+    return cuda_fail(h, e, "adjoint decide");
+  if ((e = launch_split(L, workspace, 1, s)) != cudaSuccess) return cuda_fail(h, e, "adjoint split");
+  int64_t entries = 0;
+  double pass_flops = 0.0;
+  for (int m = fs.d0_updates; m >= 1; --m) {
+    if ((e = launch_layer_tc(L, workspace, s, o->timeout_s, o->accum_chunk, o->cta_pair,
+                             o->k_snake, &entries, &pass_flops)) != cudaSuccess)
+      return cuda_fail(h, e, "adjoint layer");
+    if ((e = launch_decide(L, workspace, kDecideAdjLayer, entries, s)) != cudaSuccess)
+      return cuda_fail(h, e, "adjoint decide");
+  }
+  if ((e = launch_adj_finalize(L, workspace, dLdH, ld, s)) != cudaSuccess)
+    return cuda_fail(h, e, "adjoint finalize");
+  int status = 0;
+  e = cudaMemcpyAsync(&status, &st->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "dmpt_sp2_backward");
+  if (status != DMPT_OK) return fail(h, (dmpt_status)status, "dmpt_sp2_backward: device status%s");
+  return DMPT_OK;
 }
 
 }  // extern "C"

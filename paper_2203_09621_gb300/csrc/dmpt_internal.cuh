@@ -46,7 +46,17 @@ struct State {
   int max_layers;
   int precision;
   int layers_run;       // layers whose product finished
-  int pad0;
+  int tape;             // 1: each S0 state's 16-bit copies are kept (adjoint)
+  int z0_cur;           // operand slice (hi; lo = +1) of the current S0
+  int z0_next;          // slice the next stored S0 copies go to
+  int tape_base;        // first tape slice
+  int tape_states;      // tape capacity (states)
+  int d0_updates;       // S0 updates so far (tape states = d0_updates + 1)
+  int layout_k;         // response slots in the workspace layout
+  int k_fwd;            // directions of the forward run
+  int adj_m;            // adjoint: layer whose adjoint runs next
+  int pad1;
+  int64_t n;
   int cur1[kMaxK];
   int d1_conv[kMaxK];
   int d1_layer[kMaxK];
@@ -66,14 +76,21 @@ struct State {
 // Workspace layout (byte offsets from the workspace base, 256-aligned).
 struct Layout {
   int64_t n, Np;          // logical and padded size
-  int k;
+  int k;                  // response slots (>= 1 when a tape is kept)
   int precision;
+  int tape_states;        // 16-bit S0 copies kept for the adjoint (0: none)
   size_t elem;            // bytes per master element (8 or 4)
   size_t off_state, off_partials, off_master, off_ops16, total;
   int64_t partial_tiles;  // entries per job in the partials array
 };
 
-Layout make_layout(int64_t n, int k, int precision);
+Layout make_layout(int64_t n, int k, int precision, int tape_states = 0);
+
+// 16-bit operand slice of matrix m (0 = S0, 1 + j = S1_j) in ping-pong buffer
+// `buf`, part 0 = hi, 1 = lo.  Tape slices follow the 4 (1 + k) ping-pong ones.
+__host__ __device__ inline int zslice(int buf, int m, int part, int k) {
+  return (buf * (1 + k) + m) * 2 + part;
+}
 
 // Upper-triangular tile count for block size bt.
 inline int64_t upper_tiles(int64_t Np, int bt) {
@@ -85,16 +102,22 @@ inline int64_t upper_tiles(int64_t Np, int bt) {
 cudaError_t launch_bounds(const double* H, int64_t n, int64_t ld, double* eps_out,
                           cudaStream_t s);
 cudaError_t launch_init(const Layout& L, void* ws, const double* H, const double* H1,
-                        int64_t ld, int blocks, cudaStream_t s);
+                        int64_t ld, int k, int blocks, cudaStream_t s);
 cudaError_t launch_decide(const Layout& L, void* ws, int mode, int64_t entries,
                           cudaStream_t s);
 // Layer-product launchers.  *entries: partial-sum entries per job (tiles);
 // *pass_flops: flops of one full-K, single-term pass over all tiles.
 cudaError_t launch_layer_simt(const Layout& L, void* ws, cudaStream_t s, int64_t* entries,
                               double* pass_flops);
-cudaError_t launch_split(const Layout& L, void* ws, cudaStream_t s);
+cudaError_t launch_split(const Layout& L, void* ws, int first_job, cudaStream_t s);
+// adjoint: Gbar = sym(G) into response slot 1 (upper triangle mirrored)
+cudaError_t launch_adj_init(const Layout& L, void* ws, const double* G, int64_t ld, int blocks,
+                            cudaStream_t s);
+// dL/dH = -Gbar / (eps_N - eps_1)
+cudaError_t launch_adj_finalize(const Layout& L, void* ws, double* dLdH, int64_t ld,
+                                cudaStream_t s);
 cudaError_t launch_finalize(const Layout& L, void* ws, double* P, double* P1,
-                            int64_t ld, cudaStream_t s);
+                            int64_t ld, int k_out, cudaStream_t s);
 cudaError_t launch_trivial(int64_t n, int k, int64_t ld, int full, double* P,
                            double* P1, cudaStream_t s);
 int simt_tile(int precision);
@@ -105,7 +128,7 @@ cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double ti
                             double* pass_flops);
 int tc_tile();
 
-enum DecideMode { kDecideInit = 0, kDecideLayer = 1 };
+enum DecideMode { kDecideInit = 0, kDecideLayer = 1, kDecideAdjInit = 2, kDecideAdjLayer = 3 };
 
 // CUDA device of a handle (-1 for NULL).
 int handle_device(dmpt_handle h);

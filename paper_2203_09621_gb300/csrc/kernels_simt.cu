@@ -15,12 +15,13 @@ namespace dmpt {
 
 static inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-Layout make_layout(int64_t n, int k, int precision) {
+Layout make_layout(int64_t n, int k, int precision, int tape_states) {
   Layout L{};
   L.n = n;
   L.Np = ((n + kPad - 1) / kPad) * kPad;
   L.k = k;
   L.precision = precision;
+  L.tape_states = tape_states;
   L.elem = (precision == DMPT_FP64) ? 8 : 4;
   size_t off = 0;
   L.off_state = off;
@@ -36,7 +37,7 @@ Layout make_layout(int64_t n, int k, int precision) {
   off = align256(off + 2 * (size_t)(1 + k) * mat * L.elem);
   if (precision == DMPT_DUAL_FP16 || precision == DMPT_DUAL_BF16) {
     L.off_ops16 = off;
-    off = align256(off + 2 * (size_t)(1 + k) * 2 * mat * 2);
+    off = align256(off + (2 * (size_t)(1 + k) * 2 + 2 * (size_t)tape_states) * mat * 2);
   } else {
     L.off_ops16 = 0;
   }
@@ -137,7 +138,7 @@ cudaError_t launch_bounds(const double* H, int64_t n, int64_t ld, double* eps_ou
 template <typename T>
 __global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const double* __restrict__ H,
                                                    const double* __restrict__ H1, int64_t n,
-                                                   int64_t Np, int64_t ld, int k,
+                                                   int64_t Np, int64_t ld, int k, int lk,
                                                    double* partials, int64_t ptiles) {
   // 32 x 32 tile pairs (bi <= bj): the upper tile is read row-wise (coalesced),
   // written in place and, through shared memory, transposed into the mirror
@@ -173,7 +174,8 @@ __global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const d
         tile[rl][tx] = (double)(T)v;   // the stored (rounded) value
       }
       __syncthreads();
-      T* dst = master + (size_t)m * mat;
+      T* dst = master + (size_t)m * mat;   // buffer 0 (slots 0 .. lk)
+      (void)lk;
       for (int i = 0; i < 4; ++i) {
         const int rl = ty + 8 * i;
         const int64_t r = bi * 32 + rl, c = bj * 32 + tx;
@@ -219,16 +221,16 @@ __global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const d
 }
 
 cudaError_t launch_init(const Layout& L, void* ws, const double* H, const double* H1,
-                        int64_t ld, int blocks, cudaStream_t s) {
+                        int64_t ld, int k, int blocks, cudaStream_t s) {
   char* base = (char*)ws;
   State* st = (State*)(base + L.off_state);
   double* partials = (double*)(base + L.off_partials);
   if (L.precision == DMPT_FP64)
     init_kernel<double><<<blocks, 256, 0, s>>>(st, (double*)(base + L.off_master), H, H1, L.n,
-                                               L.Np, ld, L.k, partials, L.partial_tiles);
+                                               L.Np, ld, k, L.k, partials, L.partial_tiles);
   else
     init_kernel<float><<<blocks, 256, 0, s>>>(st, (float*)(base + L.off_master), H, H1, L.n,
-                                              L.Np, ld, L.k, partials, L.partial_tiles);
+                                              L.Np, ld, k, L.k, partials, L.partial_tiles);
   return cudaGetLastError();
 }
 
@@ -288,10 +290,12 @@ __global__ void __launch_bounds__(256) decide_kernel(State* st, const double* __
   __shared__ double red[kNQ * 256];
   __shared__ double sums[kMaxK + 1][kNQ];
   if (st->done) return;
-  const int k = st->k;
+  const bool adj = mode == kDecideAdjInit || mode == kDecideAdjLayer;
+  const int k = adj ? 1 : st->k;
   for (int job = 0; job <= k; ++job) {
-    const bool ran = mode == kDecideInit ||
-                     (job == 0 ? st->plan_square != 0 : st->plan_resp[job - 1] != 0);
+    const bool ran = adj ? job == 1
+                         : (mode == kDecideInit ||
+                            (job == 0 ? st->plan_square != 0 : st->plan_resp[job - 1] != 0));
     if (!ran) continue;  // uniform across the block
     double v[kNQ] = {0.0, 0.0, 0.0, 0.0};
     for (int64_t e = threadIdx.x; e < entries; e += 256) {
@@ -308,6 +312,53 @@ __global__ void __launch_bounds__(256) decide_kernel(State* st, const double* __
   __syncthreads();
   if (threadIdx.x != 0) return;
 
+  if (mode == kDecideAdjInit || mode == kDecideAdjLayer) {
+    // ---- adjoint of the S0 recursion, run backwards over the stored states
+    if (st->timeout_flag) {
+      st->status = DMPT_ETIMEOUT;
+      st->done = 1;
+      return;
+    }
+    if (sums[1][kQBad] > 0.0) {
+      st->status = DMPT_ENUMERIC;
+      st->done = 1;
+      return;
+    }
+    int m;
+    if (mode == kDecideAdjInit) {
+      st->k = 1;
+      st->cur1[0] = 0;
+      st->plan_square = 0;
+      st->plan_write0 = 0;
+      for (int j = 0; j < kMaxK; ++j) st->plan_resp[j] = 0;
+      st->s1_fro2[0] = sums[1][kQFroNew];
+      st->s1_exp_cur[0] = st->precision == DMPT_DUAL_FP16
+                              ? fp16_exponent_for(sqrt(st->s1_fro2[0]))
+                              : 0;
+      m = st->d0_updates;
+    } else {
+      st->cur1[0] ^= 1;
+      st->s1_fro2[0] = sums[1][kQFroNew];
+      st->s1_exp_cur[0] = st->s1_exp_next[0];
+      m = st->adj_m - 1;
+    }
+    st->adj_m = m;
+    if (m <= 0) {
+      st->plan_resp[0] = 0;
+      st->status = DMPT_OK;
+      st->done = 1;
+      return;
+    }
+    // adjoint of layer m: Gbar <- sigma_m (S_{m-1} Gbar + Gbar S_{m-1}) + (1 - sigma_m) Gbar
+    st->z0_cur = st->tape_base + 2 * (m - 1);
+    st->sigma_cur = st->sigma[m];
+    st->plan_resp[0] = 1;
+    st->s1_exp_next[0] = st->precision == DMPT_DUAL_FP16
+                             ? fp16_exponent_for(4.5 * sqrt(st->s1_fro2[0]))
+                             : 0;
+    return;
+  }
+
   if (mode == kDecideInit) {
     if (!(st->epsN > st->eps1) || !isfinite(st->epsN) || !isfinite(st->eps1) ||
         sums[0][kQBad] > 0.0) {
@@ -319,6 +370,9 @@ __global__ void __launch_bounds__(256) decide_kernel(State* st, const double* __
     st->NX = sums[0][kQFroNew];
     st->s0_exp = st->precision == DMPT_DUAL_FP16 ? kFp16TargetExp - 1 : 0;
     st->cur0 = 0;
+    st->d0_updates = 0;
+    st->z0_cur = st->tape ? st->tape_base : zslice(0, 0, 0, st->layout_k);
+    st->z0_next = st->tape ? st->tape_base + 2 : zslice(1, 0, 0, st->layout_k);
     st->d0_conv = 0;
     st->d0_layer = 0;
     st->layers_run = 0;
@@ -357,6 +411,14 @@ __global__ void __launch_bounds__(256) decide_kernel(State* st, const double* __
       st->NS = sums[0][kQTrace];    // Tr S_n      (N_S of Alg. 2)
       st->NX = sums[0][kQFroNew];   // ||S_n||_F^2 = Tr S_n^2 (N_X of the next layer)
       st->cur0 ^= 1;
+      st->d0_updates += 1;
+      if (st->tape) {
+        st->z0_cur = st->z0_next;
+        st->z0_next += 2;
+      } else {
+        st->z0_cur = zslice(st->cur0, 0, 0, st->layout_k);
+        st->z0_next = zslice(st->cur0 ^ 1, 0, 0, st->layout_k);
+      }
     } else {
       st->froerr0 = sqrt(sums[0][kQFroDiff]);  // FroErr^(0) of Alg. 2
     }
@@ -608,14 +670,15 @@ __device__ __forceinline__ float from16(__nv_bfloat16 x) { return __bfloat162flo
 
 template <typename H16>
 __global__ void split_kernel(const State* st, const float* __restrict__ master, H16* ops,
-                             int64_t Np, int k) {
+                             int64_t Np, int k, int first_job) {
   const size_t mat = (size_t)Np * Np;
-  const int m = blockIdx.y;  // matrix: 0 = S0, 1 + j = S1_j
+  const int m = first_job + blockIdx.y;  // matrix: 0 = S0, 1 + j = S1_j
   const int cur = m == 0 ? st->cur0 : st->cur1[m - 1];
   const int e = m == 0 ? st->s0_exp : st->s1_exp_cur[m - 1];
   const float* src = master + (size_t)(cur * (1 + k) + m) * mat;
-  H16* hi = ops + ((size_t)(cur * (1 + k) + m) * 2 + 0) * mat;
-  H16* lo = ops + ((size_t)(cur * (1 + k) + m) * 2 + 1) * mat;
+  const int zh = m == 0 ? st->z0_cur : zslice(cur, m, 0, k);
+  H16* hi = ops + (size_t)zh * mat;
+  H16* lo = ops + (size_t)(zh + 1) * mat;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < mat;
        i += (size_t)gridDim.x * blockDim.x) {
     const float x = ldexpf(src[i], e);
@@ -625,17 +688,107 @@ __global__ void split_kernel(const State* st, const float* __restrict__ master, 
   }
 }
 
-cudaError_t launch_split(const Layout& L, void* ws, cudaStream_t s) {
+cudaError_t launch_split(const Layout& L, void* ws, int first_job, cudaStream_t s) {
   char* base = (char*)ws;
   const State* st = (const State*)(base + L.off_state);
-  dim3 grid(152 * 4, 1 + L.k);
+  dim3 grid(152 * 4, 1 + L.k - first_job);
   if (L.precision == DMPT_DUAL_FP16)
     split_kernel<__half><<<grid, 256, 0, s>>>(st, (const float*)(base + L.off_master),
-                                              (__half*)(base + L.off_ops16), L.Np, L.k);
+                                              (__half*)(base + L.off_ops16), L.Np, L.k,
+                                              first_job);
   else
     split_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(st, (const float*)(base + L.off_master),
                                                      (__nv_bfloat16*)(base + L.off_ops16),
-                                                     L.Np, L.k);
+                                                     L.Np, L.k, first_job);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the S0 recursion (backward pass of L = Tr[G P]).
+//   Gbar = (G + G^T) / 2 into response slot 1, buffer 0 (FP32 master), with
+//   ||Gbar||_F^2 partial sums; and at the end dL/dH = -Gbar / (eps_N - eps_1)
+//   (S0 = (eps_N I - H) / (eps_N - eps_1), bounds held fixed).
+
+__global__ void __launch_bounds__(256) adj_init_kernel(const double* __restrict__ G, float* master,
+                                                       int64_t n, int64_t Np, int64_t ld, int lk,
+                                                       double* partials, int64_t ptiles) {
+  __shared__ double up[32][33];
+  __shared__ double dn[32][33];
+  __shared__ double red[2 * 256];
+  const size_t mat = (size_t)Np * Np;
+  float* dst = master + (size_t)1 * mat;   // buffer 0, slot 1
+  (void)lk;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t TB = Np / 32;
+  const int64_t pairs = TB * (TB + 1) / 2;
+  double f = 0.0, bad = 0.0;
+  for (int64_t tp = blockIdx.x; tp < pairs; tp += gridDim.x) {
+    int64_t bj = (int64_t)((sqrt(8.0 * (double)tp + 1.0) - 1.0) * 0.5);
+    while ((bj + 1) * (bj + 2) / 2 <= tp) ++bj;
+    while (bj * (bj + 1) / 2 > tp) --bj;
+    const int64_t bi = tp - bj * (bj + 1) / 2;
+    for (int i = 0; i < 4; ++i) {
+      const int rl = ty + 8 * i;
+      const int64_t r = bi * 32 + rl, c = bj * 32 + tx;
+      const int64_t r2 = bj * 32 + rl, c2 = bi * 32 + tx;
+      up[rl][tx] = (r < n && c < n) ? G[r * ld + c] : 0.0;
+      dn[rl][tx] = (r2 < n && c2 < n) ? G[r2 * ld + c2] : 0.0;
+    }
+    __syncthreads();
+    for (int i = 0; i < 4; ++i) {
+      const int rl = ty + 8 * i;
+      const int64_t r = bi * 32 + rl, c = bj * 32 + tx;
+      // (G + G^T)/2 at (r, c): up[rl][tx] and the transposed element dn[tx][rl]
+      const float v = (float)(0.5 * (up[rl][tx] + dn[tx][rl]));
+      dst[(size_t)r * Np + c] = v;
+      const double wgt = bi < bj ? 2.0 : 1.0;
+      f += wgt * (double)v * (double)v;
+      if (!isfinite(v)) bad += 1.0;
+      if (bi < bj) {
+        const float vt = (float)(0.5 * (up[tx][rl] + dn[rl][tx]));
+        dst[(size_t)(bj * 32 + rl) * Np + bi * 32 + tx] = vt;
+      }
+    }
+    __syncthreads();
+  }
+  double v[2] = {f, bad};
+  block_sum<2, 256>(v, red);
+  if (threadIdx.x == 0) {
+    double* p = partials + ((size_t)1 * ptiles + blockIdx.x) * kNQ;
+    p[kQTrace] = 0.0;
+    p[kQFroNew] = v[0];
+    p[kQFroDiff] = 0.0;
+    p[kQBad] = v[1];
+  }
+}
+
+cudaError_t launch_adj_init(const Layout& L, void* ws, const double* G, int64_t ld, int blocks,
+                            cudaStream_t s) {
+  char* base = (char*)ws;
+  adj_init_kernel<<<blocks, 256, 0, s>>>(G, (float*)(base + L.off_master), L.n, L.Np, ld, L.k,
+                                         (double*)(base + L.off_partials), L.partial_tiles);
+  return cudaGetLastError();
+}
+
+__global__ void adj_finalize_kernel(const State* st, const float* __restrict__ master,
+                                    double* dLdH, int64_t n, int64_t Np, int64_t ld, int lk) {
+  const size_t mat = (size_t)Np * Np;
+  const float* src = master + (size_t)(st->cur1[0] * (1 + lk) + 1) * mat;
+  const double scale = -1.0 / (st->epsN - st->eps1);
+  const int64_t total = n * n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / n, c = i - r * n;
+    dLdH[r * ld + c] = scale * (double)src[(size_t)r * Np + c];
+  }
+}
+
+cudaError_t launch_adj_finalize(const Layout& L, void* ws, double* dLdH, int64_t ld,
+                                cudaStream_t s) {
+  char* base = (char*)ws;
+  adj_finalize_kernel<<<152 * 4, 256, 0, s>>>((const State*)(base + L.off_state),
+                                              (const float*)(base + L.off_master), dLdH, L.n,
+                                              L.Np, ld, L.k);
   return cudaGetLastError();
 }
 
@@ -645,6 +798,7 @@ cudaError_t launch_split(const Layout& L, void* ws, cudaStream_t s) {
 template <typename T>
 __global__ void finalize_kernel(const State* st, const T* __restrict__ master, double* P,
                                 double* P1, int64_t n, int64_t Np, int64_t ld, int k) {
+  // k: layout slots; grid.y = 1 + the number of directions written out
   const size_t mat = (size_t)Np * Np;
   const int m = blockIdx.y;
   if (m == 0 && P == nullptr) return;
@@ -660,10 +814,10 @@ __global__ void finalize_kernel(const State* st, const T* __restrict__ master, d
 }
 
 cudaError_t launch_finalize(const Layout& L, void* ws, double* P, double* P1, int64_t ld,
-                            cudaStream_t s) {
+                            int k_out, cudaStream_t s) {
   char* base = (char*)ws;
   const State* st = (const State*)(base + L.off_state);
-  dim3 grid(152 * 4, 1 + L.k);
+  dim3 grid(152 * 4, 1 + k_out);
   if (L.precision == DMPT_FP64)
     finalize_kernel<double><<<grid, 256, 0, s>>>(st, (const double*)(base + L.off_master), P,
                                                  P1, L.n, L.Np, ld, L.k);

@@ -260,8 +260,11 @@ __device__ __forceinline__ int job_at(uint32_t mask, int idx) {
   return __ffs(m) - 1;
 }
 
-__device__ __forceinline__ int zslice(int buf, int m, int part, int k) {
-  return (buf * (1 + k) + m) * 2 + part;
+// Operand slice of matrix m: S0 comes from the slice the control block
+// names (ping-pong slot, or a tape slice when the S0 states are kept for the
+// adjoint); S1_j from its ping-pong slot.
+__device__ __forceinline__ int zop(int m, int buf, int part, int k, int z0) {
+  return m == 0 ? z0 + part : zslice(buf, m, part, k);
 }
 
 template <bool BF16>
@@ -285,6 +288,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   const int sigma = st->sigma_cur;
   const int write0 = st->plan_write0;
   const int s0e = st->s0_exp;
+  const int z0c = st->z0_cur, z0n = st->z0_next;
 
   const int64_t tiles = num_tiles(Np);
   const int64_t items = tiles * njobs;
@@ -351,8 +355,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           // pass 0: A = S0 rows of I, B = S_job rows of J; pass 1: swapped
           const int mA = pass == 0 ? 0 : job, bufA = pass == 0 ? cur0 : curj;
           const int mB = pass == 0 ? job : 0, bufB = pass == 0 ? curj : cur0;
-          const int zAh = zslice(bufA, mA, 0, k), zAl = zslice(bufA, mA, 1, k);
-          const int zBh = zslice(bufB, mB, 0, k), zBl = zslice(bufB, mB, 1, k);
+          const int zAh = zop(mA, bufA, 0, k, z0c), zAl = zop(mA, bufA, 1, k, z0c);
+          const int zBh = zop(mB, bufB, 0, k, z0c), zBl = zop(mB, bufB, 1, k, z0c);
           for (int kb = 0; kb < kblocks; ++kb) {
             if (!mbar_wait(bar_empty + 8 * stage, phase ^ 1, limit_ns, abort_flag,
                            timeout_global)) {
@@ -519,8 +523,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const size_t row_off = (size_t)r * Np;
       const float* Sold = master + (size_t)(curj * (1 + k) + job) * mat + row_off;
       float* Snew = master + (size_t)((curj ^ 1) * (1 + k) + job) * mat;
-      H16* hi_new = reinterpret_cast<H16*>(ops) + (size_t)zslice(curj ^ 1, job, 0, k) * mat;
-      H16* lo_new = reinterpret_cast<H16*>(ops) + (size_t)zslice(curj ^ 1, job, 1, k) * mat;
+      const int zh_new = job == 0 ? z0n : zslice(curj ^ 1, job, 0, k);
+      H16* hi_new = reinterpret_cast<H16*>(ops) + (size_t)zh_new * mat;
+      H16* lo_new = reinterpret_cast<H16*>(ops) + (size_t)(zh_new + 1) * mat;
 
       // Partial norms in FP32 with compensation (GB300's FP64 rate is a small
       // fraction of its FP32 rate): ||S_new||^2 feeds the Alg. 2 test, so its
@@ -732,6 +737,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
   const int sigma = st->sigma_cur;
   const int write0 = st->plan_write0;
   const int s0e = st->s0_exp;
+  const int z0c = st->z0_cur, z0n = st->z0_next;
 
   const uint32_t rank = cluster_rank();
   const bool leader = rank == 0;
@@ -810,8 +816,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
           const int pass = rev ? passes - 1 - pp : pp;
           const int mA = pass == 0 ? 0 : job, bufA = pass == 0 ? cur0 : curj;
           const int mB = pass == 0 ? job : 0, bufB = pass == 0 ? curj : cur0;
-          const int zAh = zslice(bufA, mA, 0, k), zAl = zslice(bufA, mA, 1, k);
-          const int zBh = zslice(bufB, mB, 0, k), zBl = zslice(bufB, mB, 1, k);
+          const int zAh = zop(mA, bufA, 0, k, z0c), zAl = zop(mA, bufA, 1, k, z0c);
+          const int zBh = zop(mB, bufB, 0, k, z0c), zBl = zop(mB, bufB, 1, k, z0c);
           for (int kq = 0; kq < kblocks; ++kq) {
             const int kb = rev ? kblocks - 1 - kq : kq;
             if (!mbar_wait(bar_empty + 8 * stage, phase ^ 1, limit_ns, abort_flag,
@@ -967,8 +973,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
       const size_t row_off = (size_t)r * Np;
       const float* Sold = master + (size_t)(curj * (1 + k) + job) * mat + row_off;
       float* Snew = master + (size_t)((curj ^ 1) * (1 + k) + job) * mat;
-      H16* hi_new = reinterpret_cast<H16*>(ops) + (size_t)zslice(curj ^ 1, job, 0, k) * mat;
-      H16* lo_new = reinterpret_cast<H16*>(ops) + (size_t)zslice(curj ^ 1, job, 1, k) * mat;
+      const int zh_new = job == 0 ? z0n : zslice(curj ^ 1, job, 0, k);
+      H16* hi_new = reinterpret_cast<H16*>(ops) + (size_t)zh_new * mat;
+      H16* lo_new = reinterpret_cast<H16*>(ops) + (size_t)(zh_new + 1) * mat;
 
       float fn_s = 0.0f, fn_c = 0.0f, fd = 0.0f, trf = 0.0f;
       int bad = 0;
@@ -1113,7 +1120,7 @@ cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double ti
   using namespace tc;
   char* base = (char*)ws;
   const bool bf16 = L.precision == DMPT_DUAL_BF16;
-  const int slices = 2 * (1 + L.k) * 2;
+  const int slices = 2 * (1 + L.k) * 2 + 2 * L.tape_states;
   CUtensorMap mA, mB;
   if (!make_map(&mA, base + L.off_ops16, L.Np, slices, BM, bf16) ||
       !make_map(&mB, base + L.off_ops16, L.Np, slices, BN, bf16))

@@ -95,6 +95,9 @@ def load_library(path: str = LIB_PATH):
                                       ctypes.POINTER(DmptOptions), vp, vp,
                                       ctypes.POINTER(DmptInfo), vp, ctypes.c_size_t, vp]
     lib.dmpt_sp2_response.restype = c_int
+    lib.dmpt_sp2_backward.argtypes = [vp, vp, i64, i64, ctypes.POINTER(DmptOptions), vp, vp,
+                                      ctypes.c_size_t, vp]
+    lib.dmpt_sp2_backward.restype = c_int
     lib.dmpt_sp2_response_static.argtypes = [vp, vp, vp, c_int, i64, i64, i64,
                                              ctypes.POINTER(DmptOptions), vp, vp,
                                              ctypes.POINTER(DmptInfo), vp]
@@ -140,7 +143,7 @@ class Info:
 
 def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_scaling=1,
             sync_every=4, timing=False, timeout_s=2.0, accum_chunk=0,
-            cta_pair=1, k_snake=1) -> DmptOptions:
+            cta_pair=1, k_snake=1, ckpt_every=0) -> DmptOptions:
     lib = load_library()
     o = DmptOptions()
     lib.dmpt_default_options(ctypes.byref(o))
@@ -155,6 +158,7 @@ def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_s
     o.accum_chunk = int(accum_chunk)
     o.cta_pair = int(cta_pair)
     o.k_snake = int(k_snake)
+    o.ckpt_every = int(ckpt_every)
     return o
 
 
@@ -212,18 +216,21 @@ class Context:
         return eps
 
     def sp2_response(self, H, H1, n_occ: int, precision="dual_fp16", out=None,
-                     want_P=True, stream=None, raise_on_error=True, **kw):
+                     want_P=True, stream=None, raise_on_error=True, workspace=None, **kw):
         """P and P1 of (H, H1) by DNN-SP2-PT on the device.
 
-        H: (n, n) float64 CUDA tensor; H1: (n, n) or (k, n, n).  Returns
-        (P or None, P1 of shape (k, n, n), Info).
+        H: (n, n) float64 CUDA tensor; H1: (n, n), (k, n, n) or None (P only).
+        Returns (P or None, P1 of shape (k, n, n) or None, Info).  `workspace`
+        (a uint8 CUDA tensor) overrides the context's shared workspace.
         """
         import torch
-        if H.dtype != torch.float64 or H1.dtype != torch.float64:
-            raise TypeError("H and H1 must be float64")
-        if not (H.is_cuda and H1.is_cuda):
-            raise TypeError("H and H1 must be CUDA tensors")
+        if H.dtype != torch.float64 or not H.is_cuda:
+            raise TypeError("H must be a float64 CUDA tensor")
         n = H.shape[0]
+        if H1 is None:
+            H1 = torch.empty(0, n, n, dtype=torch.float64, device=H.device)
+        if H1.dtype != torch.float64 or not H1.is_cuda:
+            raise TypeError("H1 must be a float64 CUDA tensor")
         if H1.dim() == 2:
             H1 = H1.unsqueeze(0)
         k = H1.shape[0]
@@ -231,24 +238,49 @@ class Context:
         H1 = H1.contiguous()
         opts = options(precision=precision, **kw)
         if out is None:
-            P1 = torch.empty(k, n, n, dtype=torch.float64, device=H.device)
-            P = torch.empty(n, n, dtype=torch.float64, device=H.device) if want_P else None
+            P1 = torch.empty(k, n, n, dtype=torch.float64, device=H.device) if k else None
+            P = torch.empty(n, n, dtype=torch.float64, device=H.device) if (want_P or k == 0) else None
         else:
             P, P1 = out
         nbytes = self.workspace_size(n, k, opts)
         if nbytes == 0:
             raise DmptError(1, "invalid sizes or options")
-        ws_ptr, ws_len = self.workspace(nbytes)
+        if workspace is not None:
+            if workspace.numel() < nbytes + 256:
+                raise DmptError(2, "workspace tensor too small")
+            ws_ptr = workspace.data_ptr() + ((-workspace.data_ptr()) % 256)
+            ws_len = workspace.numel() - ((-workspace.data_ptr()) % 256)
+        else:
+            ws_ptr, ws_len = self.workspace(nbytes)
         info = DmptInfo()
         s = stream if stream is not None else torch.cuda.current_stream(H.device)
         st = self.lib.dmpt_sp2_response(
-            self.h, H.data_ptr(), H1.data_ptr(), k, n, n, int(n_occ), ctypes.byref(opts),
-            P.data_ptr() if P is not None else None, P1.data_ptr(), ctypes.byref(info),
+            self.h, H.data_ptr(), H1.data_ptr() if k else None, k, n, n, int(n_occ),
+            ctypes.byref(opts), P.data_ptr() if P is not None else None,
+            P1.data_ptr() if P1 is not None else None, ctypes.byref(info),
             ctypes.c_void_p(ws_ptr), ws_len, ctypes.c_void_p(s.cuda_stream))
         inf = Info.from_c(info, k)
         if st != 0 and raise_on_error:
             self._check(st)
         return P, P1, inf
+
+    def sp2_backward(self, G, workspace, out=None, stream=None, **kw):
+        """dL/dH of L = Tr[G P] for the forward run that filled `workspace`
+        (a uint8 CUDA tensor used with ckpt_every=1)."""
+        import torch
+        if G.dtype != torch.float64 or not G.is_cuda:
+            raise TypeError("G must be a float64 CUDA tensor")
+        G = G.contiguous()
+        n = G.shape[0]
+        dLdH = torch.empty_like(G) if out is None else out
+        opts = options(**kw)
+        ws_ptr = workspace.data_ptr() + ((-workspace.data_ptr()) % 256)
+        ws_len = workspace.numel() - ((-workspace.data_ptr()) % 256)
+        s = stream if stream is not None else torch.cuda.current_stream(G.device)
+        self._check(self.lib.dmpt_sp2_backward(self.h, G.data_ptr(), n, n, ctypes.byref(opts),
+                                               dLdH.data_ptr(), ctypes.c_void_p(ws_ptr), ws_len,
+                                               ctypes.c_void_p(s.cuda_stream)))
+        return dLdH
 
     def sp2_response_host(self, H_host, H1_host, n_occ: int, precision="dual_fp16",
                           stream=None, **kw):
@@ -278,3 +310,46 @@ def sp2_response(H, H1, n_occ, precision="dual_fp16", **kw):
 
 def bounds(H):
     return context(H.device.index or 0).bounds(H)
+
+
+def _autograd_function():
+    import torch
+
+    class SP2Density(torch.autograd.Function):
+        """P = theta(mu I - H) by DNN-SP2-PT with the hand-written adjoint.
+
+        forward(H, n_occ, precision): runs dmpt_sp2_response with k = 0 and
+        the S0 tape kept in a workspace owned by this node; backward(gP)
+        runs dmpt_sp2_backward on that tape.
+        """
+
+        @staticmethod
+        def forward(ctx, H, n_occ, precision="dual_fp16"):
+            c = context(H.device.index or 0)
+            opts = options(precision=precision, ckpt_every=1)
+            nbytes = c.workspace_size(H.shape[0], 0, opts)
+            ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=H.device)
+            P, _, info = c.sp2_response(H.detach(), None, n_occ, precision=precision,
+                                        ckpt_every=1, workspace=ws)
+            ctx.ws = ws
+            ctx.info = info
+            return P
+
+        @staticmethod
+        def backward(ctx, gP):
+            c = context(gP.device.index or 0)
+            dLdH = c.sp2_backward(gP.detach().to(torch.float64), ctx.ws)
+            return dLdH, None, None
+
+    return SP2Density
+
+
+_sp2_density = None
+
+
+def density(H, n_occ, precision="dual_fp16"):
+    """Differentiable P(H): torch.autograd-aware wrapper of the CUDA path."""
+    global _sp2_density
+    if _sp2_density is None:
+        _sp2_density = _autograd_function()
+    return _sp2_density.apply(H, n_occ, precision)

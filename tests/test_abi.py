@@ -73,8 +73,19 @@ def test_host_only_calls(lib):
     w3 = lib.dmpt_workspace_size(1000, 3, ctypes.byref(o))
     assert 0 < w1 < w3
     assert lib.dmpt_workspace_size(0, 1, ctypes.byref(o)) == 0
-    assert lib.dmpt_workspace_size(100, 0, ctypes.byref(o)) == 0
+    assert lib.dmpt_workspace_size(100, -1, ctypes.byref(o)) == 0
     assert lib.dmpt_workspace_size(100, 9, ctypes.byref(o)) == 0
+    # k = 0 (P only) is valid and smaller than k = 1
+    assert 0 < lib.dmpt_workspace_size(1000, 0, ctypes.byref(o)) < w1
+    # the S0 tape (ckpt_every = 1) adds (max_layers + 2) hi/lo states
+    t = dmpt.DmptOptions()
+    lib.dmpt_default_options(ctypes.byref(t))
+    t.ckpt_every = 1
+    t.max_layers = 50
+    wt = lib.dmpt_workspace_size(1000, 1, ctypes.byref(t))
+    assert wt - w1 >= 52 * 2 * 1024 * 1024 * 2
+    t.ckpt_every = 2
+    assert lib.dmpt_workspace_size(1000, 1, ctypes.byref(t)) == 0
     bad = dmpt.DmptOptions()
     lib.dmpt_default_options(ctypes.byref(bad))
     bad.precision = 9
