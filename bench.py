@@ -247,6 +247,8 @@ def main():
     ap.add_argument("--input-backend", default="torch", choices=["torch", "numpy"])
     ap.add_argument("--cta-pair", type=int, default=1, choices=[0, 1])
     ap.add_argument("--k-snake", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the adjoint measurement (n=4096 forward with tape + backward)")
     args = ap.parse_args()
     global INPUT_BACKEND
     INPUT_BACKEND = args.input_backend
@@ -354,6 +356,45 @@ def main():
     _, _, info = ctx.sp2_response(H, H1, inst.n_occ, **kw)
     torch.cuda.synchronize()
 
+    # ---- adjoint (L = Tr[G P]): n = 4096 forward with the S0 tape + backward
+    adjoint = None
+    if not args.no_adjoint and rank == 0:
+        from paper_2203_09621_gb300.workloads import make_workload
+        a_inst = make_workload(4, backend="torch", device=dev)
+        Ga = a_inst.H1[0]
+        aopts = dmpt.options(precision=args.precision, ckpt_every=1)
+        aws = torch.empty(ctx.workspace_size(a_inst.n, 0, aopts) + 256, dtype=torch.uint8,
+                          device=dev)
+        for _ in range(2):  # warm-up
+            ctx.sp2_response(a_inst.H, None, a_inst.n_occ, precision=args.precision,
+                             ckpt_every=1, workspace=aws)
+            ctx.sp2_backward(Ga, aws)
+        torch.cuda.synchronize()
+        t0, t1, t2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        t0.record(stream)
+        _, _, ainfo = ctx.sp2_response(a_inst.H, None, a_inst.n_occ, precision=args.precision,
+                                       ckpt_every=1, workspace=aws)
+        t1.record(stream)
+        dLdH = ctx.sp2_backward(Ga, aws)
+        t2.record(stream)
+        torch.cuda.synchronize()
+        na = float(a_inst.n)
+        U = ainfo.d0_layer - 1
+        f_fwd = ainfo.alg_flops
+        f_bwd = U * 3 * 2 * na ** 3       # one dual response product per adjoint layer
+        adjoint = {"workload": f"adjoint n={a_inst.n} (L = Tr[G P], G sym-Gauss)",
+                   "forward_ms": t0.elapsed_time(t1), "backward_ms": t1.elapsed_time(t2),
+                   "backward_tflops": f_bwd / (t1.elapsed_time(t2) * 1e-3) / 1e12,
+                   "forward_tflops": f_fwd / (t0.elapsed_time(t1) * 1e-3) / 1e12,
+                   "adjoint_layers": U}
+        if not args.no_check:
+            from oracle.sos import response_from_eigs
+            _, P1G = response_from_eigs(a_inst.eps.cpu().numpy(), a_inst.Q.cpu().numpy(),
+                                        Ga.cpu().numpy(), a_inst.n_occ)
+            g = dLdH.cpu().numpy()
+            adjoint["rel_err_vs_oracle"] = float(np.linalg.norm(g - P1G) / np.linalg.norm(P1G))
+        del aws, a_inst
+
     # ---- accuracy against the oracle (sampled columns, known eigenpairs)
     err = None
     if not args.no_check and rank == 0:
@@ -393,6 +434,7 @@ def main():
             "layers": infos[0].layers, "d0_layer": infos[0].d0_layer,
             "rel_err_P1_sampled": err,
             "forms": forms,
+            "adjoint": adjoint,
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": None,
                          "kernel": "layer_tc2_kernel" if args.cta_pair else "layer_tc_kernel",

@@ -17,6 +17,8 @@ Contents (all float64 numpy, plain and slow on purpose):
   (Sec. IV A).
 * ``sp2``: the paper's DNN-SP2-PT recursion in FP64, step by step in the
   order of Algorithms 1-3, and the hand-derived adjoint of that recursion.
+* ``scc``: the self-consistent-charge response (fixed point of
+  H1 = H1_ext + diag(gamma diag(P1))) by linear mixing.
 
 Parity status of each function is stated in its own docstring; every
 function here is pinned by a ``-m "not gpu"`` test that does not reuse the
@@ -26,6 +28,7 @@ function's own formula.
 from .gershgorin import gershgorin_bounds
 from .sos import density_matrix, response_sos, response_from_eigs
 from .sp2 import sp2_pt, SP2Result, sp2_adjoint
+from .scc import scc_response
 
 __all__ = [
     "gershgorin_bounds",
@@ -35,4 +38,5 @@ __all__ = [
     "sp2_pt",
     "SP2Result",
     "sp2_adjoint",
+    "scc_response",
 ]

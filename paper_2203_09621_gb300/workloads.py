@@ -46,6 +46,7 @@ __all__ = [
     "make_instance",
     "sym_gauss",
     "uneven_batch",
+    "scc_gamma",
 ]
 
 
@@ -195,3 +196,23 @@ def uneven_batch(count: int = 64, n_min: int = 256, n_max: int = 2048,
                                  (gap / 2, 2.0), "gauss", 1, 0.01, seed=seed + 1,
                                  backend=backend, device=device))
     return out
+
+
+def scc_gamma(n: int, seed: int = 1000 * 3 + 99, scale: float = 40.0,
+              backend: str = "numpy", device: str = "cpu"):
+    """SPD charge-coupling kernel for the self-consistent response.
+
+    gamma_ij = (scale / n) / sqrt(|x_i - x_j|^2 + 1) with orbital coordinates
+    x ~ U[0, 20]^3 from ``default_rng(seed)`` (by default the coordinates of
+    the dipole perturbations).  The inverse-multiquadric kernel
+    1/sqrt(r^2 + c^2) is strictly positive definite for distinct points, so
+    gamma is SPD; it decays like 1/r.  The 1/n factor keeps the coupling of
+    the induced charges of comparable strength across sizes.
+    """
+    xyz = np.random.default_rng(seed).uniform(0.0, 20.0, (n, 3))
+    d2 = ((xyz[:, None, :] - xyz[None, :, :]) ** 2).sum(-1)
+    g = (scale / n) / np.sqrt(d2 + 1.0)
+    if backend == "torch":
+        import torch
+        return torch.from_numpy(g).to(device)
+    return g
