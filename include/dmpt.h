@@ -189,6 +189,39 @@ dmpt_status dmpt_sp2_backward(dmpt_handle h, const double* G, int64_t n, int64_t
                               const dmpt_options* o, double* dLdH, void* workspace,
                               size_t ws_bytes, void* stream);
 
+/* First-order responses to new perturbations, reusing the S0 states that a
+ * preceding dmpt_sp2_response call with o->ckpt_every = 1 (dual precision)
+ * kept in `workspace`: only the response recursion of Sec. III A,
+ * Eq. (S_n detailed) with Eq. (dB), runs -- one response-type layer product
+ * per layer, no squares -- with the forward's branch sequence (continued by
+ * the sigma flip of Alg. 1 past the forward's last layer) and the Alg. 3
+ * test (C_pt, FroErr^(0) of the forward).  The forward's own H1 gives the
+ * forward's P1 bit for bit.
+ *   H1  device, k blocks of n x n (ld); k <= the forward's k (>= 1).
+ *   P1  device, k blocks of n x n (ld) outputs.
+ * The forward's response slots are overwritten; the tape is kept. */
+dmpt_status dmpt_response_replay(dmpt_handle h, const double* H1, int k, int64_t n,
+                                 int64_t ld, const dmpt_options* o, double* P1, dmpt_info* info,
+                                 void* workspace, size_t ws_bytes, void* stream);
+
+/* Self-consistent first-order response (self-consistent-charge coupling,
+ * Sec. III A; the paper skips this step for its DFTB examples, Sec. IV B):
+ * the fixed point of
+ *   H1_eff = H1_ext + diag(gamma q),  q = diag(P1),  P1 = R(H1_eff),
+ * with R the response of the forward run whose S0 tape is in `workspace`
+ * (as for dmpt_response_replay) and gamma an SPD coupling (device n x n,
+ * ld).  Linear mixing of the induced charges: q <- (1 - mixing) q +
+ * mixing diag(P1), until max_j ||diag(P1_j) - q_j|| / ||diag(P1_j)|| < tol
+ * (mixing in (0, 1]); each iteration is one response replay.
+ *   iterations, residual: host outputs (may be NULL).
+ * Returns DMPT_ENOTCONV when max_iter iterations do not reach tol (P1 holds
+ * the last iterate).  Synchronises `stream` once per iteration. */
+dmpt_status dmpt_scc_response(dmpt_handle h, const double* H1_ext, const double* gamma, int k,
+                              int64_t n, int64_t ld, const dmpt_options* o, double tol,
+                              int max_iter, double mixing, double* P1, dmpt_info* info,
+                              int* iterations, double* residual, void* workspace,
+                              size_t ws_bytes, void* stream);
+
 /* Static-scratch variant of dmpt_sp2_response for callers that cannot
  * allocate device memory (a host framework that owns every allocation, code
  * that must not allocate after start-up, plug-ins that only get input and

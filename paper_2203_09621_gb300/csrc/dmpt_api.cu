@@ -100,6 +100,108 @@ __global__ void adj_state_reset_kernel(State* st) {
   st->timeout_flag = 0;
 }
 
+__global__ void replay_reset_kernel(State* st, int k) {
+  st->done = 0;
+  st->status = DMPT_OK;
+  st->timeout_flag = 0;
+  st->k = k;
+}
+
+// Read the control block a forward run left in `workspace` and check that it
+// holds an S0 tape of a converged dual-precision run of size n.
+dmpt_status read_forward_state(dmpt_handle h, void* workspace, size_t ws_bytes, int64_t n,
+                               cudaStream_t s, State* out, const char* who) {
+  if (!workspace || ((uintptr_t)workspace) % 256 || ws_bytes < sizeof(State))
+    return fail(h, DMPT_EWORKSPACE, "%s: workspace missing or misaligned", who);
+  cudaError_t e = cudaMemcpyAsync(out, workspace, sizeof(State), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, who);
+  if (out->tape != 1 || out->n != n || !out->done || out->d0_updates < 0 ||
+      out->d0_updates + 1 > out->tape_states ||
+      (out->precision != DMPT_DUAL_FP16 && out->precision != DMPT_DUAL_BF16))
+    return fail(h, DMPT_EINVAL,
+                "%s: the workspace holds no S0 tape of a dual-precision forward run of this n "
+                "(run dmpt_sp2_response with ckpt_every = 1 first)", who);
+  if (out->d0_layer < 1) return fail(h, DMPT_EINVAL, "%s: the forward run did not converge", who);
+  const Layout L = make_layout(n, out->layout_k, out->precision, out->tape_states);
+  if (ws_bytes < L.total) return fail(h, DMPT_EWORKSPACE, "%s: workspace too small", who);
+  return DMPT_OK;
+}
+
+// The response recursion replayed over the stored S0 states for new
+// perturbations H1_j (+ diag(shift_j)); writes P1 and fills info.
+dmpt_status replay_run(dmpt_handle h, const Layout& L, const double* H1, const double* shift,
+                       int k, int64_t ld, const dmpt_options* o, double* P1, dmpt_info* info,
+                       void* workspace, cudaStream_t s) {
+  State* st = (State*)workspace;
+  cudaError_t e;
+  const int blocks = 1024;
+  replay_reset_kernel<<<1, 1, 0, s>>>(st, k);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "replay reset");
+  if ((e = launch_init(L, workspace, nullptr, H1, ld, k, blocks, s, 1, shift)) != cudaSuccess)
+    return cuda_fail(h, e, "replay init");
+  if ((e = launch_decide(L, workspace, kDecideReplayInit, blocks, s)) != cudaSuccess)
+    return cuda_fail(h, e, "replay decide");
+  if ((e = launch_split(L, workspace, 1, s)) != cudaSuccess) return cuda_fail(h, e, "replay split");
+  int launched = 0, done = 0;
+  int64_t entries = 0;
+  double pass_flops = 0.0;
+  while (launched < o->max_layers && !done) {
+    for (int j = 0; j < o->sync_every && launched < o->max_layers; ++j) {
+      if ((e = launch_layer_tc(L, workspace, s, o->timeout_s, o->accum_chunk, o->cta_pair,
+                               o->k_snake, &entries, &pass_flops)) != cudaSuccess)
+        return cuda_fail(h, e, "replay layer");
+      if ((e = launch_decide(L, workspace, kDecideReplayLayer, entries, s)) != cudaSuccess)
+        return cuda_fail(h, e, "replay decide");
+      ++launched;
+    }
+    if ((e = cudaMemcpyAsync(&done, &st->done, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
+        cudaSuccess)
+      return cuda_fail(h, e, "replay poll");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(h, e, "replay loop");
+  }
+  if ((e = launch_finalize(L, workspace, nullptr, P1, ld, k, s)) != cudaSuccess)
+    return cuda_fail(h, e, "replay finalize");
+  State* hs = new State;
+  e = cudaMemcpyAsync(hs, st, sizeof(State), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    delete hs;
+    return cuda_fail(h, e, "replay state");
+  }
+  dmpt_status status = hs->done ? (dmpt_status)hs->status : DMPT_ENOTCONV;
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->status = status;
+    info->layers = hs->rp_layers;
+    info->d0_layer = hs->d0_layer;
+    bool all1 = true;
+    double alg = 0.0;
+    for (int j = 0; j < k; ++j) {
+      info->d1_layer[j] = hs->d1_layer[j];
+      all1 = all1 && hs->d1_conv[j];
+      const int last = hs->d1_conv[j] ? hs->d1_layer[j] : hs->rp_layers;
+      info->froerr1[j] = (last >= 1 && last <= DMPT_MAX_LAYERS) ? hs->froerr1[j][last] : 0.0;
+    }
+    for (int m = 1; m <= hs->rp_layers; ++m) {
+      int active = 0;
+      for (int j = 0; j < k; ++j) active += (hs->d1_conv[j] ? m <= hs->d1_layer[j] : true) ? 1 : 0;
+      alg += 3.0 * active * 2.0 * (double)L.n * L.n * L.n;
+      info->mma_flops += active * 6.0 * pass_flops;
+    }
+    info->alg_flops = alg;
+    info->converged = (status == DMPT_OK && all1) ? 1 : 0;
+    info->eps_min = hs->eps1;
+    info->eps_max = hs->epsN;
+    info->froerr0 = hs->froerr0;
+    info->product_launches = launched;
+    for (int m = 1; m <= hs->rp_layers && m <= DMPT_MAX_LAYERS; ++m) info->sigma[m - 1] = hs->sigma[m];
+  }
+  delete hs;
+  if (status != DMPT_OK) return fail(h, status, "response replay: device status %s", "");
+  return DMPT_OK;
+}
+
 double layer_alg_flops(double n, int prec, bool square, int active) {
   const double n3x2 = 2.0 * n * n * n;
   if (prec >= DMPT_DUAL_FP16) return ((square ? 2.0 : 0.0) + 3.0 * active) * n3x2;
@@ -410,6 +512,106 @@ dmpt_status dmpt_sp2_backward(dmpt_handle h, const double* G, int64_t n, int64_t
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(h, e, "dmpt_sp2_backward");
   if (status != DMPT_OK) return fail(h, (dmpt_status)status, "dmpt_sp2_backward: device status%s");
+  return DMPT_OK;
+}
+
+dmpt_status dmpt_response_replay(dmpt_handle h, const double* H1, int k, int64_t n,
+                                 int64_t ld, const dmpt_options* o, double* P1, dmpt_info* info,
+                                 void* workspace, size_t ws_bytes, void* stream) {
+  if (!h) return DMPT_EINVAL;
+  h->err[0] = 0;
+  dmpt_options defaults;
+  dmpt_default_options(&defaults);
+  if (!o) o = &defaults;
+  if (info) memset(info, 0, sizeof(*info));
+  if (!H1 || !P1) return fail(h, DMPT_EINVAL, "dmpt_response_replay: null %s", "H1/P1");
+  if (n < 1 || ld < n || k < 1 || k > DMPT_MAX_K)
+    return fail(h, DMPT_EINVAL, "dmpt_response_replay: bad n, ld or k%s");
+  if (!valid_options(o)) return fail(h, DMPT_EINVAL, "dmpt_response_replay: invalid options%s");
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceGuard g(h->device);
+  State fs;
+  dmpt_status st = read_forward_state(h, workspace, ws_bytes, n, s, &fs, "dmpt_response_replay");
+  if (st != DMPT_OK) return st;
+  if (k > fs.layout_k)
+    return fail(h, DMPT_EINVAL, "dmpt_response_replay: k exceeds the forward's response slots%s");
+  const Layout L = make_layout(n, fs.layout_k, fs.precision, fs.tape_states);
+  return replay_run(h, L, H1, nullptr, k, ld, o, P1, info, workspace, s);
+}
+
+dmpt_status dmpt_scc_response(dmpt_handle h, const double* H1_ext, const double* gamma, int k,
+                              int64_t n, int64_t ld, const dmpt_options* o, double tol,
+                              int max_iter, double mixing, double* P1, dmpt_info* info,
+                              int* iterations, double* residual, void* workspace,
+                              size_t ws_bytes, void* stream) {
+  if (!h) return DMPT_EINVAL;
+  h->err[0] = 0;
+  dmpt_options defaults;
+  dmpt_default_options(&defaults);
+  if (!o) o = &defaults;
+  if (!H1_ext || !gamma || !P1) return fail(h, DMPT_EINVAL, "dmpt_scc_response: null %s", "input");
+  if (n < 1 || ld < n || k < 1 || k > DMPT_MAX_K || max_iter < 1 || !(tol > 0.0) ||
+      !(mixing > 0.0 && mixing <= 1.0))
+    return fail(h, DMPT_EINVAL, "dmpt_scc_response: bad n, ld, k, tol, max_iter or mixing%s");
+  if (!valid_options(o)) return fail(h, DMPT_EINVAL, "dmpt_scc_response: invalid options%s");
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceGuard g(h->device);
+  State fs;
+  dmpt_status st = read_forward_state(h, workspace, ws_bytes, n, s, &fs, "dmpt_scc_response");
+  if (st != DMPT_OK) return st;
+  if (k > fs.layout_k)
+    return fail(h, DMPT_EINVAL, "dmpt_scc_response: k exceeds the forward's response slots%s");
+  const Layout L = make_layout(n, fs.layout_k, fs.precision, fs.tape_states);
+  double* q = (double*)((char*)workspace + L.off_vec);
+  double* v = q + (size_t)k * n;
+  double* red = v + (size_t)k * n;
+  cudaError_t e = cudaMemsetAsync(q, 0, (size_t)k * n * sizeof(double), s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "scc reset");
+  double res = INFINITY;
+  int it = 0;
+  std::vector<double> hred(4 * (size_t)k);
+  dmpt_info acc;
+  memset(&acc, 0, sizeof(acc));
+  for (it = 1; it <= max_iter; ++it) {
+    // H1_eff = H1_ext + diag(gamma q_in)
+    if (it > 1 && (e = launch_scc_potential(gamma, n, ld, q, v, k, s)) != cudaSuccess)
+      return cuda_fail(h, e, "scc potential");
+    dmpt_info ri;
+    st = replay_run(h, L, H1_ext, it > 1 ? v : nullptr, k, ld, o, P1, &ri, workspace, s);
+    if (st != DMPT_OK) return st;
+    acc.alg_flops += ri.alg_flops;
+    acc.mma_flops += ri.mma_flops;
+    acc.product_launches += ri.product_launches;
+    acc.layers = ri.layers;
+    acc.d0_layer = ri.d0_layer;
+    for (int j = 0; j < k; ++j) {
+      acc.d1_layer[j] = ri.d1_layer[j];
+      acc.froerr1[j] = ri.froerr1[j];
+    }
+    acc.eps_min = ri.eps_min;
+    acc.eps_max = ri.eps_max;
+    acc.froerr0 = ri.froerr0;
+    // q_out = diag(P1); residual; q_in <- (1 - mixing) q_in + mixing q_out
+    if ((e = launch_scc_mix(P1, n, ld, q, k, mixing, red, s)) != cudaSuccess)
+      return cuda_fail(h, e, "scc mix");
+    e = cudaMemcpyAsync(hred.data(), red, 4 * (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "scc residual");
+    res = 0.0;
+    for (int j = 0; j < k; ++j) {
+      const double r = sqrt(hred[4 * j] / (hred[4 * j + 1] > 0.0 ? hred[4 * j + 1] : 1e-300));
+      res = r > res ? r : res;
+    }
+    if (!(res == res)) return fail(h, DMPT_ENUMERIC, "dmpt_scc_response: non-finite residual%s");
+    if (res < tol) break;
+  }
+  if (it > max_iter) it = max_iter;
+  if (iterations) *iterations = it;
+  if (residual) *residual = res;
+  acc.status = res < tol ? DMPT_OK : DMPT_ENOTCONV;
+  acc.converged = res < tol ? 1 : 0;
+  if (info) *info = acc;
+  if (res >= tol) return fail(h, DMPT_ENOTCONV, "dmpt_scc_response: max_iter reached%s");
   return DMPT_OK;
 }
 

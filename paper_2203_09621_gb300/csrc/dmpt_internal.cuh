@@ -55,7 +55,8 @@ struct State {
   int layout_k;         // response slots in the workspace layout
   int k_fwd;            // directions of the forward run
   int adj_m;            // adjoint: layer whose adjoint runs next
-  int pad1;
+  int rp_lmax;          // replay: last layer whose sigma the forward recorded
+  int rp_layers;        // replay: layers run
   int64_t n;
   int cur1[kMaxK];
   int d1_conv[kMaxK];
@@ -80,7 +81,7 @@ struct Layout {
   int precision;
   int tape_states;        // 16-bit S0 copies kept for the adjoint (0: none)
   size_t elem;            // bytes per master element (8 or 4)
-  size_t off_state, off_partials, off_master, off_ops16, total;
+  size_t off_state, off_partials, off_master, off_ops16, off_vec, total;
   int64_t partial_tiles;  // entries per job in the partials array
 };
 
@@ -101,8 +102,17 @@ inline int64_t upper_tiles(int64_t Np, int bt) {
 // ---- launchers (kernels_simt.cu) ----
 cudaError_t launch_bounds(const double* H, int64_t n, int64_t ld, double* eps_out,
                           cudaStream_t s);
+// first_m = 0: S0 and S1_1..k; first_m = 1: S1 only (response replay), each
+// S1_j = -(H1_j + diag(shift_j)) / (eps_N - eps_1) (shift: k x n or NULL).
 cudaError_t launch_init(const Layout& L, void* ws, const double* H, const double* H1,
-                        int64_t ld, int k, int blocks, cudaStream_t s);
+                        int64_t ld, int k, int blocks, cudaStream_t s, int first_m = 0,
+                        const double* shift = nullptr);
+// self-consistent response: v_j = gamma q_j;  q_j <- (1 - alpha) q_j + alpha diag(P1_j)
+// with red[j] = {||diag(P1_j) - q_j||^2, ||diag(P1_j)||^2}
+cudaError_t launch_scc_potential(const double* gamma, int64_t n, int64_t ld, const double* q,
+                                 double* v, int k, cudaStream_t s);
+cudaError_t launch_scc_mix(const double* P1, int64_t n, int64_t ld, double* q, int k,
+                           double alpha, double* red, cudaStream_t s);
 cudaError_t launch_decide(const Layout& L, void* ws, int mode, int64_t entries,
                           cudaStream_t s);
 // Layer-product launchers.  *entries: partial-sum entries per job (tiles);
@@ -128,7 +138,14 @@ cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double ti
                             double* pass_flops);
 int tc_tile();
 
-enum DecideMode { kDecideInit = 0, kDecideLayer = 1, kDecideAdjInit = 2, kDecideAdjLayer = 3 };
+enum DecideMode {
+  kDecideInit = 0,
+  kDecideLayer = 1,
+  kDecideAdjInit = 2,
+  kDecideAdjLayer = 3,
+  kDecideReplayInit = 4,
+  kDecideReplayLayer = 5
+};
 
 // CUDA device of a handle (-1 for NULL).
 int handle_device(dmpt_handle h);

@@ -41,6 +41,9 @@ Layout make_layout(int64_t n, int k, int precision, int tape_states) {
   } else {
     L.off_ops16 = 0;
   }
+  // small vectors of the self-consistent response: q[k][n], v[k][n], red[k][4]
+  L.off_vec = off;
+  off = align256(off + ((size_t)(k > 0 ? k : 1) * (2 * (size_t)n + 4)) * sizeof(double));
   L.total = off;
   return L;
 }
@@ -139,6 +142,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const double* __restrict__ H,
                                                    const double* __restrict__ H1, int64_t n,
                                                    int64_t Np, int64_t ld, int k, int lk,
+                                                   int first_m, const double* __restrict__ shift,
                                                    double* partials, int64_t ptiles) {
   // 32 x 32 tile pairs (bi <= bj): the upper tile is read row-wise (coalesced),
   // written in place and, through shared memory, transposed into the mirror
@@ -161,14 +165,15 @@ __global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const d
     while ((bj + 1) * (bj + 2) / 2 <= tp) ++bj;
     while (bj * (bj + 1) / 2 > tp) --bj;
     const int64_t bi = tp - bj * (bj + 1) / 2;
-    for (int m = 0; m <= k; ++m) {
+    for (int m = first_m; m <= k; ++m) {
       const double* src = m == 0 ? H : H1 + (size_t)(m - 1) * n * ld;
       for (int i = 0; i < 4; ++i) {
         const int rl = ty + 8 * i;
         const int64_t r = bi * 32 + rl, c = bj * 32 + tx;
         double v = 0.0;
         if (r < n && c < n) {
-          const double h = src[r * ld + c];
+          double h = src[r * ld + c];
+          if (m > 0 && shift != nullptr && r == c) h += shift[(size_t)(m - 1) * n + r];
           v = m == 0 ? ((r == c ? eN : 0.0) - h) * w : -h * w;
         }
         tile[rl][tx] = (double)(T)v;   // the stored (rounded) value
@@ -195,15 +200,19 @@ __global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const d
       __syncthreads();
     }
   }
-  // job 0: trace, fro, bad
+  // job 0: trace, fro, bad (bad of the S1 part is reported under job 1 in replay)
   {
     double v[3] = {tr, f0, bad};
     block_sum<3, 256>(v, red);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && first_m == 0) {
       double* p = partials + ((size_t)0 * ptiles + blockIdx.x) * kNQ;
       p[kQTrace] = v[0];
       p[kQFroNew] = v[1];
       p[kQFroDiff] = 0.0;
+      p[kQBad] = v[2];
+    }
+    if (threadIdx.x == 0 && first_m == 1 && k > 0) {
+      double* p = partials + ((size_t)1 * ptiles + blockIdx.x) * kNQ;
       p[kQBad] = v[2];
     }
   }
@@ -215,22 +224,85 @@ __global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const d
       p[kQTrace] = 0.0;
       p[kQFroNew] = v[0];
       p[kQFroDiff] = 0.0;
-      p[kQBad] = 0.0;
+      if (!(first_m == 1 && j == 0)) p[kQBad] = 0.0;
     }
   }
 }
 
 cudaError_t launch_init(const Layout& L, void* ws, const double* H, const double* H1,
-                        int64_t ld, int k, int blocks, cudaStream_t s) {
+                        int64_t ld, int k, int blocks, cudaStream_t s, int first_m,
+                        const double* shift) {
   char* base = (char*)ws;
   State* st = (State*)(base + L.off_state);
   double* partials = (double*)(base + L.off_partials);
   if (L.precision == DMPT_FP64)
     init_kernel<double><<<blocks, 256, 0, s>>>(st, (double*)(base + L.off_master), H, H1, L.n,
-                                               L.Np, ld, k, L.k, partials, L.partial_tiles);
+                                               L.Np, ld, k, L.k, first_m, shift, partials,
+                                               L.partial_tiles);
   else
     init_kernel<float><<<blocks, 256, 0, s>>>(st, (float*)(base + L.off_master), H, H1, L.n,
-                                              L.Np, ld, k, L.k, partials, L.partial_tiles);
+                                              L.Np, ld, k, L.k, first_m, shift, partials,
+                                              L.partial_tiles);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Self-consistent response: charge potential and linear mixing of the
+// induced charges q = diag(P1).
+
+// v_j[r] = sum_c gamma[r][c] q_j[c]; one warp per row, FP64
+__global__ void scc_potential_kernel(const double* __restrict__ gamma, int64_t n, int64_t ld,
+                                     const double* __restrict__ q, double* v, int k) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < n; r += nw) {
+    const double* g = gamma + r * ld;
+    for (int j = 0; j < k; ++j) {
+      const double* qj = q + (size_t)j * n;
+      double acc = 0.0;
+      for (int64_t c = lane; c < n; c += 32) acc = fma(g[c], qj[c], acc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) v[(size_t)j * n + r] = acc;
+    }
+  }
+}
+
+cudaError_t launch_scc_potential(const double* gamma, int64_t n, int64_t ld, const double* q,
+                                 double* v, int k, cudaStream_t s) {
+  int64_t warps = n < 152 * 32 ? n : 152 * 32;
+  scc_potential_kernel<<<(int)((warps * 32 + 255) / 256), 256, 0, s>>>(gamma, n, ld, q, v, k);
+  return cudaGetLastError();
+}
+
+// one block per direction: red[j] = {||diag(P1_j) - q_j||^2, ||diag(P1_j)||^2}, then mix
+__global__ void __launch_bounds__(256) scc_mix_kernel(const double* __restrict__ P1, int64_t n,
+                                                      int64_t ld, double* q, double alpha,
+                                                      double* red) {
+  __shared__ double sm[2 * 256];
+  const int j = blockIdx.x;
+  const double* p = P1 + (size_t)j * n * ld;
+  double* qj = q + (size_t)j * n;
+  double d2 = 0.0, o2 = 0.0;
+  for (int64_t r = threadIdx.x; r < n; r += 256) {
+    const double qo = p[r * ld + r];
+    const double d = qo - qj[r];
+    d2 += d * d;
+    o2 += qo * qo;
+    qj[r] = (1.0 - alpha) * qj[r] + alpha * qo;
+  }
+  double v[2] = {d2, o2};
+  block_sum<2, 256>(v, sm);
+  if (threadIdx.x == 0) {
+    red[4 * j + 0] = v[0];
+    red[4 * j + 1] = v[1];
+  }
+}
+
+cudaError_t launch_scc_mix(const double* P1, int64_t n, int64_t ld, double* q, int k,
+                           double alpha, double* red, cudaStream_t s) {
+  scc_mix_kernel<<<k, 256, 0, s>>>(P1, n, ld, q, alpha, red);
   return cudaGetLastError();
 }
 
@@ -285,17 +357,44 @@ __device__ void plan_layer(State* st, int n) {
   st->n_layer = n;
 }
 
+// Plan layer m of a response replay: S0 operand = stored state
+// min(m - 1, U), the forward's sigma_m (continued by flips past the forward's
+// last layer), responses of the directions still running.
+__device__ void plan_replay(State* st, int m) {
+  const int U = st->d0_updates;
+  st->z0_cur = st->tape_base + 2 * (m - 1 < U ? m - 1 : U);
+  if (m > st->rp_lmax) st->sigma[m] = (signed char)(-st->sigma[m - 1]);
+  st->sigma_cur = st->sigma[m];
+  st->plan_square = 0;
+  st->plan_write0 = 0;
+  for (int j = 0; j < st->k; ++j) {
+    st->plan_resp[j] = !st->d1_conv[j];
+    st->s1_exp_next[j] = st->precision == DMPT_DUAL_FP16
+                             ? fp16_exponent_for(4.5 * sqrt(st->s1_fro2[j]))
+                             : 0;
+  }
+  st->n_layer = m;
+}
+
 __global__ void __launch_bounds__(256) decide_kernel(State* st, const double* __restrict__ partials,
                                                      int64_t ptiles, int64_t entries, int mode) {
   __shared__ double red[kNQ * 256];
   __shared__ double sums[kMaxK + 1][kNQ];
   if (st->done) return;
   const bool adj = mode == kDecideAdjInit || mode == kDecideAdjLayer;
+  const bool rp = mode == kDecideReplayInit || mode == kDecideReplayLayer;
   const int k = adj ? 1 : st->k;
   for (int job = 0; job <= k; ++job) {
-    const bool ran = adj ? job == 1
-                         : (mode == kDecideInit ||
-                            (job == 0 ? st->plan_square != 0 : st->plan_resp[job - 1] != 0));
+    bool ran;
+    if (adj)
+      ran = job == 1;
+    else if (mode == kDecideInit)
+      ran = true;
+    else if (mode == kDecideReplayInit)
+      ran = job >= 1;
+    else
+      ran = job == 0 ? st->plan_square != 0 : st->plan_resp[job - 1] != 0;
+    (void)rp;
     if (!ran) continue;  // uniform across the block
     double v[kNQ] = {0.0, 0.0, 0.0, 0.0};
     for (int64_t e = threadIdx.x; e < entries; e += 256) {
@@ -311,6 +410,69 @@ __global__ void __launch_bounds__(256) decide_kernel(State* st, const double* __
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
+
+  if (mode == kDecideReplayInit || mode == kDecideReplayLayer) {
+    // ---- response recursion replayed over the stored S0 states
+    if (st->timeout_flag) {
+      st->status = DMPT_ETIMEOUT;
+      st->done = 1;
+      return;
+    }
+    double bad = 0.0;
+    for (int j = 0; j < k; ++j)
+      if (mode == kDecideReplayInit || st->plan_resp[j]) bad += sums[1 + j][kQBad];
+    if (bad > 0.0) {
+      st->status = DMPT_ENUMERIC;
+      st->done = 1;
+      return;
+    }
+    if (mode == kDecideReplayInit) {
+      for (int j = 0; j < k; ++j) {
+        st->cur1[j] = 0;
+        st->d1_conv[j] = 0;
+        st->d1_layer[j] = 0;
+        st->s1_fro2[j] = sums[1 + j][kQFroNew];
+        st->s1_exp_cur[j] = st->precision == DMPT_DUAL_FP16
+                                ? fp16_exponent_for(sqrt(st->s1_fro2[j]))
+                                : 0;
+      }
+      st->rp_lmax = st->layers_run;
+      st->rp_layers = 0;
+      plan_replay(st, 1);
+      return;
+    }
+    const int n = st->n_layer;
+    for (int j = 0; j < k; ++j) {
+      if (!st->plan_resp[j]) continue;
+      const double fe = sqrt(sums[1 + j][kQFroDiff]);
+      st->froerr1[j][n] = fe;
+      const bool fired = n - 2 >= st->d0_layer &&
+                         fe >= st->c_pt * st->froerr0 * st->froerr1[j][n - 2];
+      if (fired) {
+        st->d1_conv[j] = 1;
+        st->d1_layer[j] = n;
+      } else {
+        st->cur1[j] ^= 1;
+        st->s1_fro2[j] = sums[1 + j][kQFroNew];
+        st->s1_exp_cur[j] = st->s1_exp_next[j];
+      }
+    }
+    st->rp_layers = n;
+    bool all1 = true;
+    for (int j = 0; j < k; ++j) all1 = all1 && st->d1_conv[j];
+    if (all1) {
+      st->status = DMPT_OK;
+      st->done = 1;
+      return;
+    }
+    if (n + 1 > st->max_layers) {
+      st->status = DMPT_ENOTCONV;
+      st->done = 1;
+      return;
+    }
+    plan_replay(st, n + 1);
+    return;
+  }
 
   if (mode == kDecideAdjInit || mode == kDecideAdjLayer) {
     // ---- adjoint of the S0 recursion, run backwards over the stored states

@@ -98,6 +98,14 @@ def load_library(path: str = LIB_PATH):
     lib.dmpt_sp2_backward.argtypes = [vp, vp, i64, i64, ctypes.POINTER(DmptOptions), vp, vp,
                                       ctypes.c_size_t, vp]
     lib.dmpt_sp2_backward.restype = c_int
+    lib.dmpt_response_replay.argtypes = [vp, vp, c_int, i64, i64, ctypes.POINTER(DmptOptions),
+                                         vp, ctypes.POINTER(DmptInfo), vp, ctypes.c_size_t, vp]
+    lib.dmpt_response_replay.restype = c_int
+    lib.dmpt_scc_response.argtypes = [vp, vp, vp, c_int, i64, i64, ctypes.POINTER(DmptOptions),
+                                      ctypes.c_double, c_int, ctypes.c_double, vp,
+                                      ctypes.POINTER(DmptInfo), ctypes.POINTER(c_int),
+                                      ctypes.POINTER(ctypes.c_double), vp, ctypes.c_size_t, vp]
+    lib.dmpt_scc_response.restype = c_int
     lib.dmpt_sp2_response_static.argtypes = [vp, vp, vp, c_int, i64, i64, i64,
                                              ctypes.POINTER(DmptOptions), vp, vp,
                                              ctypes.POINTER(DmptInfo), vp]
@@ -281,6 +289,57 @@ class Context:
                                                dLdH.data_ptr(), ctypes.c_void_p(ws_ptr), ws_len,
                                                ctypes.c_void_p(s.cuda_stream)))
         return dLdH
+
+    @staticmethod
+    def _ws_ptr(workspace):
+        off = (-workspace.data_ptr()) % 256
+        return workspace.data_ptr() + off, workspace.numel() - off
+
+    def response_replay(self, H1, workspace, out=None, stream=None, **kw):
+        """P1 for new perturbations H1 ((n, n) or (k, n, n)) from the S0 tape
+        of the forward run that filled `workspace` (ckpt_every=1)."""
+        import torch
+        if H1.dim() == 2:
+            H1 = H1.unsqueeze(0)
+        H1 = H1.contiguous()
+        k, n = H1.shape[0], H1.shape[1]
+        P1 = torch.empty_like(H1) if out is None else out
+        opts = options(**kw)
+        info = DmptInfo()
+        ptr, ln = self._ws_ptr(workspace)
+        s = stream if stream is not None else torch.cuda.current_stream(H1.device)
+        self._check(self.lib.dmpt_response_replay(self.h, H1.data_ptr(), k, n, n,
+                                                  ctypes.byref(opts), P1.data_ptr(),
+                                                  ctypes.byref(info), ctypes.c_void_p(ptr), ln,
+                                                  ctypes.c_void_p(s.cuda_stream)))
+        return P1, Info.from_c(info, k)
+
+    def scc_response(self, H1_ext, gamma, workspace, tol=1e-6, max_iter=100, mixing=0.8,
+                     out=None, stream=None, raise_on_error=True, **kw):
+        """Self-consistent P1 (H1 = H1_ext + diag(gamma diag(P1))) from the S0
+        tape of the forward run that filled `workspace`.  Returns
+        (P1, iterations, residual, Info)."""
+        import torch
+        if H1_ext.dim() == 2:
+            H1_ext = H1_ext.unsqueeze(0)
+        H1_ext = H1_ext.contiguous()
+        gamma = gamma.contiguous()
+        k, n = H1_ext.shape[0], H1_ext.shape[1]
+        P1 = torch.empty_like(H1_ext) if out is None else out
+        opts = options(**kw)
+        info = DmptInfo()
+        its = ctypes.c_int(0)
+        res = ctypes.c_double(0.0)
+        ptr, ln = self._ws_ptr(workspace)
+        s = stream if stream is not None else torch.cuda.current_stream(H1_ext.device)
+        st = self.lib.dmpt_scc_response(self.h, H1_ext.data_ptr(), gamma.data_ptr(), k, n, n,
+                                        ctypes.byref(opts), float(tol), int(max_iter),
+                                        float(mixing), P1.data_ptr(), ctypes.byref(info),
+                                        ctypes.byref(its), ctypes.byref(res),
+                                        ctypes.c_void_p(ptr), ln, ctypes.c_void_p(s.cuda_stream))
+        if st != 0 and raise_on_error:
+            self._check(st)
+        return P1, its.value, res.value, Info.from_c(info, k)
 
     def sp2_response_host(self, H_host, H1_host, n_occ: int, precision="dual_fp16",
                           stream=None, **kw):
