@@ -247,6 +247,8 @@ def main():
     ap.add_argument("--input-backend", default="torch", choices=["torch", "numpy"])
     ap.add_argument("--cta-pair", type=int, default=1, choices=[0, 1])
     ap.add_argument("--k-snake", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--no-scc", action="store_true",
+                    help="skip the self-consistent response measurement (same workload + tape)")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the adjoint measurement (n=4096 forward with tape + backward)")
     args = ap.parse_args()
@@ -356,6 +358,30 @@ def main():
     _, _, info = ctx.sp2_response(H, H1, inst.n_occ, **kw)
     torch.cuda.synchronize()
 
+    # ---- self-consistent response on the same workload: forward with the S0
+    #      tape, then H1 <- H1_ext + diag(gamma diag(P1)) by response replays
+    scc = None
+    if not args.no_scc and rank == 0:
+        from paper_2203_09621_gb300.workloads import scc_gamma
+        gam = scc_gamma(n, backend="torch", device=dev)
+        sopts = dmpt.options(precision=args.precision, ckpt_every=1, max_layers=64)
+        sws = torch.empty(ctx.workspace_size(n, k, sopts) + 256, dtype=torch.uint8, device=dev)
+        s0, s1, s2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        s0.record(stream)
+        ctx.sp2_response(H, H1, inst.n_occ, precision=args.precision, ckpt_every=1,
+                         max_layers=64, workspace=sws, out=(P, P1))
+        s1.record(stream)
+        P1s, its, res, sinfo = ctx.scc_response(H1, gam, sws, tol=1e-5, max_iter=50,
+                                                precision=args.precision)
+        s2.record(stream)
+        torch.cuda.synchronize()
+        scc_ms = s1.elapsed_time(s2)
+        scc = {"workload": f"dipole3 n={n} k={k} + gamma_ij = (40/n)/sqrt(r^2+1)",
+               "iterations": its, "residual": res, "forward_with_tape_ms": s0.elapsed_time(s1),
+               "scc_ms": scc_ms, "ms_per_iteration": scc_ms / max(its, 1),
+               "replay_tflops": sinfo.alg_flops / (scc_ms * 1e-3) / 1e12}
+        del sws, P1s
+
     # ---- adjoint (L = Tr[G P]): n = 4096 forward with the S0 tape + backward
     adjoint = None
     if not args.no_adjoint and rank == 0:
@@ -435,6 +461,7 @@ def main():
             "rel_err_P1_sampled": err,
             "forms": forms,
             "adjoint": adjoint,
+            "scc": scc,
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": None,
                          "kernel": "layer_tc2_kernel" if args.cta_pair else "layer_tc_kernel",
