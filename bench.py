@@ -247,6 +247,8 @@ def main():
     ap.add_argument("--input-backend", default="torch", choices=["torch", "numpy"])
     ap.add_argument("--cta-pair", type=int, default=1, choices=[0, 1])
     ap.add_argument("--k-snake", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the uneven-batch measurement (64 instances, n in [256, 2048])")
     ap.add_argument("--no-scc", action="store_true",
                     help="skip the self-consistent response measurement (same workload + tape)")
     ap.add_argument("--no-adjoint", action="store_true",
@@ -382,6 +384,39 @@ def main():
                "replay_tflops": sinfo.alg_flops / (scc_ms * 1e-3) / 1e12}
         del sws, P1s
 
+    # ---- uneven batch: 64 independent instances, n log-uniform in [256, 2048]
+    batch = None
+    if not args.no_batch and rank == 0:
+        from paper_2203_09621_gb300.workloads import uneven_batch
+        binst = uneven_batch(backend="torch", device=dev)
+        bH = [x.H for x in binst]
+        bH1 = [x.H1 for x in binst]
+        bocc = [x.n_occ for x in binst]
+        for _ in range(2):
+            ctx.sp2_response_batch(bH, bH1, bocc, precision=args.precision)
+        torch.cuda.synchronize()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        _, _, binfos = ctx.sp2_response_batch(bH, bH1, bocc, precision=args.precision)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        bms = b0.elapsed_time(b1)
+        balg = sum(i.alg_flops for i in binfos)
+        # the same instances one call after another
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for x_h, x_h1, x_o in zip(bH, bH1, bocc):
+            ctx.sp2_response(x_h, x_h1, x_o, precision=args.precision)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        sms_ = q0.elapsed_time(q1)
+        batch = {"workload": "64 instances, n log-uniform in [256, 2048], n_occ = n/2, "
+                             "gap U[0.1, 0.5], k = 1",
+                 "ms": bms, "tflops": balg / (bms * 1e-3) / 1e12,
+                 "sequential_ms": sms_, "speedup_vs_sequential": sms_ / bms,
+                 "converged": int(sum(i.converged for i in binfos))}
+        del binst, bH, bH1
+
     # ---- adjoint (L = Tr[G P]): n = 4096 forward with the S0 tape + backward
     adjoint = None
     if not args.no_adjoint and rank == 0:
@@ -461,6 +496,7 @@ def main():
             "rel_err_P1_sampled": err,
             "forms": forms,
             "adjoint": adjoint,
+            "batch": batch,
             "scc": scc,
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": None,

@@ -189,6 +189,30 @@ dmpt_status dmpt_sp2_backward(dmpt_handle h, const double* G, int64_t n, int64_t
                               const dmpt_options* o, double* dLdH, void* workspace,
                               size_t ws_bytes, void* stream);
 
+/* Many independent instances of dmpt_sp2_response in one call (uneven
+ * sizes), e.g. a batch of molecules.  Each instance runs its own layer loop
+ * (Algorithms 1-3) on its own internal stream with layer-product kernels
+ * sized to its tile count, so small instances share the GPU; one CUDA graph
+ * holds one layer of every instance and is replayed until all have
+ * converged (kernels of finished instances exit at once).
+ *   count       instances; H, H1, P, P1: host arrays of `count` device
+ *               pointers (H1/P1 entries: k blocks of n_i x n_i (ld_i)).
+ *   n, ld, n_occ: host arrays of `count` values.
+ *   k           directions per instance (same for all), 0..DMPT_MAX_K.
+ *   info        host array of `count` entries (may be NULL).
+ *   workspace   dmpt_workspace_size_batch() bytes, 256-byte aligned.
+ * Options: no tape (ckpt_every = 0) and no per-launch timing.  Synchronises
+ * the issuing stream every o->sync_every layers; the caller's `stream` is
+ * ordered before and after the batch.  Returns the first failing instance's
+ * status (all instances are still written). */
+size_t dmpt_workspace_size_batch(int count, const int64_t* n, int k, const dmpt_options* o);
+dmpt_status dmpt_sp2_response_batch(dmpt_handle h, int count, const double* const* H,
+                                    const double* const* H1, int k, const int64_t* n,
+                                    const int64_t* ld, const int64_t* n_occ,
+                                    const dmpt_options* o, double* const* P, double* const* P1,
+                                    dmpt_info* info, void* workspace, size_t ws_bytes,
+                                    void* stream);
+
 /* First-order responses to new perturbations, reusing the S0 states that a
  * preceding dmpt_sp2_response call with o->ckpt_every = 1 (dual precision)
  * kept in `workspace`: only the response recursion of Sec. III A,

@@ -18,7 +18,11 @@ struct dmpt_ctx {
   int device = 0;
   int sm_count = 0;
   char err[512] = {0};
-  std::vector<cudaEvent_t> events;  // timing pairs, created on first use
+  std::vector<cudaEvent_t> events;   // timing pairs, created on first use
+  std::vector<cudaStream_t> streams; // per-instance streams of batched solves
+  std::vector<cudaEvent_t> joins;    // per-instance join events
+  cudaStream_t origin = nullptr;     // capture / issue stream of batched solves
+  cudaEvent_t fork = nullptr;
 };
 
 namespace {
@@ -276,6 +280,10 @@ dmpt_status dmpt_destroy(dmpt_handle h) {
   {
     DeviceGuard g(h->device);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->joins) cudaEventDestroy(e);
+    for (cudaStream_t st : h->streams) cudaStreamDestroy(st);
+    if (h->origin) cudaStreamDestroy(h->origin);
+    if (h->fork) cudaEventDestroy(h->fork);
   }
   delete h;
   return DMPT_OK;
@@ -512,6 +520,227 @@ dmpt_status dmpt_sp2_backward(dmpt_handle h, const double* G, int64_t n, int64_t
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(h, e, "dmpt_sp2_backward");
   if (status != DMPT_OK) return fail(h, (dmpt_status)status, "dmpt_sp2_backward: device status%s");
+  return DMPT_OK;
+}
+
+static size_t batch_scratch_bytes(int count) {
+  return ((size_t)count * sizeof(long long) + 2 * sizeof(int) + 255) & ~size_t(255);
+}
+
+size_t dmpt_workspace_size_batch(int count, const int64_t* n, int k, const dmpt_options* o) {
+  dmpt_options d;
+  dmpt_default_options(&d);
+  if (!o) o = &d;
+  if (count < 1 || !n || k < 0 || k > DMPT_MAX_K || !valid_options(o) || o->ckpt_every != 0)
+    return 0;
+  size_t total = batch_scratch_bytes(count);
+  for (int i = 0; i < count; ++i) {
+    if (n[i] < 1) return 0;
+    total += (layout_for(n[i], k, o).total + 255) & ~size_t(255);
+  }
+  return total;
+}
+
+dmpt_status dmpt_sp2_response_batch(dmpt_handle h, int count, const double* const* H,
+                                    const double* const* H1, int k, const int64_t* n,
+                                    const int64_t* ld, const int64_t* n_occ,
+                                    const dmpt_options* o, double* const* P, double* const* P1,
+                                    dmpt_info* info, void* workspace, size_t ws_bytes,
+                                    void* stream) {
+  if (!h) return DMPT_EINVAL;
+  h->err[0] = 0;
+  dmpt_options defaults;
+  dmpt_default_options(&defaults);
+  if (!o) o = &defaults;
+  if (count < 1 || !H || !n || !ld || !n_occ || (k > 0 && (!H1 || !P1)) || (k == 0 && !P))
+    return fail(h, DMPT_EINVAL, "dmpt_sp2_response_batch: bad arguments%s");
+  if (k < 0 || k > DMPT_MAX_K || !valid_options(o) || o->ckpt_every != 0 || o->timing)
+    return fail(h, DMPT_EINVAL, "dmpt_sp2_response_batch: bad k or options (no tape, no timing)%s");
+  for (int i = 0; i < count; ++i) {
+    if (!H[i] || n[i] < 1 || ld[i] < n[i] || n_occ[i] < 0 || n_occ[i] > n[i] ||
+        (k > 0 && (!H1[i] || !P1[i])) || (k == 0 && !P[i]))
+      return fail(h, DMPT_EINVAL, "dmpt_sp2_response_batch: bad instance%s");
+  }
+  const size_t need = dmpt_workspace_size_batch(count, n, k, o);
+  if (!workspace || ((uintptr_t)workspace) % 256 || ws_bytes < need)
+    return fail(h, DMPT_EWORKSPACE, "dmpt_sp2_response_batch: workspace missing or too small%s");
+  if (info) memset(info, 0, sizeof(dmpt_info) * (size_t)count);
+  DeviceGuard g(h->device);
+  cudaError_t e;
+  cudaStream_t caller = (cudaStream_t)stream;
+  // streams and events (created once per handle, reused)
+  while ((int)h->streams.size() < count) {
+    cudaStream_t st;
+    if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(h, e, "batch stream");
+    h->streams.push_back(st);
+    cudaEvent_t ev;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(h, e, "batch event");
+    h->joins.push_back(ev);
+  }
+  if (!h->origin && (e = cudaStreamCreateWithFlags(&h->origin, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(h, e, "batch origin stream");
+  if (!h->fork && (e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(h, e, "batch fork event");
+  const bool dual = o->precision >= DMPT_DUAL_FP16;
+
+  // carve the workspace: [scratch: state offsets, all-done flag][instance 0][instance 1]...
+  char* base = (char*)workspace;
+  long long* d_offs = (long long*)base;
+  int* d_flag = (int*)(base + (size_t)count * sizeof(long long));
+  std::vector<Layout> L(count);
+  std::vector<long long> offs(count);
+  std::vector<int> active(count, 0);
+  size_t off = batch_scratch_bytes(count);
+  for (int i = 0; i < count; ++i) {
+    L[i] = layout_for(n[i], k, o);
+    offs[i] = (long long)off;
+    off += (L[i].total + 255) & ~size_t(255);
+    active[i] = (n_occ[i] > 0 && n_occ[i] < n[i]) ? 1 : 0;
+  }
+  // fork: the origin stream and every instance stream follow the caller's stream
+  if ((e = cudaEventRecord(h->fork, caller)) != cudaSuccess) return cuda_fail(h, e, "batch fork");
+  if ((e = cudaStreamWaitEvent(h->origin, h->fork, 0)) != cudaSuccess) return cuda_fail(h, e, "fork");
+  // control blocks polled for completion: active (non-trivial) instances only
+  std::vector<long long> act_offs;
+  for (int i = 0; i < count; ++i)
+    if (active[i]) act_offs.push_back(offs[i]);
+  const int n_active = (int)act_offs.size();
+  if (n_active > 0 &&
+      (e = cudaMemcpyAsync(d_offs, act_offs.data(), sizeof(long long) * n_active,
+                           cudaMemcpyHostToDevice, h->origin)) != cudaSuccess)
+    return cuda_fail(h, e, "batch offsets");
+  if ((e = cudaStreamSynchronize(h->origin)) != cudaSuccess) return cuda_fail(h, e, "batch fork");
+  std::vector<int64_t> entries(count, 0);
+  std::vector<double> pass_flops(count, 0.0);
+  auto issue_step = [&](int i) -> cudaError_t {
+    cudaStream_t si = h->streams[i];
+    void* ws = base + offs[i];
+    cudaError_t r = dual ? launch_layer_tc(L[i], ws, si, o->timeout_s, o->accum_chunk,
+                                           o->cta_pair, o->k_snake, &entries[i], &pass_flops[i])
+                         : launch_layer_simt(L[i], ws, si, &entries[i], &pass_flops[i]);
+    if (r != cudaSuccess) return r;
+    return launch_decide(L[i], ws, kDecideLayer, entries[i], si);
+  };
+  for (int i = 0; i < count; ++i) {
+    cudaStream_t si = h->streams[i];
+    if ((e = cudaStreamWaitEvent(si, h->fork, 0)) != cudaSuccess) return cuda_fail(h, e, "fork");
+    if (!active[i]) {
+      if ((e = launch_trivial(n[i], k, ld[i], n_occ[i] == n[i], P ? P[i] : nullptr,
+                              k ? P1[i] : nullptr, si)) != cudaSuccess)
+        return cuda_fail(h, e, "batch trivial");
+      continue;
+    }
+    void* ws = base + offs[i];
+    State* st = (State*)ws;
+    if ((e = cudaMemsetAsync(st, 0, sizeof(State), si)) != cudaSuccess) return cuda_fail(h, e, "state");
+    state_init_kernel<<<1, 1, 0, si>>>(st, k, o->max_layers, o->precision, (double)n_occ[i],
+                                       o->c_pt, o->c_d0, 0, 4 * (1 + L[i].k), 0, L[i].k, n[i]);
+    if ((e = launch_bounds(H[i], n[i], ld[i], &st->eps1, si)) != cudaSuccess)
+      return cuda_fail(h, e, "batch bounds");
+    if ((e = launch_init(L[i], ws, H[i], k ? H1[i] : nullptr, ld[i], k, 1024, si)) != cudaSuccess)
+      return cuda_fail(h, e, "batch init");
+    if ((e = launch_decide(L[i], ws, kDecideInit, 1024, si)) != cudaSuccess)
+      return cuda_fail(h, e, "batch decide");
+    if (dual && (e = launch_split(L[i], ws, 0, si)) != cudaSuccess) return cuda_fail(h, e, "split");
+    if ((e = issue_step(i)) != cudaSuccess) return cuda_fail(h, e, "batch first layer");
+  }
+  // join everything into the origin stream
+  for (int i = 0; i < count; ++i) {
+    if ((e = cudaEventRecord(h->joins[i], h->streams[i])) != cudaSuccess) return cuda_fail(h, e, "join");
+    if ((e = cudaStreamWaitEvent(h->origin, h->joins[i], 0)) != cudaSuccess) return cuda_fail(h, e, "join");
+  }
+  // one CUDA graph = one layer of every active instance, each on its own stream
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if ((e = cudaStreamBeginCapture(h->origin, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+    return cuda_fail(h, e, "batch capture");
+  cudaError_t ce = cudaEventRecord(h->fork, h->origin);
+  for (int i = 0; i < count && ce == cudaSuccess; ++i) {
+    if (!active[i]) continue;
+    ce = cudaStreamWaitEvent(h->streams[i], h->fork, 0);
+    if (ce == cudaSuccess) ce = issue_step(i);
+    if (ce == cudaSuccess) ce = cudaEventRecord(h->joins[i], h->streams[i]);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(h->origin, h->joins[i], 0);
+  }
+  e = cudaStreamEndCapture(h->origin, &graph);
+  if (ce != cudaSuccess || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(h, ce != cudaSuccess ? ce : e, "batch capture");
+  }
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(h, e, "batch instantiate");
+  int steps = 1, all_done = n_active == 0 ? 1 : 0;
+  while (steps < o->max_layers && !all_done) {
+    for (int j = 0; j < o->sync_every && steps < o->max_layers; ++j, ++steps) {
+      if ((e = cudaGraphLaunch(exec, h->origin)) != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        return cuda_fail(h, e, "batch graph launch");
+      }
+    }
+    if ((e = launch_batch_all_done(base, d_offs, n_active, d_flag, h->origin)) == cudaSuccess)
+      e = cudaMemcpyAsync(&all_done, d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->origin);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->origin);
+    if (e != cudaSuccess) {
+      cudaGraphExecDestroy(exec);
+      return cuda_fail(h, e, "batch poll");
+    }
+  }
+  cudaGraphExecDestroy(exec);
+  dmpt_status worst = DMPT_OK;
+  std::vector<State> hs(1);
+  for (int i = 0; i < count; ++i) {
+    if (!active[i]) {
+      if (info) {
+        info[i].status = DMPT_OK;
+        info[i].converged = 1;
+      }
+      continue;
+    }
+    void* ws = base + offs[i];
+    if ((e = launch_finalize(L[i], ws, P ? P[i] : nullptr, k ? P1[i] : nullptr, ld[i], k,
+                             h->origin)) != cudaSuccess)
+      return cuda_fail(h, e, "batch finalize");
+    e = cudaMemcpyAsync(hs.data(), ws, sizeof(State), cudaMemcpyDeviceToHost, h->origin);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->origin);
+    if (e != cudaSuccess) return cuda_fail(h, e, "batch state");
+    const State& S = hs[0];
+    const dmpt_status si = S.done ? (dmpt_status)S.status : DMPT_ENOTCONV;
+    if (si != DMPT_OK && worst == DMPT_OK) worst = si;
+    if (info) {
+      dmpt_info& I = info[i];
+      I.status = si;
+      I.layers = S.layers_run;
+      I.d0_layer = S.d0_layer;
+      bool all1 = S.d0_conv != 0;
+      for (int j = 0; j < k; ++j) {
+        I.d1_layer[j] = S.d1_layer[j];
+        all1 = all1 && S.d1_conv[j];
+      }
+      I.converged = (si == DMPT_OK && all1) ? 1 : 0;
+      I.eps_min = S.eps1;
+      I.eps_max = S.epsN;
+      I.froerr0 = S.froerr0;
+      I.product_launches = steps;
+      double alg = 0.0;
+      for (int m = 1; m <= S.layers_run; ++m) {
+        const bool sq = S.d0_layer == 0 || m <= S.d0_layer;
+        int act = 0;
+        for (int j = 0; j < k; ++j) act += (S.d1_conv[j] ? m <= S.d1_layer[j] : true) ? 1 : 0;
+        alg += layer_alg_flops((double)n[i], o->precision, sq, act);
+        I.mma_flops += layer_mma_flops(L[i], pass_flops[i], sq, act);
+      }
+      I.alg_flops = alg;
+      for (int m = 1; m <= S.layers_run && m <= DMPT_MAX_LAYERS; ++m) I.sigma[m - 1] = S.sigma[m];
+    }
+  }
+  // the caller's stream continues after the batch
+  if ((e = cudaEventRecord(h->fork, h->origin)) == cudaSuccess)
+    e = cudaStreamWaitEvent(caller, h->fork, 0);
+  if (e != cudaSuccess) return cuda_fail(h, e, "batch join");
+  if (worst != DMPT_OK) return fail(h, worst, "dmpt_sp2_response_batch: an instance failed%s");
   return DMPT_OK;
 }
 

@@ -147,6 +147,10 @@ enum DecideMode {
   kDecideReplayLayer = 5
 };
 
+// batched solves: *flag = 1 when every instance's control block is done
+cudaError_t launch_batch_all_done(const void* base, const long long* offs, int count, int* flag,
+                                  cudaStream_t s);
+
 // CUDA device of a handle (-1 for NULL).
 int handle_device(dmpt_handle h);
 

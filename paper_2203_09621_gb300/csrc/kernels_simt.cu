@@ -1010,3 +1010,23 @@ cudaError_t launch_trivial(int64_t n, int k, int64_t ld, int full, double* P, do
 }
 
 }  // namespace dmpt
+
+namespace dmpt {
+// *flag = 1 when every instance's control block (at base + offs[i]) says done
+__global__ void batch_all_done_kernel(const char* base, const long long* offs, int count,
+                                      int* flag) {
+  int all = 1;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    const State* st = (const State*)(base + offs[i]);
+    if (!st->done) all = 0;
+  }
+  all = __syncthreads_and(all);
+  if (threadIdx.x == 0) *flag = all;
+}
+
+cudaError_t launch_batch_all_done(const void* base, const long long* offs, int count, int* flag,
+                                  cudaStream_t s) {
+  batch_all_done_kernel<<<1, 256, 0, s>>>((const char*)base, offs, count, flag);
+  return cudaGetLastError();
+}
+}  // namespace dmpt

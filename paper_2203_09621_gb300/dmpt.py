@@ -106,6 +106,15 @@ def load_library(path: str = LIB_PATH):
                                       ctypes.POINTER(DmptInfo), ctypes.POINTER(c_int),
                                       ctypes.POINTER(ctypes.c_double), vp, ctypes.c_size_t, vp]
     lib.dmpt_scc_response.restype = c_int
+    lib.dmpt_workspace_size_batch.argtypes = [c_int, ctypes.POINTER(i64), c_int,
+                                              ctypes.POINTER(DmptOptions)]
+    lib.dmpt_workspace_size_batch.restype = ctypes.c_size_t
+    lib.dmpt_sp2_response_batch.argtypes = [vp, c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int,
+                                            ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                            ctypes.POINTER(i64), ctypes.POINTER(DmptOptions),
+                                            ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                            ctypes.POINTER(DmptInfo), vp, ctypes.c_size_t, vp]
+    lib.dmpt_sp2_response_batch.restype = c_int
     lib.dmpt_sp2_response_static.argtypes = [vp, vp, vp, c_int, i64, i64, i64,
                                              ctypes.POINTER(DmptOptions), vp, vp,
                                              ctypes.POINTER(DmptInfo), vp]
@@ -289,6 +298,39 @@ class Context:
                                                dLdH.data_ptr(), ctypes.c_void_p(ws_ptr), ws_len,
                                                ctypes.c_void_p(s.cuda_stream)))
         return dLdH
+
+    def sp2_response_batch(self, Hs, H1s, n_occs, precision="dual_fp16", stream=None,
+                           raise_on_error=True, **kw):
+        """Independent instances (lists of float64 CUDA tensors) in one call.
+        Returns (list of P, list of P1 (k, n, n) or None, list of Info)."""
+        import torch
+        count = len(Hs)
+        Hs = [h.contiguous() for h in Hs]
+        k = 0 if H1s is None else (H1s[0].shape[0] if H1s[0].dim() == 3 else 1)
+        if H1s is not None:
+            H1s = [(h1 if h1.dim() == 3 else h1.unsqueeze(0)).contiguous() for h1 in H1s]
+        ns = [h.shape[0] for h in Hs]
+        Ps = [torch.empty_like(h) for h in Hs]
+        P1s = [torch.empty(k, n, n, dtype=torch.float64, device=h.device) for n, h in zip(ns, Hs)] if k else None
+        opts = options(precision=precision, **kw)
+        I64 = ctypes.c_int64 * count
+        VP = ctypes.c_void_p * count
+        n_arr = I64(*ns)
+        nbytes = self.lib.dmpt_workspace_size_batch(count, n_arr, k, ctypes.byref(opts))
+        if nbytes == 0:
+            raise DmptError(1, "invalid batch sizes or options")
+        ws_ptr, ws_len = self.workspace(nbytes)
+        infos = (DmptInfo * count)()
+        s = stream if stream is not None else torch.cuda.current_stream(Hs[0].device)
+        st = self.lib.dmpt_sp2_response_batch(
+            self.h, count, VP(*[h.data_ptr() for h in Hs]),
+            VP(*[h1.data_ptr() for h1 in H1s]) if k else None, k, n_arr, I64(*ns),
+            I64(*[int(x) for x in n_occs]), ctypes.byref(opts), VP(*[p.data_ptr() for p in Ps]),
+            VP(*[p.data_ptr() for p in P1s]) if k else None, infos, ctypes.c_void_p(ws_ptr),
+            ws_len, ctypes.c_void_p(s.cuda_stream))
+        if st != 0 and raise_on_error:
+            self._check(st)
+        return Ps, P1s, [Info.from_c(infos[i], k) for i in range(count)]
 
     @staticmethod
     def _ws_ptr(workspace):
