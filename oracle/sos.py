@@ -20,6 +20,10 @@ Sec. III A restricts the theory to non-degenerate systems: a gap between
 level n_occ and n_occ + 1 is required, and these functions raise if it is
 missing.
 
+``response2_from_eigs`` / ``response2_sos`` give the second-order response
+D2 = (1/2) d^2P/dlambda^2 (Eq. (eq:D_k), k = 2) by the second-order
+Daleckii-Krein formula.
+
 Pinned by: the 2x2 closed form differentiated symbolically
 (tests/golden/two_level.json and the sympy test), the invariants P^2 = P,
 Tr P = n_occ, [H, P] = 0, Tr P1 = 0, P P1 + P1 P = P1,
@@ -106,3 +110,53 @@ def response_columns(eps, V, H1, n_occ, cols):
     cols = np.asarray(cols)
     # P1 = Vo M Vv^T + Vv M^T Vo^T, column j: Vo (M Vv[j]) + Vv (M^T Vo[j])
     return Vo @ (M @ Vv[cols, :].T) + Vv @ (M.T @ Vo[cols, :].T)
+
+
+def _second_divided_differences(eps, f, m):
+    """F2[i, j] = f[eps_i, eps_m, eps_j] for the step occupations f (0/1).
+
+    First divided differences f[x, y] = (f(x) - f(y)) / (x - y), and
+    f'(x) = 0 away from mu; second ones f[a, b, c] = (f[a, b] - f[b, c]) /
+    (a - c), and at a = c the derivative of f[a, b] in a, which is
+    -(f(a) - f(b)) / (a - b)^2 (0 when b = a as well).
+    """
+    n = eps.shape[0]
+    d1 = np.zeros(n)                      # f[eps_i, eps_m]
+    mask = np.arange(n) != m
+    d1[mask] = (f[mask] - f[m]) / (eps[mask] - eps[m])
+    num = d1[:, None] - d1[None, :]       # f[i, m] - f[m, j]
+    den = eps[:, None] - eps[None, :]
+    F2 = np.zeros((n, n))
+    off = ~np.eye(n, dtype=bool)
+    F2[off] = num[off] / den[off]
+    diag = np.zeros(n)
+    diag[mask] = -(f[mask] - f[m]) / (eps[mask] - eps[m]) ** 2
+    F2[np.arange(n), np.arange(n)] = diag
+    return F2
+
+
+def response2_from_eigs(eps, V, H1, n_occ):
+    """Second-order response D2 = (1/2) d^2 P(H + lambda H1)/dlambda^2 at 0.
+
+    Eq. (eq:D_k) with k = 2 (a linear perturbation, H2 = 0).  The second
+    Daleckii-Krein formula for a spectral function f:
+        D2 = V [ sum_m f[eps_i, eps_m, eps_j] Y_im Y_mj ]_ij V^T,  Y = V^T H1 V,
+    with the second divided differences of the step occupations (all
+    eigenvalues away from mu).  O(n^3) time, O(n^2) memory.
+    """
+    eps = np.asarray(eps, dtype=np.float64)
+    V = np.asarray(V, dtype=np.float64)
+    n = eps.shape[0]
+    _check_gap(eps, n_occ)
+    f = _occupations(n, n_occ)
+    Y = V.T @ np.asarray(H1, dtype=np.float64) @ V
+    M = np.zeros((n, n))
+    for m in range(n):
+        M += _second_divided_differences(eps, f, m) * np.outer(Y[:, m], Y[m, :])
+    return V @ M @ V.T
+
+
+def response2_sos(H, H1, n_occ):
+    """D2 for one perturbation via eigh (see response2_from_eigs)."""
+    eps, V = np.linalg.eigh(np.asarray(H, dtype=np.float64))
+    return response2_from_eigs(eps, V, H1, n_occ)

@@ -68,6 +68,8 @@ class SP2Result:
     d1_layer: List[int] = field(default_factory=list)    # per k: layer whose test fired
     bounds: tuple = (0.0, 0.0)
     checkpoints: dict = field(default_factory=dict)       # n -> S_n (if requested)
+    d2_layer: List[int] = field(default_factory=list)    # order 2: layer whose test fired
+    P2: Optional[np.ndarray] = None     # (k, n, n) S2 at exit (D^(2)), order = 2
 
 
 def _sign_tie_minus(x):
@@ -75,8 +77,18 @@ def _sign_tie_minus(x):
 
 
 def sp2_pt(H, H1, n_occ, c_pt=9.0, c_d0=4.5, max_layers=100, bounds=None,
-           keep_states=False):
-    """Algorithms 1-3 in FP64.  H1: one (n, n) matrix or a (k, n, n) stack."""
+           keep_states=False, order=1):
+    """Algorithms 1-3 in FP64.  H1: one (n, n) matrix or a (k, n, n) stack.
+
+    order = 2 also propagates the second-order term of Eq. (S_n detailed)
+    (H2 = 0, so S2_0 = 0):
+        S2_n = sigma_n (S0 S2 + S1 S1 + S2 S0) + (1 - sigma_n) S2.
+    The paper gives stopping criteria for orders 0 and 1 only; the reading
+    taken here applies the test of Alg. 3 to the second-order idempotency
+    error FroErr2_n = ||S2 - (S0 S2 + S1 S1 + S2 S0)||_F with the same C_pt
+    and FroErr^(0) (Eq. (ConvCrit) in the same form), each direction's S2
+    freezing when it fires; S2 keeps using the (possibly frozen) S1.
+    """
     H = np.asarray(H, dtype=np.float64)
     H1 = np.asarray(H1, dtype=np.float64)
     if H1.ndim == 2:
@@ -98,6 +110,10 @@ def sp2_pt(H, H1, n_occ, c_pt=9.0, c_d0=4.5, max_layers=100, bounds=None,
     S0 = W0 * H + (epsN / (epsN - eps1)) * np.eye(n)
     NS = np.trace(S0)
     S1 = [W0 * H1[j] for j in range(k)]                 # B_0^(1) = 0
+    S2 = [np.zeros((n, n)) for _ in range(k)] if order == 2 else []
+    d2_conv = [order != 2] * k
+    froerr2 = [dict() for _ in range(k)]
+    d2_layer = [0] * k
 
     n_layer = 1
     d0_conv = False
@@ -111,16 +127,19 @@ def sp2_pt(H, H1, n_occ, c_pt=9.0, c_d0=4.5, max_layers=100, bounds=None,
     ckpt = {0: S0.copy()} if keep_states else {}
     converged = True
 
-    while not (d0_conv and all(d1_conv)):
+    while not (d0_conv and all(d1_conv) and all(d2_conv)):
         if n_layer > max_layers:
             converged = False
             n_layer -= 1
             break
         # activation f^(1) for every direction still running
         X1 = [None] * k
+        X2 = [None] * k
         for j in range(k):
             if not d1_conv[j]:
                 X1[j] = S0 @ S1[j] + S1[j] @ S0
+            if order == 2 and not d2_conv[j]:
+                X2[j] = S0 @ S2[j] + S1[j] @ S1[j] + S2[j] @ S0   # uses S1_{n-1}
         if not d0_conv:
             X0 = S0 @ S0                                  # activation f^(0)
             NX = np.trace(X0)
@@ -159,6 +178,18 @@ def sp2_pt(H, H1, n_occ, c_pt=9.0, c_d0=4.5, max_layers=100, bounds=None,
                     d1_layer[j] = n_layer
             if not d1_conv[j]:
                 S1[j] = s * X1[j] + (1 - s) * S1[j]
+        for j in range(k):
+            if d2_conv[j]:
+                continue
+            if d0_conv:
+                fe = np.linalg.norm(S2[j] - X2[j], "fro")
+                froerr2[j][n_layer] = fe
+                prev = froerr2[j].get(n_layer - 2)
+                if n_layer - 2 >= d0_layer and prev is not None and fe >= c_pt * froerr0 * prev:
+                    d2_conv[j] = True
+                    d2_layer[j] = n_layer
+            if not d2_conv[j]:
+                S2[j] = s * X2[j] + (1 - s) * S2[j]
         n_layer += 1
     else:
         n_layer -= 1
@@ -168,7 +199,8 @@ def sp2_pt(H, H1, n_occ, c_pt=9.0, c_d0=4.5, max_layers=100, bounds=None,
     for j in range(k):
         fe_lists.append([froerr1[j].get(m, float("nan")) for m in range(1, layers + 1)])
     return SP2Result(P=S0, P1=np.stack(S1), layers=layers, d0_layer=d0_layer,
-                     converged=converged,
+                     converged=converged, P2=np.stack(S2) if order == 2 else None,
+                     d2_layer=d2_layer,
                      sigma=[sigma[m] for m in range(1, layers + 1)],
                      iderr=[iderr[m] for m in sorted(iderr)],
                      froerr0=float(froerr0) if froerr0 is not None else float("nan"),
