@@ -90,7 +90,9 @@ typedef struct {
                            128 x 256 tile                                      */
   int k_snake;          /* CTA-pair form: 1 = alternate the K-sweep direction
                            between scheduling rounds for L2 reuse (default 1) */
-  int reserved[4];
+  int order;            /* response order the workspace is sized for: 1
+                           (default), 2 for dmpt_sp2_response2                */
+  int reserved[3];
 } dmpt_options;
 
 /* Filled on the host by dmpt_sp2_response (when info != NULL). */
@@ -164,6 +166,22 @@ dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1,
                               const dmpt_options* o, double* P, double* P1,
                               dmpt_info* info, void* workspace, size_t ws_bytes,
                               void* stream);
+
+/* Second-order response as well (Sec. III A, Eq. (S_n detailed) with k = 2;
+ * Eq. (eq:D_k): D^(2) = (1/2) d^2 P / dlambda^2 for H(lambda) = H + lambda H1):
+ *   S2_0 = 0,  S2_n = sigma_n (S0 S2 + S1 S1 + S2 S0) + (1 - sigma_n) S2,
+ * each dual product on the tensor cores (passes S0 S2, S2 S0, S1 S1 into one
+ * accumulator).  The paper states stopping criteria for orders 0 and 1 only;
+ * each S2_j stops by the test of Alg. 3 applied to its own idempotency error
+ * ||S2 - (S0 S2 + S1 S1 + S2 S0)||_F (same C_pt and FroErr^(0)).
+ *   Same arguments as dmpt_sp2_response plus P2 (device, k blocks n x n,
+ *   ld); 1 <= k <= DMPT_MAX_K / 2; dual precisions, no tape.  The workspace
+ *   is dmpt_workspace_size(n, k, o) with o->order = 2.  In info, entries
+ *   k .. 2k-1 of d1_layer / froerr1 are those of the second-order terms. */
+dmpt_status dmpt_sp2_response2(dmpt_handle h, const double* H, const double* H1, int k,
+                               int64_t n, int64_t ld, int64_t n_occ, const dmpt_options* o,
+                               double* P, double* P1, double* P2, dmpt_info* info,
+                               void* workspace, size_t ws_bytes, void* stream);
 
 /* Adjoint of the S0 recursion: the gradient of L = Tr[G P] with respect to H
  * for the P of the preceding dmpt_sp2_response call that used `workspace`

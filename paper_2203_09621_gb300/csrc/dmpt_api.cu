@@ -61,6 +61,7 @@ bool valid_options(const dmpt_options* o) {
   if (o->accum_chunk < 0) return false;
   if (o->cta_pair < 0 || o->cta_pair > 1) return false;
   if (o->k_snake < 0 || o->k_snake > 1) return false;
+  if (o->order < 1 || o->order > 2) return false;
   return true;
 }
 
@@ -68,13 +69,16 @@ bool valid_options(const dmpt_options* o) {
 // one when S0 states are kept, for the adjoint) and tape capacity.
 Layout layout_for(int64_t n, int k, const dmpt_options* o) {
   const bool tape = o->ckpt_every == 1;
-  const int slots = (tape && k == 0) ? 1 : k;
+  const int slots = o->order == 2 ? 2 * k : ((tape && k == 0) ? 1 : k);
   return make_layout(n, slots, o->precision, tape ? o->max_layers + 2 : 0);
 }
 
 __global__ void state_init_kernel(State* st, int k, int max_layers, int precision, double n_occ,
                                   double c_pt, double c_d0, int tape, int tape_base,
-                                  int tape_states, int layout_k, int64_t n) {
+                                  int tape_states, int layout_k, int64_t n, int order = 1,
+                                  int k1 = 0) {
+  st->order = order;
+  st->k1 = order == 2 ? k1 : k;
   st->tape = tape;
   st->tape_base = tape_base;
   st->tape_states = tape_states;
@@ -206,16 +210,20 @@ dmpt_status replay_run(dmpt_handle h, const Layout& L, const double* H1, const d
   return DMPT_OK;
 }
 
-double layer_alg_flops(double n, int prec, bool square, int active) {
+double layer_alg_flops(double n, int prec, bool square, int active, int active2 = 0) {
+  // dual: square A + B + B^T (2 products), response A + B + C (3), second-order
+  // term S0 S2 (3, its transpose free) + S1 S1 (2, like the square)
   const double n3x2 = 2.0 * n * n * n;
-  if (prec >= DMPT_DUAL_FP16) return ((square ? 2.0 : 0.0) + 3.0 * active) * n3x2;
-  return ((square ? 1.0 : 0.0) + 1.0 * active) * n3x2;
+  if (prec >= DMPT_DUAL_FP16)
+    return ((square ? 2.0 : 0.0) + 3.0 * active + 5.0 * active2) * n3x2;
+  return ((square ? 1.0 : 0.0) + 1.0 * active + 2.0 * active2) * n3x2;
 }
 
 double layer_mma_flops(const Layout& L, double per /* one full-K single-term pass */,
-                       bool square, int active) {
+                       bool square, int active, int active2 = 0) {
   const bool dual = L.precision >= DMPT_DUAL_FP16;
-  return (square ? (dual ? 3.0 : 1.0) : 0.0) * per + active * (dual ? 6.0 : 2.0) * per;
+  return (square ? (dual ? 3.0 : 1.0) : 0.0) * per + active * (dual ? 6.0 : 2.0) * per +
+         active2 * 9.0 * per;
 }
 
 }  // namespace
@@ -241,6 +249,7 @@ void dmpt_default_options(dmpt_options* o) {
   o->accum_chunk = 0;
   o->cta_pair = 1;
   o->k_snake = 1;
+  o->order = 1;
 }
 
 const char* dmpt_status_string(dmpt_status s) {
@@ -294,6 +303,7 @@ size_t dmpt_workspace_size(int64_t n, int k, const dmpt_options* o) {
   dmpt_default_options(&d);
   if (!o) o = &d;
   if (n < 1 || k < 0 || k > DMPT_MAX_K || !valid_options(o)) return 0;
+  if (o->order == 2 && (2 * k > DMPT_MAX_K || k < 1)) return 0;
   return layout_for(n, k, o).total;
 }
 
@@ -309,15 +319,11 @@ dmpt_status dmpt_bounds(dmpt_handle h, const double* H, int64_t n, int64_t ld, d
   return DMPT_OK;
 }
 
-dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, int k,
-                              int64_t n, int64_t ld, int64_t n_occ, const dmpt_options* o,
-                              double* P, double* P1, dmpt_info* info, void* workspace,
-                              size_t ws_bytes, void* stream) {
-  if (!h) return DMPT_EINVAL;
-  h->err[0] = 0;
-  dmpt_options defaults;
-  dmpt_default_options(&defaults);
-  if (!o) o = &defaults;
+static dmpt_status forward_impl(dmpt_handle h, const double* H, const double* H1, int k,
+                                int64_t n, int64_t ld, int64_t n_occ, const dmpt_options* o,
+                                double* P, double* P1, double* P2, dmpt_info* info,
+                                void* workspace, size_t ws_bytes, void* stream) {
+  const int order = o->order;
   if (info) memset(info, 0, sizeof(*info));
   if (k < 0 || k > DMPT_MAX_K) return fail(h, DMPT_EINVAL, "dmpt_sp2_response: k out of range%s");
   if (!H || (k > 0 && (!H1 || !P1)) || (k == 0 && !P))
@@ -325,6 +331,13 @@ dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, 
   if (n < 1 || ld < n) return fail(h, DMPT_EINVAL, "dmpt_sp2_response: need n >= 1, ld >= n%s");
   if (n_occ < 0 || n_occ > n) return fail(h, DMPT_EINVAL, "dmpt_sp2_response: n_occ out of [0, n]%s");
   if (!valid_options(o)) return fail(h, DMPT_EINVAL, "dmpt_sp2_response: invalid options%s");
+  if (order == 2) {
+    if (k < 1 || 2 * k > DMPT_MAX_K || !P2)
+      return fail(h, DMPT_EINVAL, "dmpt_sp2_response2: need 1 <= k <= DMPT_MAX_K / 2 and P2%s");
+    if (o->precision < DMPT_DUAL_FP16 || o->ckpt_every != 0)
+      return fail(h, DMPT_EUNSUPPORTED,
+                  "dmpt_sp2_response2: the second order needs a dual precision and no tape%s");
+  }
   if (o->ckpt_every != 0 && o->precision < DMPT_DUAL_FP16)
     return fail(h, DMPT_EUNSUPPORTED,
                 "dmpt_sp2_response: the S0 tape (ckpt_every = 1) needs a dual precision%s");
@@ -333,6 +346,7 @@ dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, 
 
   if (n_occ == 0 || n_occ == n) {
     cudaError_t e = launch_trivial(n, k, ld, n_occ == n, P, P1, s);
+    if (e == cudaSuccess && order == 2) e = launch_trivial(n, k, ld, 0, nullptr, P2, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(h, e, "dmpt_sp2_response (trivial)");
     if (info) {
@@ -354,13 +368,14 @@ dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, 
   State* st = (State*)(base + L.off_state);
   cudaError_t e = cudaMemsetAsync(st, 0, sizeof(State), s);
   if (e != cudaSuccess) return cuda_fail(h, e, "state reset");
-  state_init_kernel<<<1, 1, 0, s>>>(st, k, o->max_layers, o->precision, (double)n_occ, o->c_pt,
-                                    o->c_d0, L.tape_states > 0 ? 1 : 0, 4 * (1 + L.k),
-                                    L.tape_states, L.k, n);
+  state_init_kernel<<<1, 1, 0, s>>>(st, order == 2 ? 2 * k : k, o->max_layers, o->precision,
+                                    (double)n_occ, o->c_pt, o->c_d0, L.tape_states > 0 ? 1 : 0,
+                                    4 * (1 + L.k), L.tape_states, L.k, n, order, k);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "state init");
   if ((e = launch_bounds(H, n, ld, &st->eps1, s)) != cudaSuccess) return cuda_fail(h, e, "bounds");
   const int init_blocks = 1024;
-  if ((e = launch_init(L, workspace, H, H1, ld, k, init_blocks, s)) != cudaSuccess)
+  if ((e = launch_init(L, workspace, H, H1, ld, k, init_blocks, s, 0, nullptr,
+                       order == 2 ? k : 0)) != cudaSuccess)
     return cuda_fail(h, e, "init");
   if ((e = launch_decide(L, workspace, kDecideInit, init_blocks, s)) != cudaSuccess)
     return cuda_fail(h, e, "decide(init)");
@@ -399,6 +414,8 @@ dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, 
   }
   if ((e = launch_finalize(L, workspace, P, P1, ld, k, s)) != cudaSuccess)
     return cuda_fail(h, e, "finalize");
+  if (order == 2 && (e = launch_finalize(L, workspace, nullptr, P2, ld, k, s, k + 1)) != cudaSuccess)
+    return cuda_fail(h, e, "finalize (second order)");
 
   State* host_state = new State;
   e = cudaMemcpyAsync(host_state, st, sizeof(State), cudaMemcpyDeviceToHost, s);
@@ -415,7 +432,8 @@ dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, 
     info->layers = S.layers_run;
     info->d0_layer = S.d0_layer;
     bool all1 = S.d0_conv != 0;
-    for (int j = 0; j < k; ++j) {
+    const int kj = order == 2 ? 2 * k : k;   // order 2: entries k .. 2k-1 are the S2 terms
+    for (int j = 0; j < kj; ++j) {
       info->d1_layer[j] = S.d1_layer[j];
       all1 = all1 && S.d1_conv[j];
       // last FroErr^(1) recorded for direction j
@@ -431,10 +449,13 @@ dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, 
     double mma = 0.0, alg = 0.0;
     for (int m = 1; m <= S.layers_run; ++m) {
       const bool sq = S.d0_layer == 0 || m <= S.d0_layer;
-      int active = 0;
-      for (int j = 0; j < k; ++j) active += (S.d1_conv[j] ? m <= S.d1_layer[j] : true) ? 1 : 0;
-      mma += layer_mma_flops(L, pass_flops, sq, active);
-      alg += layer_alg_flops((double)n, o->precision, sq, active);
+      int active = 0, active2 = 0;
+      for (int j = 0; j < kj; ++j) {
+        const int a = (S.d1_conv[j] ? m <= S.d1_layer[j] : true) ? 1 : 0;
+        if (j < k) active += a; else active2 += a;
+      }
+      mma += layer_mma_flops(L, pass_flops, sq, active, active2);
+      alg += layer_alg_flops((double)n, o->precision, sq, active, active2);
     }
     info->mma_flops = mma;
     info->alg_flops = alg;
@@ -457,6 +478,37 @@ dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, 
   if (status == DMPT_ENUMERIC) fail(h, status, "non-finite values or eps_N <= eps_1%s");
   if (status == DMPT_ENOTCONV) fail(h, status, "max_layers reached%s");
   return status;
+}
+
+dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, int k,
+                              int64_t n, int64_t ld, int64_t n_occ, const dmpt_options* o,
+                              double* P, double* P1, dmpt_info* info, void* workspace,
+                              size_t ws_bytes, void* stream) {
+  if (!h) return DMPT_EINVAL;
+  h->err[0] = 0;
+  dmpt_options defaults;
+  dmpt_default_options(&defaults);
+  if (!o) o = &defaults;
+  if (info) memset(info, 0, sizeof(*info));
+  if (o->order != 1)
+    return fail(h, DMPT_EINVAL, "dmpt_sp2_response: o->order must be 1 (use dmpt_sp2_response2)%s");
+  return forward_impl(h, H, H1, k, n, ld, n_occ, o, P, P1, nullptr, info, workspace, ws_bytes,
+                      stream);
+}
+
+dmpt_status dmpt_sp2_response2(dmpt_handle h, const double* H, const double* H1, int k,
+                               int64_t n, int64_t ld, int64_t n_occ, const dmpt_options* o,
+                               double* P, double* P1, double* P2, dmpt_info* info,
+                               void* workspace, size_t ws_bytes, void* stream) {
+  if (!h) return DMPT_EINVAL;
+  h->err[0] = 0;
+  dmpt_options opts;
+  dmpt_default_options(&opts);
+  if (o) opts = *o;
+  opts.order = 2;
+  if (info) memset(info, 0, sizeof(*info));
+  return forward_impl(h, H, H1, k, n, ld, n_occ, &opts, P, P1, P2, info, workspace, ws_bytes,
+                      stream);
 }
 
 dmpt_status dmpt_sp2_backward(dmpt_handle h, const double* G, int64_t n, int64_t ld,

@@ -57,6 +57,8 @@ struct State {
   int adj_m;            // adjoint: layer whose adjoint runs next
   int rp_lmax;          // replay: last layer whose sigma the forward recorded
   int rp_layers;        // replay: layers run
+  int order;            // 1: first-order response; 2: also the second-order term
+  int k1;               // first-order directions (jobs k1 + 1 .. 2 k1 are order 2)
   int64_t n;
   int cur1[kMaxK];
   int d1_conv[kMaxK];
@@ -106,7 +108,7 @@ cudaError_t launch_bounds(const double* H, int64_t n, int64_t ld, double* eps_ou
 // S1_j = -(H1_j + diag(shift_j)) / (eps_N - eps_1) (shift: k x n or NULL).
 cudaError_t launch_init(const Layout& L, void* ws, const double* H, const double* H1,
                         int64_t ld, int k, int blocks, cudaStream_t s, int first_m = 0,
-                        const double* shift = nullptr);
+                        const double* shift = nullptr, int k_zero = 0);
 // self-consistent response: v_j = gamma q_j;  q_j <- (1 - alpha) q_j + alpha diag(P1_j)
 // with red[j] = {||diag(P1_j) - q_j||^2, ||diag(P1_j)||^2}
 cudaError_t launch_scc_potential(const double* gamma, int64_t n, int64_t ld, const double* q,
@@ -126,8 +128,9 @@ cudaError_t launch_adj_init(const Layout& L, void* ws, const double* G, int64_t 
 // dL/dH = -Gbar / (eps_N - eps_1)
 cudaError_t launch_adj_finalize(const Layout& L, void* ws, double* dLdH, int64_t ld,
                                 cudaStream_t s);
+// P (if not NULL) and k_out response blocks from slots slot0 .. slot0 + k_out - 1
 cudaError_t launch_finalize(const Layout& L, void* ws, double* P, double* P1,
-                            int64_t ld, int k_out, cudaStream_t s);
+                            int64_t ld, int k_out, cudaStream_t s, int slot0 = 1);
 cudaError_t launch_trivial(int64_t n, int k, int64_t ld, int full, double* P,
                            double* P1, cudaStream_t s);
 int simt_tile(int precision);

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const d
                                                    const double* __restrict__ H1, int64_t n,
                                                    int64_t Np, int64_t ld, int k, int lk,
                                                    int first_m, const double* __restrict__ shift,
-                                                   double* partials, int64_t ptiles) {
+                                                   int k_zero, double* partials, int64_t ptiles) {
   // 32 x 32 tile pairs (bi <= bj): the upper tile is read row-wise (coalesced),
   // written in place and, through shared memory, transposed into the mirror
   // tile, so both triangles of S come from the upper triangle of the input.
@@ -200,6 +200,20 @@ __global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const d
       __syncthreads();
     }
   }
+  // second-order slots start at zero (a linear perturbation has H2 = 0)
+  for (int m = k + 1; m <= k + k_zero; ++m) {
+    T* dst = master + (size_t)m * mat;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)mat;
+         idx += (int64_t)gridDim.x * blockDim.x)
+      dst[idx] = (T)0;
+    if (threadIdx.x == 0) {
+      double* p = partials + ((size_t)m * ptiles + blockIdx.x) * kNQ;
+      p[kQTrace] = 0.0;
+      p[kQFroNew] = 0.0;
+      p[kQFroDiff] = 0.0;
+      p[kQBad] = 0.0;
+    }
+  }
   // job 0: trace, fro, bad (bad of the S1 part is reported under job 1 in replay)
   {
     double v[3] = {tr, f0, bad};
@@ -231,18 +245,18 @@ __global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const d
 
 cudaError_t launch_init(const Layout& L, void* ws, const double* H, const double* H1,
                         int64_t ld, int k, int blocks, cudaStream_t s, int first_m,
-                        const double* shift) {
+                        const double* shift, int k_zero) {
   char* base = (char*)ws;
   State* st = (State*)(base + L.off_state);
   double* partials = (double*)(base + L.off_partials);
   if (L.precision == DMPT_FP64)
     init_kernel<double><<<blocks, 256, 0, s>>>(st, (double*)(base + L.off_master), H, H1, L.n,
-                                               L.Np, ld, k, L.k, first_m, shift, partials,
-                                               L.partial_tiles);
+                                               L.Np, ld, k, L.k, first_m, shift, k_zero,
+                                               partials, L.partial_tiles);
   else
     init_kernel<float><<<blocks, 256, 0, s>>>(st, (float*)(base + L.off_master), H, H1, L.n,
-                                              L.Np, ld, k, L.k, first_m, shift, partials,
-                                              L.partial_tiles);
+                                              L.Np, ld, k, L.k, first_m, shift, k_zero,
+                                              partials, L.partial_tiles);
   return cudaGetLastError();
 }
 
@@ -349,10 +363,11 @@ __device__ void plan_layer(State* st, int n) {
   for (int j = 0; j < st->k; ++j) {
     st->plan_resp[j] = !st->d1_conv[j];
     // |S1_n|_max <= ||S1_n||_2 <= (2 ||S0||_2 + |1 - sigma|) ||S1_{n-1}||_2
-    //            <= 4.5 ||S1_{n-1}||_F   (spectrum of S0 within [-0.25, 1.25])
-    st->s1_exp_next[j] = st->precision == DMPT_DUAL_FP16
-                             ? fp16_exponent_for(4.5 * sqrt(st->s1_fro2[j]))
-                             : 0;
+    //            <= 4.5 ||S1_{n-1}||_F   (spectrum of S0 within [-0.25, 1.25]);
+    // second-order slots add ||S1 S1||_2 <= ||S1||_F^2 (twice, for 2 S - S^2)
+    double bound = 4.5 * sqrt(st->s1_fro2[j]);
+    if (st->order == 2 && j >= st->k1) bound += 2.0 * st->s1_fro2[j - st->k1];
+    st->s1_exp_next[j] = st->precision == DMPT_DUAL_FP16 ? fp16_exponent_for(bound) : 0;
   }
   st->n_layer = n;
 }
@@ -959,14 +974,16 @@ cudaError_t launch_adj_finalize(const Layout& L, void* ws, double* dLdH, int64_t
 
 template <typename T>
 __global__ void finalize_kernel(const State* st, const T* __restrict__ master, double* P,
-                                double* P1, int64_t n, int64_t Np, int64_t ld, int k) {
-  // k: layout slots; grid.y = 1 + the number of directions written out
+                                double* P1, int64_t n, int64_t Np, int64_t ld, int k, int slot0) {
+  // k: layout slots; grid.y = 1 + the number of blocks written to P1, which
+  // come from slots slot0, slot0 + 1, ...
   const size_t mat = (size_t)Np * Np;
-  const int m = blockIdx.y;
-  if (m == 0 && P == nullptr) return;
+  const int y = blockIdx.y;
+  if (y == 0 && P == nullptr) return;
+  const int m = y == 0 ? 0 : slot0 + y - 1;
   const int cur = m == 0 ? st->cur0 : st->cur1[m - 1];
   const T* src = master + (size_t)(cur * (1 + k) + m) * mat;
-  double* dst = m == 0 ? P : P1 + (size_t)(m - 1) * n * ld;
+  double* dst = y == 0 ? P : P1 + (size_t)(y - 1) * n * ld;
   const int64_t total = n * n;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -976,16 +993,16 @@ __global__ void finalize_kernel(const State* st, const T* __restrict__ master, d
 }
 
 cudaError_t launch_finalize(const Layout& L, void* ws, double* P, double* P1, int64_t ld,
-                            int k_out, cudaStream_t s) {
+                            int k_out, cudaStream_t s, int slot0) {
   char* base = (char*)ws;
   const State* st = (const State*)(base + L.off_state);
   dim3 grid(152 * 4, 1 + k_out);
   if (L.precision == DMPT_FP64)
     finalize_kernel<double><<<grid, 256, 0, s>>>(st, (const double*)(base + L.off_master), P,
-                                                 P1, L.n, L.Np, ld, L.k);
+                                                 P1, L.n, L.Np, ld, L.k, slot0);
   else
     finalize_kernel<float><<<grid, 256, 0, s>>>(st, (const float*)(base + L.off_master), P, P1,
-                                                L.n, L.Np, ld, L.k);
+                                                L.n, L.Np, ld, L.k, slot0);
   return cudaGetLastError();
 }
 

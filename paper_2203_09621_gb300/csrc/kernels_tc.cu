@@ -260,6 +260,36 @@ __device__ __forceinline__ int job_at(uint32_t mask, int idx) {
   return __ffs(m) - 1;
 }
 
+// Jobs of a layer: 0 = square of S0; 1..k1 = first-order response of
+// direction job - 1 (passes S0 S1, S1 S0); k1 + 1 .. 2 k1 (order 2) =
+// second-order term of direction job - 1 - k1 (passes S0 S2, S2 S0, S1 S1).
+// The job id is also the matrix slot of the result.
+__device__ __forceinline__ int job_passes(int job, int k1) {
+  return job == 0 ? 1 : (job <= k1 ? 2 : 3);
+}
+// operand slots (A, B) of pass `pass` of job `job`
+__device__ __forceinline__ void job_operands(int job, int pass, int k1, int* mA, int* mB) {
+  if (job == 0) {
+    *mA = 0;
+    *mB = 0;
+  } else if (pass == 0) {
+    *mA = 0;
+    *mB = job;
+  } else if (pass == 1) {
+    *mA = job;
+    *mB = 0;
+  } else {
+    *mA = job - k1;   // S1 of the same direction, times itself
+    *mB = job - k1;
+  }
+}
+// K-pass of accumulation chunk c (chunks never straddle passes); the
+// producer of the pair kernel runs the passes backwards in odd rounds
+__device__ __forceinline__ int chunk_pass(int c, int cpp, int passes, bool rev) {
+  const int p = c / cpp;
+  return rev ? passes - 1 - p : p;
+}
+
 // Operand slice of matrix m: S0 comes from the slice the control block
 // names (ping-pong slot, or a tape slice when the S0 states are kept for the
 // adjoint); S1_j from its ping-pong slot.
@@ -289,6 +319,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   const int write0 = st->plan_write0;
   const int s0e = st->s0_exp;
   const int z0c = st->z0_cur, z0n = st->z0_next;
+  const int k1 = st->order == 2 ? st->k1 : k;   // first-order directions
 
   const int64_t tiles = num_tiles(Np);
   const int64_t items = tiles * njobs;
@@ -349,12 +380,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int job = job_at(jmask, (int)(it / tiles));
         int I, J;
         tile_coords(it % tiles, &I, &J);
-        const int passes = job == 0 ? 1 : 2;
-        const int curj = job == 0 ? cur0 : st->cur1[job - 1];
+        const int passes = job_passes(job, k1);
         for (int pass = 0; pass < passes && ok; ++pass) {
-          // pass 0: A = S0 rows of I, B = S_job rows of J; pass 1: swapped
-          const int mA = pass == 0 ? 0 : job, bufA = pass == 0 ? cur0 : curj;
-          const int mB = pass == 0 ? job : 0, bufB = pass == 0 ? curj : cur0;
+          // A = rows I of slot mA, B = rows J of slot mB (B[k][j] = B[j][k])
+          int mA, mB;
+          job_operands(job, pass, k1, &mA, &mB);
+          const int bufA = mA == 0 ? cur0 : st->cur1[mA - 1];
+          const int bufB = mB == 0 ? cur0 : st->cur1[mB - 1];
           const int zAh = zop(mA, bufA, 0, k, z0c), zAl = zop(mA, bufA, 1, k, z0c);
           const int zBh = zop(mB, bufB, 0, k, z0c), zBl = zop(mB, bufB, 1, k, z0c);
           for (int kb = 0; kb < kblocks; ++kb) {
@@ -407,10 +439,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       bool ok = true;
       for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
         const int job = job_at(jmask, (int)(it / tiles));
-        const int nst = (job == 0 ? 1 : 2) * kblocks;
+        const int nst = job_passes(job, k1) * kblocks;
         uint32_t d = 0, acc = 0;
         for (int si = 0; si < nst; ++si) {
-          if (si % chunk == 0) {
+          const int sp = si % kblocks;   // stage within its K pass
+          if (sp % chunk == 0) {
             if (!mbar_wait(bar_tempty + 8 * ab, abphase ^ 1, limit_ns, abort_flag,
                            timeout_global)) {
               ok = false;
@@ -442,7 +475,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             stage = 0;
             phase ^= 1;
           }
-          if (si % chunk == chunk - 1 || si == nst - 1) {
+          if (sp % chunk == chunk - 1 || sp == kblocks - 1) {
             mma_commit(bar_tfull + 8 * ab);  // chunk accumulator ready
             if (++ab == 2) {
               ab = 0;
@@ -470,10 +503,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     int ab = 0;
     uint32_t abphase = 0;
     bool alive = true;
+    const bool crev = false;   // this kernel always runs the passes forwards
     for (int64_t it = blockIdx.x; it < items && alive; it += gridDim.x) {
       const int job = job_at(jmask, (int)(it / tiles));
-      const int nst = (job == 0 ? 1 : 2) * kblocks;
-      const int nchunks = (nst + chunk - 1) / chunk;
+      const int passes = job_passes(job, k1);
+      const int cpp = (kblocks + chunk - 1) / chunk;   // chunks per pass
+      const int nchunks = passes * cpp;
+      // exact power-of-two unscale of each pass's products
+      float upass[3];
+      {
+        const int ej = job == 0 ? s0e : st->s1_exp_cur[job - 1];
+        upass[0] = upass[1] = ldexpf(1.0f, -(s0e + ej));
+        upass[2] = job > k1 ? ldexpf(1.0f, -2 * st->s1_exp_cur[job - k1 - 1]) : 0.0f;
+      }
 
       // ---- sum the chunk accumulators in FP32 (round to nearest)
       float sum[128];
@@ -490,12 +532,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         fence_after();
         const uint32_t ta = tmem_base + tlane + (uint32_t)(ab * BN + half * 128);
+        const float u = upass[chunk_pass(ch, cpp, passes, crev)];
 #pragma unroll
         for (int cc = 0; cc < 8; ++cc) {
           uint32_t x[16];
           tmem_ld16(ta + 16 * cc, x);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) sum[16 * cc + i] += __uint_as_float(x[i]);
+          for (int i = 0; i < 16; ++i) sum[16 * cc + i] = fmaf(__uint_as_float(x[i]), u, sum[16 * cc + i]);
         }
         fence_before();
         __syncwarp();
@@ -512,10 +555,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       int I, J;
       tile_coords(t, &I, &J);
       const int curj = job == 0 ? cur0 : st->cur1[job - 1];
-      const int e_cur = job == 0 ? s0e : st->s1_exp_cur[job - 1];
       const int e_new = job == 0 ? s0e : st->s1_exp_next[job - 1];
-      const float unscale = ldexpf(1.0f, -(s0e + e_cur));   // exact powers of two
-      const float scale_new = ldexpf(1.0f, e_new);
+      const float scale_new = ldexpf(1.0f, e_new);   // exact power of two
       const float sg = (float)sigma, om = 1.0f - (float)sigma;
       const bool write = job != 0 || write0;
       const int r = I * BM + rloc;
@@ -543,7 +584,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         H16 nh[4], nl[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const float xv = sum[4 * g + i] * unscale;
+          const float xv = sum[4 * g + i];
           const int c = cb + i;
           const bool own = c >= r;
           const float w = (c == r) ? 1.0f : 2.0f;
@@ -738,6 +779,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
   const int write0 = st->plan_write0;
   const int s0e = st->s0_exp;
   const int z0c = st->z0_cur, z0n = st->z0_next;
+  const int k1 = st->order == 2 ? st->k1 : k;   // first-order directions
 
   const uint32_t rank = cluster_rank();
   const bool leader = rank == 0;
@@ -803,8 +845,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
         const int job = job_at(jmask, (int)(it / tiles));
         int I2, J;
         pair_tile_coords(it % tiles, &I2, &J);
-        const int passes = job == 0 ? 1 : 2;
-        const int curj = job == 0 ? cur0 : st->cur1[job - 1];
+        const int passes = job_passes(job, k1);
         const int rowA = I2 * 2 * BM + (int)rank * BM;
         const int rowB = J * BN + (int)rank * BM;
         // all pairs move through their tiles' K ranges in near lockstep; in
@@ -814,8 +855,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
         const bool rev = k_snake && (round & 1);
         for (int pp = 0; pp < passes && ok; ++pp) {
           const int pass = rev ? passes - 1 - pp : pp;
-          const int mA = pass == 0 ? 0 : job, bufA = pass == 0 ? cur0 : curj;
-          const int mB = pass == 0 ? job : 0, bufB = pass == 0 ? curj : cur0;
+          int mA, mB;
+          job_operands(job, pass, k1, &mA, &mB);
+          const int bufA = mA == 0 ? cur0 : st->cur1[mA - 1];
+          const int bufB = mB == 0 ? cur0 : st->cur1[mB - 1];
           const int zAh = zop(mA, bufA, 0, k, z0c), zAl = zop(mA, bufA, 1, k, z0c);
           const int zBh = zop(mB, bufB, 0, k, z0c), zBl = zop(mB, bufB, 1, k, z0c);
           for (int kq = 0; kq < kblocks; ++kq) {
@@ -862,10 +905,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
       bool ok = true;
       for (int64_t it = pair; it < items && ok; it += npairs) {
         const int job = job_at(jmask, (int)(it / tiles));
-        const int nst = (job == 0 ? 1 : 2) * kblocks;
+        const int nst = job_passes(job, k1) * kblocks;
         uint32_t d = 0, acc = 0;
         for (int si = 0; si < nst; ++si) {
-          if (si % chunk == 0) {
+          const int sp = si % kblocks;   // stage within its K pass
+          if (sp % chunk == 0) {
             if (!mbar_wait(bar_tempty + 8 * ab, abphase ^ 1, limit_ns, abort_flag,
                            timeout_global)) {
               ok = false;
@@ -897,7 +941,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
             stage = 0;
             phase ^= 1;
           }
-          if (si % chunk == chunk - 1 || si == nst - 1) {
+          if (sp % chunk == chunk - 1 || sp == kblocks - 1) {
             mma_commit_pair(bar_tfull + 8 * ab);    // chunk ready in both CTAs
             if (++ab == 2) {
               ab = 0;
@@ -925,10 +969,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     int ab = 0;
     uint32_t abphase = 0;
     bool alive = true;
-    for (int64_t it = pair; it < items && alive; it += npairs) {
+    int64_t eround = 0;
+    for (int64_t it = pair; it < items && alive; it += npairs, ++eround) {
+      const bool crev = k_snake && (eround & 1);   // same order as the producer
       const int job = job_at(jmask, (int)(it / tiles));
-      const int nst = (job == 0 ? 1 : 2) * kblocks;
-      const int nchunks = (nst + chunk - 1) / chunk;
+      const int passes = job_passes(job, k1);
+      const int cpp = (kblocks + chunk - 1) / chunk;   // chunks per pass
+      const int nchunks = passes * cpp;
+      // exact power-of-two unscale of each pass's products
+      float upass[3];
+      {
+        const int ej = job == 0 ? s0e : st->s1_exp_cur[job - 1];
+        upass[0] = upass[1] = ldexpf(1.0f, -(s0e + ej));
+        upass[2] = job > k1 ? ldexpf(1.0f, -2 * st->s1_exp_cur[job - k1 - 1]) : 0.0f;
+      }
       float sum[128];
 #pragma unroll
       for (int i = 0; i < 128; ++i) sum[i] = 0.0f;
@@ -941,12 +995,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
         }
         fence_after();
         const uint32_t ta = tmem_base + tlane + (uint32_t)(ab * BN + half * 128);
+        const float u = upass[chunk_pass(ch, cpp, passes, crev)];
 #pragma unroll
         for (int cc = 0; cc < 8; ++cc) {
           uint32_t x[16];
           tmem_ld16(ta + 16 * cc, x);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) sum[16 * cc + i] += __uint_as_float(x[i]);
+          for (int i = 0; i < 16; ++i) sum[16 * cc + i] = fmaf(__uint_as_float(x[i]), u, sum[16 * cc + i]);
         }
         fence_before();
         __syncwarp();
@@ -962,10 +1017,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
       int I2, J;
       pair_tile_coords(t, &I2, &J);
       const int curj = job == 0 ? cur0 : st->cur1[job - 1];
-      const int e_cur = job == 0 ? s0e : st->s1_exp_cur[job - 1];
       const int e_new = job == 0 ? s0e : st->s1_exp_next[job - 1];
-      const float unscale = ldexpf(1.0f, -(s0e + e_cur));
-      const float scale_new = ldexpf(1.0f, e_new);
+      const float scale_new = ldexpf(1.0f, e_new);   // exact power of two
       const float sg = (float)sigma, om = 1.0f - (float)sigma;
       const bool write = job != 0 || write0;
       const int r = I2 * 2 * BM + (int)rank * BM + rloc;
@@ -989,7 +1042,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
         H16 nh[4], nl[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const float xv = sum[4 * g + i] * unscale;
+          const float xv = sum[4 * g + i];
           const int c = cb + i;
           const bool own = c >= r;
           const float w = (c == r) ? 1.0f : 2.0f;

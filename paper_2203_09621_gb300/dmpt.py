@@ -40,7 +40,8 @@ class DmptOptions(ctypes.Structure):
         ("accum_chunk", ctypes.c_int),
         ("cta_pair", ctypes.c_int),
         ("k_snake", ctypes.c_int),
-        ("reserved", ctypes.c_int * 4),
+        ("order", ctypes.c_int),
+        ("reserved", ctypes.c_int * 3),
     ]
 
 
@@ -95,6 +96,10 @@ def load_library(path: str = LIB_PATH):
                                       ctypes.POINTER(DmptOptions), vp, vp,
                                       ctypes.POINTER(DmptInfo), vp, ctypes.c_size_t, vp]
     lib.dmpt_sp2_response.restype = c_int
+    lib.dmpt_sp2_response2.argtypes = [vp, vp, vp, c_int, i64, i64, i64,
+                                       ctypes.POINTER(DmptOptions), vp, vp, vp,
+                                       ctypes.POINTER(DmptInfo), vp, ctypes.c_size_t, vp]
+    lib.dmpt_sp2_response2.restype = c_int
     lib.dmpt_sp2_backward.argtypes = [vp, vp, i64, i64, ctypes.POINTER(DmptOptions), vp, vp,
                                       ctypes.c_size_t, vp]
     lib.dmpt_sp2_backward.restype = c_int
@@ -160,7 +165,7 @@ class Info:
 
 def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_scaling=1,
             sync_every=4, timing=False, timeout_s=2.0, accum_chunk=0,
-            cta_pair=1, k_snake=1, ckpt_every=0) -> DmptOptions:
+            cta_pair=1, k_snake=1, ckpt_every=0, order=1) -> DmptOptions:
     lib = load_library()
     o = DmptOptions()
     lib.dmpt_default_options(ctypes.byref(o))
@@ -176,6 +181,7 @@ def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_s
     o.cta_pair = int(cta_pair)
     o.k_snake = int(k_snake)
     o.ckpt_every = int(ckpt_every)
+    o.order = int(order)
     return o
 
 
@@ -280,6 +286,35 @@ class Context:
         if st != 0 and raise_on_error:
             self._check(st)
         return P, P1, inf
+
+    def sp2_response2(self, H, H1, n_occ, precision="dual_fp16", stream=None,
+                      raise_on_error=True, **kw):
+        """P, P1 and the second-order response P2 = (1/2) d^2P/dlambda^2.
+        Returns (P, P1 (k, n, n), P2 (k, n, n), Info); Info.d1_layer[k:] are
+        the second-order stop layers."""
+        import torch
+        H = H.contiguous()
+        if H1.dim() == 2:
+            H1 = H1.unsqueeze(0)
+        H1 = H1.contiguous()
+        k, n = H1.shape[0], H.shape[0]
+        opts = options(precision=precision, order=2, **kw)
+        P = torch.empty_like(H)
+        P1 = torch.empty_like(H1)
+        P2 = torch.empty_like(H1)
+        nbytes = self.workspace_size(n, k, opts)
+        if nbytes == 0:
+            raise DmptError(1, "invalid sizes or options")
+        ws_ptr, ws_len = self.workspace(nbytes)
+        info = DmptInfo()
+        s = stream if stream is not None else torch.cuda.current_stream(H.device)
+        st = self.lib.dmpt_sp2_response2(self.h, H.data_ptr(), H1.data_ptr(), k, n, n, int(n_occ),
+                                         ctypes.byref(opts), P.data_ptr(), P1.data_ptr(),
+                                         P2.data_ptr(), ctypes.byref(info), ctypes.c_void_p(ws_ptr),
+                                         ws_len, ctypes.c_void_p(s.cuda_stream))
+        if st != 0 and raise_on_error:
+            self._check(st)
+        return P, P1, P2, Info.from_c(info, 2 * k)
 
     def sp2_backward(self, G, workspace, out=None, stream=None, **kw):
         """dL/dH of L = Tr[G P] for the forward run that filled `workspace`
