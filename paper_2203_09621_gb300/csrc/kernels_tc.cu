@@ -441,9 +441,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int job = job_at(jmask, (int)(it / tiles));
         const int nst = job_passes(job, k1) * kblocks;
         uint32_t d = 0, acc = 0;
+        int sp = 0;   // stage within its K pass
+        int cp = 0;   // stage within its accumulation chunk
         for (int si = 0; si < nst; ++si) {
-          const int sp = si % kblocks;   // stage within its K pass
-          if (sp % chunk == 0) {
+          if (cp == 0) {
             if (!mbar_wait(bar_tempty + 8 * ab, abphase ^ 1, limit_ns, abort_flag,
                            timeout_global)) {
               ok = false;
@@ -475,7 +476,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             stage = 0;
             phase ^= 1;
           }
-          if (sp % chunk == chunk - 1 || sp == kblocks - 1) {
+          const bool chunk_end = cp == chunk - 1 || sp == kblocks - 1;
+          if (++cp == chunk || sp == kblocks - 1) cp = 0;
+          if (++sp == kblocks) sp = 0;
+          if (chunk_end) {
             mma_commit(bar_tfull + 8 * ab);  // chunk accumulator ready
             if (++ab == 2) {
               ab = 0;
@@ -907,9 +911,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
         const int job = job_at(jmask, (int)(it / tiles));
         const int nst = job_passes(job, k1) * kblocks;
         uint32_t d = 0, acc = 0;
+        int sp = 0;   // stage within its K pass
+        int cp = 0;   // stage within its accumulation chunk
         for (int si = 0; si < nst; ++si) {
-          const int sp = si % kblocks;   // stage within its K pass
-          if (sp % chunk == 0) {
+          if (cp == 0) {
             if (!mbar_wait(bar_tempty + 8 * ab, abphase ^ 1, limit_ns, abort_flag,
                            timeout_global)) {
               ok = false;
@@ -941,7 +946,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
             stage = 0;
             phase ^= 1;
           }
-          if (sp % chunk == chunk - 1 || sp == kblocks - 1) {
+          const bool chunk_end = cp == chunk - 1 || sp == kblocks - 1;
+          if (++cp == chunk || sp == kblocks - 1) cp = 0;
+          if (++sp == kblocks) sp = 0;
+          if (chunk_end) {
             mma_commit_pair(bar_tfull + 8 * ab);    // chunk ready in both CTAs
             if (++ab == 2) {
               ab = 0;
