@@ -247,6 +247,7 @@ def main():
     ap.add_argument("--input-backend", default="torch", choices=["torch", "numpy"])
     ap.add_argument("--cta-pair", type=int, default=1, choices=[0, 1])
     ap.add_argument("--k-snake", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--tile-band", type=int, default=8)
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the uneven-batch measurement (64 instances, n in [256, 2048])")
     ap.add_argument("--no-scc", action="store_true",
@@ -280,7 +281,8 @@ def main():
     P1 = torch.empty(k, n, n, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     kw = dict(precision=args.precision, out=(P, P1), stream=stream,
-              accum_chunk=args.accum_chunk, cta_pair=args.cta_pair, k_snake=args.k_snake)
+              accum_chunk=args.accum_chunk, cta_pair=args.cta_pair, k_snake=args.k_snake,
+              tile_band=args.tile_band)
 
     # warm-up (also sizes the workspace)
     for _ in range(args.warmup):

@@ -92,7 +92,10 @@ typedef struct {
                            between scheduling rounds for L2 reuse (default 1) */
   int order;            /* response order the workspace is sized for: 1
                            (default), 2 for dmpt_sp2_response2                */
-  int reserved[3];
+  int tile_band;        /* CTA-pair form: tile order in bands of this many
+                           256-column blocks, row-major inside a band (L2 reuse
+                           of operand panels); 0 = column-major (default 8)   */
+  int reserved[2];
 } dmpt_options;
 
 /* Filled on the host by dmpt_sp2_response (when info != NULL). */

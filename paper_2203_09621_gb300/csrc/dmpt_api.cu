@@ -62,6 +62,7 @@ bool valid_options(const dmpt_options* o) {
   if (o->cta_pair < 0 || o->cta_pair > 1) return false;
   if (o->k_snake < 0 || o->k_snake > 1) return false;
   if (o->order < 1 || o->order > 2) return false;
+  if (o->tile_band < 0 || o->tile_band > 1024) return false;
   return true;
 }
 
@@ -157,7 +158,7 @@ dmpt_status replay_run(dmpt_handle h, const Layout& L, const double* H1, const d
   while (launched < o->max_layers && !done) {
     for (int j = 0; j < o->sync_every && launched < o->max_layers; ++j) {
       if ((e = launch_layer_tc(L, workspace, s, o->timeout_s, o->accum_chunk, o->cta_pair,
-                               o->k_snake, &entries, &pass_flops)) != cudaSuccess)
+                               o->k_snake, o->tile_band, &entries, &pass_flops)) != cudaSuccess)
         return cuda_fail(h, e, "replay layer");
       if ((e = launch_decide(L, workspace, kDecideReplayLayer, entries, s)) != cudaSuccess)
         return cuda_fail(h, e, "replay decide");
@@ -250,6 +251,7 @@ void dmpt_default_options(dmpt_options* o) {
   o->cta_pair = 1;
   o->k_snake = 1;
   o->order = 1;
+  o->tile_band = 8;
 }
 
 const char* dmpt_status_string(dmpt_status s) {
@@ -399,7 +401,7 @@ static dmpt_status forward_impl(dmpt_handle h, const double* H, const double* H1
     for (int j = 0; j < o->sync_every && launched < max_layers; ++j) {
       if (o->timing) cudaEventRecord(h->events[2 * launched], s);
       e = dual ? launch_layer_tc(L, workspace, s, o->timeout_s, o->accum_chunk, o->cta_pair,
-                                 o->k_snake, &entries, &pass_flops)
+                                 o->k_snake, o->tile_band, &entries, &pass_flops)
                : launch_layer_simt(L, workspace, s, &entries, &pass_flops);
       if (e != cudaSuccess) return cuda_fail(h, e, "layer product");
       if (o->timing) cudaEventRecord(h->events[2 * launched + 1], s);
@@ -560,7 +562,7 @@ dmpt_status dmpt_sp2_backward(dmpt_handle h, const double* G, int64_t n, int64_t
   double pass_flops = 0.0;
   for (int m = fs.d0_updates; m >= 1; --m) {
     if ((e = launch_layer_tc(L, workspace, s, o->timeout_s, o->accum_chunk, o->cta_pair,
-                             o->k_snake, &entries, &pass_flops)) != cudaSuccess)
+                             o->k_snake, o->tile_band, &entries, &pass_flops)) != cudaSuccess)
       return cuda_fail(h, e, "adjoint layer");
     if ((e = launch_decide(L, workspace, kDecideAdjLayer, entries, s)) != cudaSuccess)
       return cuda_fail(h, e, "adjoint decide");
@@ -670,7 +672,7 @@ dmpt_status dmpt_sp2_response_batch(dmpt_handle h, int count, const double* cons
     cudaStream_t si = h->streams[i];
     void* ws = base + offs[i];
     cudaError_t r = dual ? launch_layer_tc(L[i], ws, si, o->timeout_s, o->accum_chunk,
-                                           o->cta_pair, o->k_snake, &entries[i], &pass_flops[i])
+                                           o->cta_pair, o->k_snake, o->tile_band, &entries[i], &pass_flops[i])
                          : launch_layer_simt(L[i], ws, si, &entries[i], &pass_flops[i]);
     if (r != cudaSuccess) return r;
     return launch_decide(L[i], ws, kDecideLayer, entries[i], si);

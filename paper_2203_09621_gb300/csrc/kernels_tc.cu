@@ -712,6 +712,40 @@ __device__ __forceinline__ void pair_tile_coords(int64_t t, int* I2, int* J) {
   *I2 = (int)(t - (int64_t)j * (j + 1) / 2);
 }
 
+// Banded order of the pair tiles (I2 <= J): column blocks are grouped into
+// bands of `band` blocks; inside a band the tiles run I2-major, so the pairs
+// working at the same time cover a compact block of rows and columns and
+// share their operand panels in L2.  band <= 0 keeps the plain J-major order.
+__device__ __forceinline__ void pair_tile_banded(int64_t t, int tj, int band, int* I2, int* J) {
+  if (band <= 0) {
+    pair_tile_coords(t, I2, J);
+    return;
+  }
+  int J0 = 0;
+  while (true) {
+    const int w = tj - J0 < band ? tj - J0 : band;
+    const int64_t cnt = (int64_t)J0 * w + (int64_t)w * (w + 1) / 2;   // tiles in this band
+    if (t < cnt || J0 + w >= tj) {
+      if (t < (int64_t)J0 * w) {          // rows above the band's diagonal block
+        *I2 = (int)(t / w);
+        *J = J0 + (int)(t % w);
+        return;
+      }
+      int64_t u = t - (int64_t)J0 * w;    // upper triangle of the w x w diagonal block
+      int r = 0;
+      while (u >= w - r) {
+        u -= w - r;
+        ++r;
+      }
+      *I2 = J0 + r;
+      *J = J0 + r + (int)u;
+      return;
+    }
+    t -= cnt;
+    J0 += w;
+  }
+}
+
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -766,7 +800,7 @@ template <bool BF16>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     layer_tc2_kernel(const __grid_constant__ CUtensorMap mapA, State* st, float* __restrict__ master,
                      uint16_t* __restrict__ ops, int64_t Np, int k, double* __restrict__ partials,
-                     int64_t ptiles, uint64_t limit_ns, int chunk, int k_snake) {
+                     int64_t ptiles, uint64_t limit_ns, int chunk, int k_snake, int band) {
   using CV = Cvt<BF16>;
   using H16 = typename CV::T;
   extern __shared__ uint8_t smem_raw[];
@@ -848,7 +882,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
       for (int64_t it = pair; it < items && ok; it += npairs, ++round) {
         const int job = job_at(jmask, (int)(it / tiles));
         int I2, J;
-        pair_tile_coords(it % tiles, &I2, &J);
+        pair_tile_banded(it % tiles, (int)(Np / BN), band, &I2, &J);
         const int passes = job_passes(job, k1);
         const int rowA = I2 * 2 * BM + (int)rank * BM;
         const int rowB = J * BN + (int)rank * BM;
@@ -1023,7 +1057,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 
       const int64_t t = it % tiles;
       int I2, J;
-      pair_tile_coords(t, &I2, &J);
+      pair_tile_banded(t, (int)(Np / BN), band, &I2, &J);
       const int curj = job == 0 ? cur0 : st->cur1[job - 1];
       const int e_new = job == 0 ? s0e : st->s1_exp_next[job - 1];
       const float scale_new = ldexpf(1.0f, e_new);   // exact power of two
@@ -1176,8 +1210,8 @@ bool make_map(CUtensorMap* map, void* base, int64_t Np, int slices, int box_rows
 int tc_tile() { return tc::BN; }
 
 cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double timeout_s,
-                            int accum_chunk_k, int cta_pair, int k_snake, int64_t* entries,
-                            double* pass_flops) {
+                            int accum_chunk_k, int cta_pair, int k_snake, int band,
+                            int64_t* entries, double* pass_flops) {
   using namespace tc;
   char* base = (char*)ws;
   const bool bf16 = L.precision == DMPT_DUAL_BF16;
@@ -1216,10 +1250,12 @@ cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double ti
     const int grid = (int)(2 * pairs);
     if (bf16)
       layer_tc2_kernel<true><<<grid, NUM_THREADS, P_SMEM_BYTES, s>>>(
-          mA, st, master, ops, L.Np, L.k, partials, L.partial_tiles, limit_ns, chunk, k_snake);
+          mA, st, master, ops, L.Np, L.k, partials, L.partial_tiles, limit_ns, chunk, k_snake,
+          band);
     else
       layer_tc2_kernel<false><<<grid, NUM_THREADS, P_SMEM_BYTES, s>>>(
-          mA, st, master, ops, L.Np, L.k, partials, L.partial_tiles, limit_ns, chunk, k_snake);
+          mA, st, master, ops, L.Np, L.k, partials, L.partial_tiles, limit_ns, chunk, k_snake,
+          band);
     if (entries) *entries = 2 * tiles;
     if (pass_flops) *pass_flops = (double)tiles * 2 * BM * BN * (double)L.Np * 2.0;
     return cudaGetLastError();

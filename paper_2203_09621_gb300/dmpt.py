@@ -41,7 +41,8 @@ class DmptOptions(ctypes.Structure):
         ("cta_pair", ctypes.c_int),
         ("k_snake", ctypes.c_int),
         ("order", ctypes.c_int),
-        ("reserved", ctypes.c_int * 3),
+        ("tile_band", ctypes.c_int),
+        ("reserved", ctypes.c_int * 2),
     ]
 
 
@@ -165,7 +166,7 @@ class Info:
 
 def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_scaling=1,
             sync_every=4, timing=False, timeout_s=2.0, accum_chunk=0,
-            cta_pair=1, k_snake=1, ckpt_every=0, order=1) -> DmptOptions:
+            cta_pair=1, k_snake=1, ckpt_every=0, order=1, tile_band=8) -> DmptOptions:
     lib = load_library()
     o = DmptOptions()
     lib.dmpt_default_options(ctypes.byref(o))
@@ -182,6 +183,7 @@ def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_s
     o.k_snake = int(k_snake)
     o.ckpt_every = int(ckpt_every)
     o.order = int(order)
+    o.tile_band = int(tile_band)
     return o
 
 
