@@ -95,7 +95,11 @@ typedef struct {
   int tile_band;        /* CTA-pair form: tile order in bands of this many
                            256-column blocks, row-major inside a band (L2 reuse
                            of operand panels); 0 = column-major (default 8)   */
-  int reserved[2];
+  int inject_stall;     /* test hook for the failure path (dual forms): 1 makes
+                           the layer product wait on a barrier nothing arrives
+                           on, so its bounded waits expire and the call returns
+                           DMPT_ETIMEOUT after about timeout_s; 0 (default)    */
+  int reserved[1];
 } dmpt_options;
 
 /* Filled on the host by dmpt_sp2_response (when info != NULL). */

@@ -63,6 +63,7 @@ bool valid_options(const dmpt_options* o) {
   if (o->k_snake < 0 || o->k_snake > 1) return false;
   if (o->order < 1 || o->order > 2) return false;
   if (o->tile_band < 0 || o->tile_band > 1024) return false;
+  if (o->inject_stall < 0 || o->inject_stall > 1) return false;
   return true;
 }
 
@@ -401,7 +402,8 @@ static dmpt_status forward_impl(dmpt_handle h, const double* H, const double* H1
     for (int j = 0; j < o->sync_every && launched < max_layers; ++j) {
       if (o->timing) cudaEventRecord(h->events[2 * launched], s);
       e = dual ? launch_layer_tc(L, workspace, s, o->timeout_s, o->accum_chunk, o->cta_pair,
-                                 o->k_snake, o->tile_band, &entries, &pass_flops)
+                                 o->k_snake, o->tile_band, &entries, &pass_flops,
+                                 o->inject_stall)
                : launch_layer_simt(L, workspace, s, &entries, &pass_flops);
       if (e != cudaSuccess) return cuda_fail(h, e, "layer product");
       if (o->timing) cudaEventRecord(h->events[2 * launched + 1], s);

@@ -138,7 +138,7 @@ int simt_tile(int precision);
 // ---- tensor-core path (kernels_tc.cu) ----
 cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double timeout_s,
                             int accum_chunk_k, int cta_pair, int k_snake, int band,
-                            int64_t* entries, double* pass_flops);
+                            int64_t* entries, double* pass_flops, int inject_stall = 0);
 int tc_tile();
 
 enum DecideMode {

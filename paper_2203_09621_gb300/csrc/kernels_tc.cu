@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     layer_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                     State* st, float* __restrict__ master, uint16_t* __restrict__ ops,
                     int64_t Np, int k, double* __restrict__ partials, int64_t ptiles,
-                    uint64_t limit_ns, int chunk) {
+                    uint64_t limit_ns, int chunk, int inject_stall) {
   using CV = Cvt<BF16>;
   using H16 = typename CV::T;
   extern __shared__ uint8_t smem_raw[];
@@ -436,7 +436,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       uint32_t phase = 0;
       int ab = 0;
       uint32_t abphase = 0;
-      bool ok = true;
+      // test hook: wait on a barrier nothing arrives on, so that the bounded
+      // waits of every role run out and the timeout path is exercised
+      bool ok = !(inject_stall &&
+                  !mbar_wait(bar_drain, 0, limit_ns, abort_flag, timeout_global));
       for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
         const int job = job_at(jmask, (int)(it / tiles));
         const int nst = job_passes(job, k1) * kblocks;
@@ -800,7 +803,8 @@ template <bool BF16>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     layer_tc2_kernel(const __grid_constant__ CUtensorMap mapA, State* st, float* __restrict__ master,
                      uint16_t* __restrict__ ops, int64_t Np, int k, double* __restrict__ partials,
-                     int64_t ptiles, uint64_t limit_ns, int chunk, int k_snake, int band) {
+                     int64_t ptiles, uint64_t limit_ns, int chunk, int k_snake, int band,
+                     int inject_stall) {
   using CV = Cvt<BF16>;
   using H16 = typename CV::T;
   extern __shared__ uint8_t smem_raw[];
@@ -940,7 +944,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
       uint32_t phase = 0;
       int ab = 0;
       uint32_t abphase = 0;
-      bool ok = true;
+      // test hook (see the single-CTA kernel)
+      bool ok = !(inject_stall &&
+                  !mbar_wait(bar_drain, 0, limit_ns, abort_flag, timeout_global));
       for (int64_t it = pair; it < items && ok; it += npairs) {
         const int job = job_at(jmask, (int)(it / tiles));
         const int nst = job_passes(job, k1) * kblocks;
@@ -1211,7 +1217,7 @@ int tc_tile() { return tc::BN; }
 
 cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double timeout_s,
                             int accum_chunk_k, int cta_pair, int k_snake, int band,
-                            int64_t* entries, double* pass_flops) {
+                            int64_t* entries, double* pass_flops, int inject_stall) {
   using namespace tc;
   char* base = (char*)ws;
   const bool bf16 = L.precision == DMPT_DUAL_BF16;
@@ -1251,11 +1257,11 @@ cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double ti
     if (bf16)
       layer_tc2_kernel<true><<<grid, NUM_THREADS, P_SMEM_BYTES, s>>>(
           mA, st, master, ops, L.Np, L.k, partials, L.partial_tiles, limit_ns, chunk, k_snake,
-          band);
+          band, inject_stall);
     else
       layer_tc2_kernel<false><<<grid, NUM_THREADS, P_SMEM_BYTES, s>>>(
           mA, st, master, ops, L.Np, L.k, partials, L.partial_tiles, limit_ns, chunk, k_snake,
-          band);
+          band, inject_stall);
     if (entries) *entries = 2 * tiles;
     if (pass_flops) *pass_flops = (double)tiles * 2 * BM * BN * (double)L.Np * 2.0;
     return cudaGetLastError();
@@ -1268,11 +1274,11 @@ cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double ti
   if (bf16)
     layer_tc_kernel<true><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(mA, mB, st, master, ops, L.Np,
                                                                 L.k, partials, L.partial_tiles,
-                                                                limit_ns, chunk);
+                                                                limit_ns, chunk, inject_stall);
   else
     layer_tc_kernel<false><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(mA, mB, st, master, ops, L.Np,
                                                                  L.k, partials, L.partial_tiles,
-                                                                 limit_ns, chunk);
+                                                                 limit_ns, chunk, inject_stall);
   if (entries) *entries = tiles;
   if (pass_flops) *pass_flops = (double)tiles * BM * BN * (double)L.Np * 2.0;
   return cudaGetLastError();

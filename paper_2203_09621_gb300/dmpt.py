@@ -42,7 +42,8 @@ class DmptOptions(ctypes.Structure):
         ("k_snake", ctypes.c_int),
         ("order", ctypes.c_int),
         ("tile_band", ctypes.c_int),
-        ("reserved", ctypes.c_int * 2),
+        ("inject_stall", ctypes.c_int),
+        ("reserved", ctypes.c_int * 1),
     ]
 
 
@@ -166,7 +167,8 @@ class Info:
 
 def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_scaling=1,
             sync_every=4, timing=False, timeout_s=2.0, accum_chunk=0,
-            cta_pair=1, k_snake=1, ckpt_every=0, order=1, tile_band=8) -> DmptOptions:
+            cta_pair=1, k_snake=1, ckpt_every=0, order=1, tile_band=8,
+            inject_stall=0) -> DmptOptions:
     lib = load_library()
     o = DmptOptions()
     lib.dmpt_default_options(ctypes.byref(o))
@@ -184,6 +186,7 @@ def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_s
     o.ckpt_every = int(ckpt_every)
     o.order = int(order)
     o.tile_band = int(tile_band)
+    o.inject_stall = int(inject_stall)
     return o
 
 
