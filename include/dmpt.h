@@ -271,6 +271,36 @@ dmpt_status dmpt_scc_response(dmpt_handle h, const double* H1_ext, const double*
                               int* iterations, double* residual, void* workspace,
                               size_t ws_bytes, void* stream);
 
+/* A sequence of problems held in host memory, solved one after another
+ * (Algorithms 1-3 for each, as dmpt_sp2_response with ld = n).  Inputs are
+ * copied in and results copied out on two copy streams of the handle, with
+ * two device buffer sets, so that the copy-in of instance i+1 and the
+ * copy-out of instance i-1 run while instance i is being solved.
+ *   count      instances (>= 0).
+ *   H_host     host array of `count` pointers to n x n row-major float64
+ *              matrices in host memory.
+ *   H1_host    host array of `count` pointers, each to k contiguous n x n
+ *              blocks (NULL allowed when k = 0).
+ *   P_host     host array of `count` output pointers (n x n), or NULL to
+ *              skip copying P out; entries may be NULL.
+ *   P1_host    host array of `count` output pointers (k blocks each).
+ *   info       host array of `count` entries (may be NULL).
+ *   workspace  dmpt_workspace_size_host() bytes of device memory, 256-byte
+ *              aligned: the solver's workspace plus the two buffer sets.
+ * Host buffers should be page-locked (cudaHostAlloc or cudaHostRegister) for
+ * the copies to overlap the solves; pageable buffers give the same results
+ * without the overlap.  First order only (o->order = 1).  `stream` is
+ * ordered before the first copy and after the last; the call returns when
+ * every result is in host memory.  Returns the first instance's non-OK
+ * status; the instances after it are not run. */
+size_t dmpt_workspace_size_host(int64_t n, int k, const dmpt_options* o);
+dmpt_status dmpt_sp2_response_host(dmpt_handle h, int count, const double* const* H_host,
+                                   const double* const* H1_host, int k, int64_t n,
+                                   int64_t n_occ, const dmpt_options* o,
+                                   double* const* P_host, double* const* P1_host,
+                                   dmpt_info* info, void* workspace, size_t ws_bytes,
+                                   void* stream);
+
 /* Static-scratch variant of dmpt_sp2_response for callers that cannot
  * allocate device memory (a host framework that owns every allocation, code
  * that must not allocate after start-up, plug-ins that only get input and

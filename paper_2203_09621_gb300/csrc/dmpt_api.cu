@@ -23,6 +23,10 @@ struct dmpt_ctx {
   std::vector<cudaEvent_t> joins;    // per-instance join events
   cudaStream_t origin = nullptr;     // capture / issue stream of batched solves
   cudaEvent_t fork = nullptr;
+  // host-buffer pipeline: copy-in / copy-out streams and their events
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_in[2] = {nullptr, nullptr}, ev_solved[2] = {nullptr, nullptr},
+              ev_out[2] = {nullptr, nullptr}, ev_end[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -296,6 +300,11 @@ dmpt_status dmpt_destroy(dmpt_handle h) {
     for (cudaStream_t st : h->streams) cudaStreamDestroy(st);
     if (h->origin) cudaStreamDestroy(h->origin);
     if (h->fork) cudaEventDestroy(h->fork);
+    if (h->copy_in) cudaStreamDestroy(h->copy_in);
+    if (h->copy_out) cudaStreamDestroy(h->copy_out);
+    for (cudaEvent_t e : {h->ev_start, h->ev_in[0], h->ev_in[1], h->ev_solved[0], h->ev_solved[1],
+                          h->ev_out[0], h->ev_out[1], h->ev_end[0], h->ev_end[1]})
+      if (e) cudaEventDestroy(e);
   }
   delete h;
   return DMPT_OK;
@@ -498,6 +507,124 @@ dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, 
     return fail(h, DMPT_EINVAL, "dmpt_sp2_response: o->order must be 1 (use dmpt_sp2_response2)%s");
   return forward_impl(h, H, H1, k, n, ld, n_occ, o, P, P1, nullptr, info, workspace, ws_bytes,
                       stream);
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t dmpt_workspace_size_host(int64_t n, int k, const dmpt_options* o) {
+  const size_t ws = dmpt_workspace_size(n, k, o);
+  if (!ws) return 0;
+  const size_t io = align256((size_t)n * n * sizeof(double) * (1 + k));
+  return align256(ws) + 4 * io;   // two input and two output buffer sets
+}
+
+dmpt_status dmpt_sp2_response_host(dmpt_handle h, int count, const double* const* H_host,
+                                   const double* const* H1_host, int k, int64_t n,
+                                   int64_t n_occ, const dmpt_options* o,
+                                   double* const* P_host, double* const* P1_host,
+                                   dmpt_info* info, void* workspace, size_t ws_bytes,
+                                   void* stream) {
+  if (!h) return DMPT_EINVAL;
+  h->err[0] = 0;
+  dmpt_options defaults;
+  dmpt_default_options(&defaults);
+  if (!o) o = &defaults;
+  if (info)
+    for (int i = 0; i < count; ++i) memset(&info[i], 0, sizeof(info[i]));
+  if (count < 0 || k < 0 || k > DMPT_MAX_K || n < 1)
+    return fail(h, DMPT_EINVAL, "dmpt_sp2_response_host: need count >= 0, 0 <= k <= DMPT_MAX_K, n >= 1%s");
+  if (o->order != 1)
+    return fail(h, DMPT_EINVAL, "dmpt_sp2_response_host: o->order must be 1%s");
+  if (count == 0) return DMPT_OK;
+  if (!H_host || (k > 0 && (!H1_host || !P1_host)) || (k == 0 && !P_host))
+    return fail(h, DMPT_EINVAL, "dmpt_sp2_response_host: null %s", "pointer array");
+  for (int i = 0; i < count; ++i)
+    if (!H_host[i] || (k > 0 && (!H1_host[i] || !P1_host[i])) || (k == 0 && !P_host[i]))
+      return fail(h, DMPT_EINVAL, "dmpt_sp2_response_host: null %s", "host buffer");
+  const size_t ws = dmpt_workspace_size(n, k, o);
+  if (!ws) return fail(h, DMPT_EINVAL, "dmpt_sp2_response_host: invalid options%s");
+  if (!workspace || ((uintptr_t)workspace) % 256 || ws_bytes < dmpt_workspace_size_host(n, k, o))
+    return fail(h, DMPT_EWORKSPACE, "dmpt_sp2_response_host: workspace too small or misaligned%s");
+  DeviceGuard g(h->device);
+  cudaError_t e = cudaSuccess;
+  if (!h->copy_in) {
+    if ((e = cudaStreamCreateWithFlags(&h->copy_in, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&h->copy_out, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(h, e, "copy stream create");
+    for (cudaEvent_t* ev : {&h->ev_start, &h->ev_in[0], &h->ev_in[1], &h->ev_solved[0],
+                            &h->ev_solved[1], &h->ev_out[0], &h->ev_out[1], &h->ev_end[0],
+                            &h->ev_end[1]})
+      if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(h, e, "copy event create");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nn = (size_t)n * n;
+  const size_t mat = nn * sizeof(double);
+  const size_t io = align256(mat * (1 + k));
+  char* bufs = (char*)workspace + align256(ws);
+  double* in[2] = {(double*)bufs, (double*)(bufs + io)};
+  double* out[2] = {(double*)(bufs + 2 * io), (double*)(bufs + 3 * io)};
+
+  // the copies start after the caller's earlier work on `stream`
+  if ((e = cudaEventRecord(h->ev_start, s)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(h->copy_in, h->ev_start, 0)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(h->copy_out, h->ev_start, 0)) != cudaSuccess)
+    return cuda_fail(h, e, "copy ordering");
+  // Instance i uses buffer set i % 2.  The copy-in of i + 1 is issued after
+  // the solve of i - 1 has returned (forward_impl synchronises `stream`), so
+  // the set it overwrites is no longer read.
+  auto copy_in = [&](int i) -> cudaError_t {
+    double* d = in[i & 1];
+    cudaError_t r = cudaMemcpyAsync(d, H_host[i], mat, cudaMemcpyHostToDevice, h->copy_in);
+    if (r == cudaSuccess && k > 0)
+      r = cudaMemcpyAsync(d + nn, H1_host[i], mat * k, cudaMemcpyHostToDevice, h->copy_in);
+    if (r == cudaSuccess) r = cudaEventRecord(h->ev_in[i & 1], h->copy_in);
+    return r;
+  };
+  dmpt_status status = DMPT_OK;
+  if ((e = copy_in(0)) != cudaSuccess) status = cuda_fail(h, e, "copy in");
+  for (int i = 0; i < count && status == DMPT_OK; ++i) {
+    const int b = i & 1;
+    if (i + 1 < count && (e = copy_in(i + 1)) != cudaSuccess) {
+      status = cuda_fail(h, e, "copy in");
+      break;
+    }
+    // inputs of i are on the device; the copy-out of i - 2 has left set b
+    if ((e = cudaStreamWaitEvent(s, h->ev_in[b], 0)) != cudaSuccess ||
+        (i >= 2 && (e = cudaStreamWaitEvent(s, h->ev_out[b], 0)) != cudaSuccess)) {
+      status = cuda_fail(h, e, "copy ordering");
+      break;
+    }
+    double* Pd = out[b];
+    double* P1d = out[b] + nn;
+    status = forward_impl(h, in[b], k > 0 ? in[b] + nn : nullptr, k, n, n, n_occ, o, Pd,
+                          k > 0 ? P1d : nullptr, nullptr, info ? &info[i] : nullptr, workspace,
+                          ws, s);
+    if (status != DMPT_OK) break;
+    if ((e = cudaEventRecord(h->ev_solved[b], s)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(h->copy_out, h->ev_solved[b], 0)) != cudaSuccess ||
+        (P_host && P_host[i] &&
+         (e = cudaMemcpyAsync(P_host[i], Pd, mat, cudaMemcpyDeviceToHost, h->copy_out)) !=
+             cudaSuccess) ||
+        (k > 0 && (e = cudaMemcpyAsync(P1_host[i], P1d, mat * k, cudaMemcpyDeviceToHost,
+                                       h->copy_out)) != cudaSuccess) ||
+        (e = cudaEventRecord(h->ev_out[b], h->copy_out)) != cudaSuccess) {
+      status = cuda_fail(h, e, "copy out");
+      break;
+    }
+  }
+  // every copy has finished before the call returns; `stream` is ordered after them
+  cudaError_t e1 = cudaEventRecord(h->ev_end[0], h->copy_in);
+  cudaError_t e2 = cudaEventRecord(h->ev_end[1], h->copy_out);
+  if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(s, h->ev_end[0], 0);
+  if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, h->ev_end[1], 0);
+  cudaError_t e3 = cudaStreamSynchronize(s);
+  if (status == DMPT_OK) {
+    if (e1 != cudaSuccess) return cuda_fail(h, e1, "copy join");
+    if (e2 != cudaSuccess) return cuda_fail(h, e2, "copy join");
+    if (e3 != cudaSuccess) return cuda_fail(h, e3, "copy join");
+  }
+  return status;
 }
 
 dmpt_status dmpt_sp2_response2(dmpt_handle h, const double* H, const double* H1, int k,

@@ -113,6 +113,13 @@ def load_library(path: str = LIB_PATH):
                                       ctypes.POINTER(DmptInfo), ctypes.POINTER(c_int),
                                       ctypes.POINTER(ctypes.c_double), vp, ctypes.c_size_t, vp]
     lib.dmpt_scc_response.restype = c_int
+    lib.dmpt_workspace_size_host.argtypes = [i64, c_int, ctypes.POINTER(DmptOptions)]
+    lib.dmpt_workspace_size_host.restype = ctypes.c_size_t
+    lib.dmpt_sp2_response_host.argtypes = [vp, c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int,
+                                           i64, i64, ctypes.POINTER(DmptOptions),
+                                           ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                           ctypes.POINTER(DmptInfo), vp, ctypes.c_size_t, vp]
+    lib.dmpt_sp2_response_host.restype = c_int
     lib.dmpt_workspace_size_batch.argtypes = [c_int, ctypes.POINTER(i64), c_int,
                                               ctypes.POINTER(DmptOptions)]
     lib.dmpt_workspace_size_batch.restype = ctypes.c_size_t
@@ -423,15 +430,60 @@ class Context:
             self._check(st)
         return P1, its.value, res.value, Info.from_c(info, k)
 
+    def solve_host(self, Hs, H1s, n_occ: int, P1_out=None, P_out=None, precision="dual_fp16",
+                   stream=None, raise_on_error=True, workspace=None, **kw):
+        """Instances held in host memory (dmpt_sp2_response_host): lists of
+        (n, n) and (k, n, n) float64 CPU tensors, pinned for the copies to
+        overlap the solves.  Results go to `P1_out` / `P_out` (lists of CPU
+        tensors, allocated pinned when None; P is copied out only when
+        `P_out` is given).  Returns (P list or None, P1 list, Info list)."""
+        import torch
+        count = len(Hs)
+        n = Hs[0].shape[0]
+        Hs = [h if h.is_contiguous() else h.contiguous() for h in Hs]
+        H1s = [(h1 if h1.dim() == 3 else h1.unsqueeze(0)) for h1 in H1s]
+        H1s = [h1 if h1.is_contiguous() else h1.contiguous() for h1 in H1s]
+        k = H1s[0].shape[0]
+        for h, h1 in zip(Hs, H1s):
+            if h.device.type != "cpu" or h1.device.type != "cpu" or h.dtype != torch.float64 \
+                    or h1.dtype != torch.float64 or h.shape != (n, n) or h1.shape != (k, n, n):
+                raise ValueError("solve_host wants float64 CPU tensors of one size")
+        if P1_out is None:
+            P1_out = [torch.empty(k, n, n, dtype=torch.float64).pin_memory() for _ in range(count)]
+        opts = options(precision=precision, **kw)
+        nbytes = self.lib.dmpt_workspace_size_host(n, k, ctypes.byref(opts))
+        if nbytes == 0:
+            raise DmptError(1, "invalid size or options")
+        if workspace is not None:
+            if workspace.numel() < nbytes + 256:
+                raise DmptError(2, "workspace tensor too small")
+            ws_ptr, ws_len = self._ws_ptr(workspace)
+        else:
+            ws_ptr, ws_len = self.workspace(nbytes)
+        dev = torch.device(f"cuda:{self.device}")
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        VP = ctypes.c_void_p * count
+        infos = (DmptInfo * count)()
+        st = self.lib.dmpt_sp2_response_host(
+            self.h, count, VP(*[h.data_ptr() for h in Hs]), VP(*[h1.data_ptr() for h1 in H1s]), k,
+            n, int(n_occ), ctypes.byref(opts),
+            VP(*[p.data_ptr() for p in P_out]) if P_out is not None else None,
+            VP(*[p.data_ptr() for p in P1_out]), infos, ctypes.c_void_p(ws_ptr), ws_len,
+            ctypes.c_void_p(s.cuda_stream))
+        if st != 0 and raise_on_error:
+            self._check(st)
+        return P_out, P1_out, [Info.from_c(infos[i], k) for i in range(count)]
+
     def sp2_response_host(self, H_host, H1_host, n_occ: int, precision="dual_fp16",
                           stream=None, **kw):
-        """End-to-end call from host (pinned CPU) tensors: copy in, solve, copy out."""
+        """One instance from host (CPU, ideally pinned) tensors through the C
+        ABI's host entry point: copy in, solve, copy out.  Returns (P, P1, Info)."""
         import torch
-        dev = torch.device(f"cuda:{self.device}")
-        H = H_host.to(dev, non_blocking=True)
-        H1 = H1_host.to(dev, non_blocking=True)
-        P, P1, inf = self.sp2_response(H, H1, n_occ, precision=precision, stream=stream, **kw)
-        return (P.to("cpu") if P is not None else None), P1.to("cpu"), inf
+        n = H_host.shape[0]
+        P = torch.empty(n, n, dtype=torch.float64).pin_memory()
+        Ps, P1s, infos = self.solve_host([H_host], [H1_host], n_occ, P_out=[P],
+                                         precision=precision, stream=stream, **kw)
+        return Ps[0], P1s[0], infos[0]
 
 
 _default_ctx: Optional[Context] = None

@@ -97,3 +97,22 @@ def test_host_only_calls(lib):
     assert lib.dmpt_sp2_response(None, None, None, 1, 4, 4, 2, None, None, None, None, None, 0,
                                  None) == 1
     assert lib.dmpt_destroy(None) == 1
+
+
+def test_host_pipeline_sizes_and_argument_errors(lib):
+    """dmpt_sp2_response_host: the workspace is the solver's plus two input
+    and two output buffer sets of (1 + k) n x n float64; argument errors are
+    reported before any device work."""
+    from paper_2203_09621_gb300 import dmpt
+
+    o = dmpt.DmptOptions()
+    lib.dmpt_default_options(ctypes.byref(o))
+    for n, k in ((1000, 1), (8192, 3), (300, 0)):
+        ws = lib.dmpt_workspace_size(n, k, ctypes.byref(o))
+        io = -(-(n * n * 8 * (1 + k)) // 256) * 256
+        assert lib.dmpt_workspace_size_host(n, k, ctypes.byref(o)) == -(-ws // 256) * 256 + 4 * io
+    assert lib.dmpt_workspace_size_host(0, 1, ctypes.byref(o)) == 0
+    assert lib.dmpt_workspace_size_host(100, 9, ctypes.byref(o)) == 0
+    # null handle
+    assert lib.dmpt_sp2_response_host(None, 1, None, None, 1, 4, 2, None, None, None, None,
+                                      None, 0, None) == 1
