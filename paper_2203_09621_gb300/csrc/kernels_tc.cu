@@ -78,6 +78,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]),
+      "f"(v[8]), "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]),
+      "f"(v[15])
+      : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // PTX helpers
 
@@ -699,6 +709,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 //   tempty[b] leader only: 16 arrivals (8 epilogue warps per CTA)
 
 constexpr int P_STAGES = 6;
+constexpr int64_t kRolledMaxN = 4096;   // padded sizes that use the rolled tile epilogue
 constexpr int P_STAGE_BYTES = 2 * A_BYTES + 2 * A_BYTES;   // A hi/lo + B-half hi/lo: 32 KB
 constexpr int P_SMEM_BYTES = P_STAGES * P_STAGE_BYTES + 1024 + 1024 + EPI_THREADS * 4 * 8;
 
@@ -799,7 +810,16 @@ __host__ __device__ constexpr uint32_t make_idesc_m256(int ab_type) {
          ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
 }
 
-template <bool BF16>
+// ROLLED selects how the tile epilogue reads the tile's sums.  false: from
+// the registers that accumulated the chunks, in a loop unrolled over the
+// 128 columns.  true: the sums are written back into the tensor-memory
+// buffer of the tile's last chunk and read 16 columns at a time in a rolled
+// loop (no register spills, far less code per tile); the buffer returns to
+// the MMA only after that loop, so the MMA can run one chunk ahead instead
+// of two.  The rolled form is faster when a launch has few tiles per pair;
+// on long launches the unrolled form's slower, HBM-bound tile epilogue keeps
+// the pairs closer to lockstep, which the operand panels' L2 reuse needs.
+template <bool BF16, bool ROLLED>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     layer_tc2_kernel(const __grid_constant__ CUtensorMap mapA, State* st, float* __restrict__ master,
                      uint16_t* __restrict__ ops, int64_t Np, int k, double* __restrict__ partials,
@@ -1051,6 +1071,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
           for (int i = 0; i < 16; ++i) sum[16 * cc + i] = fmaf(__uint_as_float(x[i]), u, sum[16 * cc + i]);
         }
+        if (ROLLED && ch + 1 == nchunks) break;   // keep the last chunk's buffer
         fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive_cluster(lead_tempty + 8 * ab);
@@ -1060,6 +1081,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
         }
       }
       if (!alive) break;
+      // rolled form: the tile's sums go back into its last chunk's buffer
+      [[maybe_unused]] uint32_t ta_sum = 0;
+      if constexpr (ROLLED) {
+        ta_sum = tmem_base + tlane + (uint32_t)(ab * BN + half * 128);
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) tmem_st16(ta_sum + 16 * cc, sum + 16 * cc);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      }
 
       const int64_t t = it % tiles;
       int I2, J;
@@ -1080,6 +1109,90 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 
       float fn_s = 0.0f, fn_c = 0.0f, fd = 0.0f, trf = 0.0f;
       int bad = 0;
+      // The column loop is written out twice (rolled / unrolled) rather than
+      // shared through a function: either form's register allocation depends
+      // on it, and both were measured in exactly this shape.
+      if constexpr (ROLLED) {
+#pragma unroll 1
+      for (int g16 = 0; g16 < 8; ++g16) {
+        uint32_t xs[16];
+        tmem_ld16(ta_sum + 16 * g16, xs);
+#pragma unroll
+      for (int gg = 0; gg < 4; ++gg) {
+        const int cb = c0 + 16 * g16 + 4 * gg;
+        if (r > cb + 3) continue;
+        const float4 o4 = *reinterpret_cast<const float4*>(Sold + cb);
+        const float old[4] = {o4.x, o4.y, o4.z, o4.w};
+        float nw[4];
+        H16 nh[4], nl[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float xv = __uint_as_float(xs[4 * gg + i]);
+          const int c = cb + i;
+          const bool own = c >= r;
+          const float w = (c == r) ? 1.0f : 2.0f;
+          bad += (own && !isfinite(xv)) ? 1 : 0;
+          const float dd = old[i] - xv;
+          fd = own ? fmaf(w * dd, dd, fd) : fd;
+          const float n1 = sg * xv + om * old[i];
+          nw[i] = n1;
+          if (own && write) {
+            const float p = w * n1 * n1;
+            const float e = w * fmaf(n1, n1, -n1 * n1);
+            const float tt = fn_s + p;
+            const float bp = tt - fn_s;
+            fn_c += (fn_s - (tt - bp)) + (p - bp) + e;
+            fn_s = tt;
+            if (c == r) trf += n1;
+          }
+          const float y = n1 * scale_new;
+          nh[i] = CV::to(y);
+          nl[i] = CV::to(y - CV::from(nh[i]));
+        }
+        if (!write) continue;
+        if (r <= cb) {
+          *reinterpret_cast<float4*>(Snew + row_off + cb) = make_float4(nw[0], nw[1], nw[2], nw[3]);
+          uint2 ph, pl2;
+          ph.x = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[0])) |
+                 ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[1])) << 16);
+          ph.y = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[2])) |
+                 ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[3])) << 16);
+          pl2.x = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[0])) |
+                  ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[1])) << 16);
+          pl2.y = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[2])) |
+                  ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[3])) << 16);
+          *reinterpret_cast<uint2*>(hi_new + row_off + cb) = ph;
+          *reinterpret_cast<uint2*>(lo_new + row_off + cb) = pl2;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            if (cb + i >= r) {
+              Snew[row_off + cb + i] = nw[i];
+              hi_new[row_off + cb + i] = nh[i];
+              lo_new[row_off + cb + i] = nl[i];
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int c = cb + i;
+          if (c > r) {
+            const size_t m = (size_t)c * Np + r;
+            Snew[m] = nw[i];
+            hi_new[m] = nh[i];
+            lo_new[m] = nl[i];
+          }
+        }
+      }
+      }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(lead_tempty + 8 * ab);
+        if (++ab == 2) {
+          ab = 0;
+          abphase ^= 1;
+        }
+      } else {
 #pragma unroll
       for (int g = 0; g < 32; ++g) {
         const int cb = c0 + 4 * g;
@@ -1146,6 +1259,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
             lo_new[m] = nl[i];
           }
         }
+      }
       }
       red[0 * EPI_THREADS + et] = (double)trf;
       red[1 * EPI_THREADS + et] = (double)fn_s + (double)fn_c;
@@ -1235,10 +1349,14 @@ cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double ti
                          SMEM_BYTES);
     cudaFuncSetAttribute(layer_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          SMEM_BYTES);
-    cudaFuncSetAttribute(layer_tc2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         P_SMEM_BYTES);
-    cudaFuncSetAttribute(layer_tc2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         P_SMEM_BYTES);
+    cudaFuncSetAttribute(layer_tc2_kernel<false, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
+    cudaFuncSetAttribute(layer_tc2_kernel<true, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
+    cudaFuncSetAttribute(layer_tc2_kernel<false, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
+    cudaFuncSetAttribute(layer_tc2_kernel<true, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
   }
   const uint64_t limit_ns = (uint64_t)(timeout_s * 1e9);
   int ck = accum_chunk_k > 0 ? accum_chunk_k : DEFAULT_CHUNK_K;
@@ -1254,14 +1372,13 @@ cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double ti
     int64_t pairs = sms / 2;
     if (pairs > max_items) pairs = max_items;
     const int grid = (int)(2 * pairs);
-    if (bf16)
-      layer_tc2_kernel<true><<<grid, NUM_THREADS, P_SMEM_BYTES, s>>>(
-          mA, st, master, ops, L.Np, L.k, partials, L.partial_tiles, limit_ns, chunk, k_snake,
-          band, inject_stall);
-    else
-      layer_tc2_kernel<false><<<grid, NUM_THREADS, P_SMEM_BYTES, s>>>(
-          mA, st, master, ops, L.Np, L.k, partials, L.partial_tiles, limit_ns, chunk, k_snake,
-          band, inject_stall);
+    // rolled tile epilogue up to n = 4096 (at most ~7 tiles per pair and job)
+    const bool rolled = L.Np <= kRolledMaxN;
+    auto kern = bf16 ? (rolled ? layer_tc2_kernel<true, true> : layer_tc2_kernel<true, false>)
+                     : (rolled ? layer_tc2_kernel<false, true> : layer_tc2_kernel<false, false>);
+    kern<<<grid, NUM_THREADS, P_SMEM_BYTES, s>>>(mA, st, master, ops, L.Np, L.k, partials,
+                                                 L.partial_tiles, limit_ns, chunk, k_snake, band,
+                                                 inject_stall);
     if (entries) *entries = 2 * tiles;
     if (pass_flops) *pass_flops = (double)tiles * 2 * BM * BN * (double)L.Np * 2.0;
     return cudaGetLastError();
