@@ -10,6 +10,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "dmpt_internal.cuh"
@@ -706,8 +707,19 @@ dmpt_status dmpt_sp2_backward(dmpt_handle h, const double* G, int64_t n, int64_t
   return DMPT_OK;
 }
 
-static size_t batch_scratch_bytes(int count) {
+// Batch scratch: [state offsets, all-done flag] [GroupInst table]
+// [GroupDecide table] [group timeout flag], each 256-byte aligned.
+static size_t batch_poll_bytes(int count) {
   return ((size_t)count * sizeof(long long) + 2 * sizeof(int) + 255) & ~size_t(255);
+}
+static size_t batch_ginst_bytes(int count) {
+  return ((size_t)count * sizeof(GroupInst) + 255) & ~size_t(255);
+}
+static size_t batch_gdec_bytes(int count) {
+  return ((size_t)count * sizeof(GroupDecide) + 255) & ~size_t(255);
+}
+static size_t batch_scratch_bytes(int count) {
+  return batch_poll_bytes(count) + batch_ginst_bytes(count) + batch_gdec_bytes(count) + 256;
 }
 
 size_t dmpt_workspace_size_batch(int count, const int64_t* n, int k, const dmpt_options* o) {
@@ -790,6 +802,14 @@ dmpt_status dmpt_sp2_response_batch(dmpt_handle h, int count, const double* cons
   for (int i = 0; i < count; ++i)
     if (active[i]) act_offs.push_back(offs[i]);
   const int n_active = (int)act_offs.size();
+  // dual precision on CTA pairs: one grouped launch per layer step for all
+  // instances (GroupInst table, batched decide); otherwise one launch per
+  // instance on its own stream
+  const bool grouped = dual && o->cta_pair && o->order == 1 && n_active > 0 &&
+                       n_active <= kGroupMax;
+  GroupInst* d_ginst = (GroupInst*)(base + batch_poll_bytes(count));
+  GroupDecide* d_gdec = (GroupDecide*)((char*)d_ginst + batch_ginst_bytes(count));
+  int* d_gtimeout = (int*)((char*)d_gdec + batch_gdec_bytes(count));
   if (n_active > 0 &&
       (e = cudaMemcpyAsync(d_offs, act_offs.data(), sizeof(long long) * n_active,
                            cudaMemcpyHostToDevice, h->origin)) != cudaSuccess)
@@ -827,7 +847,37 @@ dmpt_status dmpt_sp2_response_batch(dmpt_handle h, int count, const double* cons
     if ((e = launch_decide(L[i], ws, kDecideInit, 1024, si)) != cudaSuccess)
       return cuda_fail(h, e, "batch decide");
     if (dual && (e = launch_split(L[i], ws, 0, si)) != cudaSuccess) return cuda_fail(h, e, "split");
-    if ((e = issue_step(i)) != cudaSuccess) return cuda_fail(h, e, "batch first layer");
+    if (!grouped && (e = issue_step(i)) != cudaSuccess) return cuda_fail(h, e, "batch first layer");
+  }
+  int n_group = 0;
+  if (grouped) {
+    // instances by decreasing size, so the item pool starts with the longest tiles
+    std::vector<int> order;
+    for (int i = 0; i < count; ++i)
+      if (active[i]) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return L[a].Np > L[b].Np; });
+    std::vector<GroupInst> gi(order.size());
+    std::vector<GroupDecide> gd(order.size());
+    for (size_t j = 0; j < order.size(); ++j) {
+      const int i = order[j];
+      void* ws = base + offs[i];
+      if (!make_group_inst(L[i], ws, h->sm_count, &gi[j]))
+        return fail(h, DMPT_ECUDA, "dmpt_sp2_response_batch: %s", "tensor map encoding failed");
+      pair_tile_info(L[i], &entries[i], &pass_flops[i]);
+      gd[j].st = gi[j].st;
+      gd[j].partials = gi[j].partials;
+      gd[j].ptiles = gi[j].ptiles;
+      gd[j].entries = entries[i];
+    }
+    n_group = (int)order.size();
+    if ((e = cudaMemcpyAsync(d_ginst, gi.data(), sizeof(GroupInst) * gi.size(),
+                             cudaMemcpyHostToDevice, h->origin)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_gdec, gd.data(), sizeof(GroupDecide) * gd.size(),
+                             cudaMemcpyHostToDevice, h->origin)) != cudaSuccess ||
+        (e = cudaMemsetAsync(d_gtimeout, 0, sizeof(int), h->origin)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(h->origin)) != cudaSuccess)
+      return cuda_fail(h, e, "batch group tables");
   }
   // join everything into the origin stream
   for (int i = 0; i < count; ++i) {
@@ -840,7 +890,13 @@ dmpt_status dmpt_sp2_response_batch(dmpt_handle h, int count, const double* cons
   if ((e = cudaStreamBeginCapture(h->origin, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
     return cuda_fail(h, e, "batch capture");
   cudaError_t ce = cudaEventRecord(h->fork, h->origin);
-  for (int i = 0; i < count && ce == cudaSuccess; ++i) {
+  if (grouped) {
+    ce = launch_layer_tc_group(d_ginst, n_group, o->precision == DMPT_DUAL_BF16, d_gtimeout,
+                               o->timeout_s, o->accum_chunk, o->k_snake, o->tile_band,
+                               h->sm_count, h->origin);
+    if (ce == cudaSuccess) ce = launch_decide_group(d_gdec, n_group, d_gtimeout, h->origin);
+  }
+  for (int i = 0; i < count && ce == cudaSuccess && !grouped; ++i) {
     if (!active[i]) continue;
     ce = cudaStreamWaitEvent(h->streams[i], h->fork, 0);
     if (ce == cudaSuccess) ce = issue_step(i);
@@ -855,7 +911,7 @@ dmpt_status dmpt_sp2_response_batch(dmpt_handle h, int count, const double* cons
   e = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(h, e, "batch instantiate");
-  int steps = 1, all_done = n_active == 0 ? 1 : 0;
+  int steps = grouped ? 0 : 1, all_done = n_active == 0 ? 1 : 0;
   while (steps < o->max_layers && !all_done) {
     for (int j = 0; j < o->sync_every && steps < o->max_layers; ++j, ++steps) {
       if ((e = cudaGraphLaunch(exec, h->origin)) != cudaSuccess) {

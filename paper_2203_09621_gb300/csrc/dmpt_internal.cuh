@@ -8,6 +8,7 @@
 // exponents).  The product kernels read that plan from State at launch.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -140,6 +141,44 @@ cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double ti
                             int accum_chunk_k, int cta_pair, int k_snake, int band,
                             int64_t* entries, double* pass_flops, int inject_stall = 0);
 int tc_tile();
+
+// ---- grouped layer products of a batch (kernels_tc.cu) ----
+// One instance of a grouped launch: everything the pair kernel takes as
+// arguments for a single instance, in device memory (the tensor map first;
+// the struct takes the map's alignment).
+struct GroupInst {
+  CUtensorMap map;     // 3-D map over the instance's 16-bit operand slices
+  State* st;
+  float* master;
+  uint16_t* ops;
+  double* partials;
+  int64_t Np;
+  int64_t ptiles;      // partial-sum entries per job
+  int k;
+  int npairs;          // CTA pairs a single-instance launch would use (K-snake rounds)
+};
+// Per-instance inputs of the batched decide kernel.
+struct GroupDecide {
+  State* st;
+  const double* partials;
+  int64_t ptiles;
+  int64_t entries;
+};
+constexpr int kGroupMax = 1024;   // instances per grouped launch
+// Fills `gi` for the instance whose workspace is `ws` (false: no tensor map).
+bool make_group_inst(const Layout& L, void* ws, int sm_count, GroupInst* gi);
+// Partial-sum entries per job and the flops of one single-term pass of the
+// pair kernel for layout L.
+void pair_tile_info(const Layout& L, int64_t* entries, double* pass_flops);
+// One layer of every instance in `inst` (device array of `count`) in one
+// launch; a bounded wait that expires sets *group_timeout.
+cudaError_t launch_layer_tc_group(const GroupInst* inst, int count, bool bf16, int* group_timeout,
+                                  double timeout_s, int accum_chunk_k, int k_snake, int band,
+                                  int sm_count, cudaStream_t s);
+// Decide step of every instance (device array of `count`), one block each; a
+// set *group_timeout marks every instance timed out.
+cudaError_t launch_decide_group(const GroupDecide* args, int count, const int* group_timeout,
+                                cudaStream_t s);
 
 enum DecideMode {
   kDecideInit = 0,

@@ -391,10 +391,10 @@ __device__ void plan_replay(State* st, int m) {
   st->n_layer = m;
 }
 
-__global__ void __launch_bounds__(256) decide_kernel(State* st, const double* __restrict__ partials,
-                                                     int64_t ptiles, int64_t entries, int mode) {
-  __shared__ double red[kNQ * 256];
-  __shared__ double sums[kMaxK + 1][kNQ];
+// The decide step of one instance, run by one 256-thread block (red: kNQ x
+// 256 doubles, sums: (kMaxK + 1) x kNQ doubles of shared memory).
+__device__ void decide_body(State* st, const double* __restrict__ partials, int64_t ptiles,
+                            int64_t entries, int mode, double* red, double (*sums)[kNQ]) {
   if (st->done) return;
   const bool adj = mode == kDecideAdjInit || mode == kDecideAdjLayer;
   const bool rp = mode == kDecideReplayInit || mode == kDecideReplayLayer;
@@ -632,6 +632,31 @@ __global__ void __launch_bounds__(256) decide_kernel(State* st, const double* __
     return;
   }
   plan_layer(st, n + 1);
+}
+
+__global__ void __launch_bounds__(256) decide_kernel(State* st, const double* __restrict__ partials,
+                                                     int64_t ptiles, int64_t entries, int mode) {
+  __shared__ double red[kNQ * 256];
+  __shared__ double sums[kMaxK + 1][kNQ];
+  decide_body(st, partials, ptiles, entries, mode, red, sums);
+}
+
+// Layer decide of every instance of a grouped launch, one block each.
+__global__ void __launch_bounds__(256) decide_group_kernel(const GroupDecide* __restrict__ args,
+                                                           const int* __restrict__ group_timeout) {
+  __shared__ double red[kNQ * 256];
+  __shared__ double sums[kMaxK + 1][kNQ];
+  const GroupDecide a = args[blockIdx.x];
+  if (threadIdx.x == 0 && *group_timeout && !a.st->done) a.st->timeout_flag = 1;
+  __syncthreads();
+  decide_body(a.st, a.partials, a.ptiles, a.entries, kDecideLayer, red, sums);
+}
+
+cudaError_t launch_decide_group(const GroupDecide* args, int count, const int* group_timeout,
+                                cudaStream_t s) {
+  if (count < 1) return cudaSuccess;
+  decide_group_kernel<<<count, 256, 0, s>>>(args, group_timeout);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_decide(const Layout& L, void* ws, int mode, int64_t entries, cudaStream_t s) {

@@ -1296,6 +1296,476 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Grouped pair kernel: one layer of many instances of a batch in one launch.
+//
+// Each instance keeps its own control block, workspace and tensor map (a
+// GroupInst in device memory).  At entry every CTA reads each instance's
+// plan for this layer (which jobs run) and forms the prefix sums of the
+// instances' item counts (tiles x jobs) in shared memory; the items of all
+// instances make one pool that the 76 CTA pairs walk round-robin, as the
+// single-instance kernel walks its own items.  An item's instance is found
+// by binary search over the prefix sums.  Everything an item computes --
+// its tile, passes, accumulation chunks, K direction (the K-snake parity is
+// taken from the round the single-instance launch would run it in) and its
+// tile epilogue (the rolled form) -- is what the single-instance kernel
+// computes for it, so the results are the same bit for bit.
+
+// largest i with first[i] <= g (first[0] = 0 <= g)
+__device__ __forceinline__ int group_find(const int64_t* first, int count, int64_t g) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= g)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void tensormap_acquire(const void* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
+
+// The decoded item of a grouped launch.
+struct GroupItem {
+  int inst;        // instance
+  int job;
+  int passes;
+  int kblocks;
+  int64_t t;       // pair tile
+  bool rev;        // K-snake direction
+};
+
+__device__ __forceinline__ GroupItem group_item(const GroupInst* __restrict__ inst,
+                                                const int64_t* first, const uint32_t* jmask,
+                                                int count, int64_t g, int k_snake) {
+  GroupItem r;
+  r.inst = group_find(first, count, g);
+  const GroupInst& gi = inst[r.inst];
+  const int64_t loc = g - first[r.inst];
+  const int64_t tiles = num_pair_tiles(gi.Np);
+  r.job = job_at(jmask[r.inst], (int)(loc / tiles));
+  r.t = loc % tiles;
+  r.passes = job_passes(r.job, gi.k);
+  r.kblocks = (int)(gi.Np / BK);
+  r.rev = k_snake && ((loc / gi.npairs) & 1);
+  return r;
+}
+
+template <bool BF16>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
+    layer_tc2_group_kernel(const GroupInst* __restrict__ inst, int count, int* group_timeout,
+                           uint64_t limit_ns, int chunk, int k_snake, int band) {
+  using CV = Cvt<BF16>;
+  using H16 = typename CV::T;
+  extern __shared__ uint8_t smem_raw[];
+
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw);
+  const uint32_t ring = base;
+  uint8_t* misc = gbase + P_STAGES * P_STAGE_BYTES;
+  int64_t* first = reinterpret_cast<int64_t*>(misc + 1024 + EPI_THREADS * 4 * 8);
+  uint32_t* jmask = reinterpret_cast<uint32_t*>(first + count + 1);
+
+  // ---- this layer's items of every instance (same values in every CTA:
+  //      the control blocks do not change during the launch)
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    const State* sti = inst[i].st;
+    uint32_t jm = 0;
+    if (!sti->done) {
+      jm = sti->plan_square ? 1u : 0u;
+      for (int j = 0; j < inst[i].k; ++j)
+        if (sti->plan_resp[j]) jm |= 1u << (1 + j);
+    }
+    jmask[i] = jm;
+    first[i + 1] = num_pair_tiles(inst[i].Np) * __popc(jm);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    first[0] = 0;
+    for (int i = 0; i < count; ++i) first[i + 1] += first[i];
+  }
+  __syncthreads();
+  const int64_t items = first[count];
+  if (items == 0) return;   // every CTA takes this exit together
+
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const int64_t pair = blockIdx.x >> 1;
+  const int64_t npairs = gridDim.x >> 1;
+
+  uint64_t* bars = reinterpret_cast<uint64_t*>(misc);
+  const uint32_t bar_full = smem_u32(bars);
+  const uint32_t bar_empty = bar_full + 8 * P_STAGES;
+  const uint32_t bar_tfull = bar_empty + 8 * P_STAGES;
+  const uint32_t bar_tempty = bar_tfull + 8 * 2;
+  const uint32_t bar_drain = bar_tempty + 8 * 2;
+  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(misc + 256);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(misc + 264);
+  double* red = reinterpret_cast<double*>(misc + 1024);
+  const uint32_t lead_full = map_to_rank(bar_full, 0);
+  const uint32_t lead_tempty = map_to_rank(bar_tempty, 0);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P_STAGES; ++s) {
+      mbar_init(bar_full + 8 * s, 1);
+      mbar_init(bar_empty + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bar_tfull + 8 * b, 1);
+      mbar_init(bar_tempty + 8 * b, 2 * EPI_WARPS);
+    }
+    mbar_init(bar_drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32((const void*)tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+  }
+  fence_before();
+  cluster_sync_all();   // barriers of both CTAs initialised, TMEM allocated
+  fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  int* timeout_global = group_timeout;
+
+  if (warp == 0) {
+    // ================= TMA producer (both CTAs load their own halves) ======
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      int last_inst = -1;
+      for (int64_t g = pair; g < items && ok; g += npairs) {
+        const GroupItem itm = group_item(inst, first, jmask, count, g, k_snake);
+        const GroupInst& gi = inst[itm.inst];
+        if (itm.inst != last_inst) {
+          tensormap_acquire(&gi.map);
+          last_inst = itm.inst;
+        }
+        const State* sti = gi.st;
+        const int k = gi.k;
+        const int cur0 = sti->cur0, z0c = sti->z0_cur;
+        int I2, J;
+        pair_tile_banded(itm.t, (int)(gi.Np / BN), band, &I2, &J);
+        const int rowA = I2 * 2 * BM + (int)rank * BM;
+        const int rowB = J * BN + (int)rank * BM;
+        for (int pp = 0; pp < itm.passes && ok; ++pp) {
+          const int pass = itm.rev ? itm.passes - 1 - pp : pp;
+          int mA, mB;
+          job_operands(itm.job, pass, k, &mA, &mB);
+          const int bufA = mA == 0 ? cur0 : sti->cur1[mA - 1];
+          const int bufB = mB == 0 ? cur0 : sti->cur1[mB - 1];
+          const int zAh = zop(mA, bufA, 0, k, z0c), zAl = zop(mA, bufA, 1, k, z0c);
+          const int zBh = zop(mB, bufB, 0, k, z0c), zBl = zop(mB, bufB, 1, k, z0c);
+          for (int kq = 0; kq < itm.kblocks; ++kq) {
+            const int kb = itm.rev ? itm.kblocks - 1 - kq : kq;
+            if (!mbar_wait(bar_empty + 8 * stage, phase ^ 1, limit_ns, abort_flag,
+                           timeout_global)) {
+              ok = false;
+              break;
+            }
+            const uint32_t sA = ring + stage * P_STAGE_BYTES;
+            if (leader) mbar_expect_tx(bar_full + 8 * stage, 2 * P_STAGE_BYTES);
+            const uint32_t fb = lead_full + 8 * stage;
+            tma_load_3d_pair(sA, &gi.map, kb * BK, rowA, zAh, fb);
+            tma_load_3d_pair(sA + A_BYTES, &gi.map, kb * BK, rowA, zAl, fb);
+            tma_load_3d_pair(sA + 2 * A_BYTES, &gi.map, kb * BK, rowB, zBh, fb);
+            tma_load_3d_pair(sA + 3 * A_BYTES, &gi.map, kb * BK, rowB, zBl, fb);
+            if (++stage == P_STAGES) {
+              stage = 0;
+              phase ^= 1;
+            }
+          }
+        }
+      }
+      // wait (bounded) for this CTA's copies to land before the CTA may exit
+      for (int i = 0; i < P_STAGES; ++i) {
+        const uint64_t t0 = gtimer();
+        while (!mbar_try_wait(bar_empty + 8 * stage, phase ^ 1) && gtimer() - t0 < limit_ns) {
+        }
+        if (++stage == P_STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ================= MMA issuer (leader CTA only) =================
+    if (leader && lane == 0) {
+      constexpr uint32_t idesc = make_idesc_m256(BF16 ? 1 : 0);
+      int stage = 0;
+      uint32_t phase = 0;
+      int ab = 0;
+      uint32_t abphase = 0;
+      bool ok = true;
+      for (int64_t g = pair; g < items && ok; g += npairs) {
+        const GroupItem itm = group_item(inst, first, jmask, count, g, k_snake);
+        const int kblocks = itm.kblocks;
+        const int nst = itm.passes * kblocks;
+        uint32_t d = 0, acc = 0;
+        int sp = 0;   // stage within its K pass
+        int cp = 0;   // stage within its accumulation chunk
+        for (int si = 0; si < nst; ++si) {
+          if (cp == 0) {
+            if (!mbar_wait(bar_tempty + 8 * ab, abphase ^ 1, limit_ns, abort_flag,
+                           timeout_global)) {
+              ok = false;
+              break;
+            }
+            fence_after();
+            d = tmem_base + (uint32_t)(ab * BN);
+            acc = 0;
+          }
+          if (!mbar_wait(bar_full + 8 * stage, phase, limit_ns, abort_flag, timeout_global)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t sA = ring + stage * P_STAGE_BYTES;
+          const uint64_t ah = sw64_desc(sA), al = sw64_desc(sA + A_BYTES);
+          const uint64_t bh = sw64_desc(sA + 2 * A_BYTES);
+          const uint64_t bl = sw64_desc(sA + 3 * A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t off = (uint64_t)((kk * 32) >> 4);
+            mma_f16_pair(d, ah + off, bh + off, idesc, acc);   // hi * hi
+            acc = 1;
+            mma_f16_pair(d, ah + off, bl + off, idesc, 1);     // hi * lo
+            mma_f16_pair(d, al + off, bh + off, idesc, 1);     // lo * hi
+          }
+          mma_commit_pair(bar_empty + 8 * stage);   // frees the stage in both CTAs
+          if (++stage == P_STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+          const bool chunk_end = cp == chunk - 1 || sp == kblocks - 1;
+          if (++cp == chunk || sp == kblocks - 1) cp = 0;
+          if (++sp == kblocks) sp = 0;
+          if (chunk_end) {
+            mma_commit_pair(bar_tfull + 8 * ab);    // chunk ready in both CTAs
+            if (++ab == 2) {
+              ab = 0;
+              abphase ^= 1;
+            }
+          }
+        }
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              bar_drain)
+          : "memory");
+      const uint64_t t0 = gtimer();
+      while (!mbar_try_wait(bar_drain, 0) && gtimer() - t0 < limit_ns) {
+      }
+    }
+  } else if (warp >= EPI_WARP0) {
+    // ================= epilogue (both CTAs, own 128 rows) =================
+    const int q = warp & 3;
+    const int half = (warp - EPI_WARP0) >> 2;
+    const int rloc = 32 * q + lane;
+    const int et = threadIdx.x - 32 * EPI_WARP0;
+    const uint32_t tlane = (uint32_t)(32 * q) << 16;
+    int ab = 0;
+    uint32_t abphase = 0;
+    bool alive = true;
+    for (int64_t g = pair; g < items && alive; g += npairs) {
+      const GroupItem itm = group_item(inst, first, jmask, count, g, k_snake);
+      const GroupInst& gi = inst[itm.inst];
+      const State* sti = gi.st;
+      const int job = itm.job;
+      const int k = gi.k;
+      const int passes = itm.passes;
+      const int cpp = (itm.kblocks + chunk - 1) / chunk;   // chunks per pass
+      const int nchunks = passes * cpp;
+      const int s0e = sti->s0_exp;
+      float upass[3];
+      {
+        const int ej = job == 0 ? s0e : sti->s1_exp_cur[job - 1];
+        upass[0] = upass[1] = ldexpf(1.0f, -(s0e + ej));
+        upass[2] = 0.0f;   // first-order jobs only
+      }
+      float sum[128];
+#pragma unroll
+      for (int i = 0; i < 128; ++i) sum[i] = 0.0f;
+      for (int ch = 0; ch < nchunks; ++ch) {
+        const bool ok =
+            mbar_wait(bar_tfull + 8 * ab, abphase, limit_ns, abort_flag, timeout_global);
+        if (!epi_all(ok && !*abort_flag)) {
+          alive = false;
+          break;
+        }
+        fence_after();
+        const uint32_t ta = tmem_base + tlane + (uint32_t)(ab * BN + half * 128);
+        const float u = upass[chunk_pass(ch, cpp, passes, itm.rev)];
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) {
+          uint32_t x[16];
+          tmem_ld16(ta + 16 * cc, x);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) sum[16 * cc + i] = fmaf(__uint_as_float(x[i]), u, sum[16 * cc + i]);
+        }
+        if (ch + 1 == nchunks) break;   // keep the last chunk's buffer
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(lead_tempty + 8 * ab);
+        if (++ab == 2) {
+          ab = 0;
+          abphase ^= 1;
+        }
+      }
+      if (!alive) break;
+      // the tile's sums go back into its last chunk's buffer (rolled epilogue)
+      const uint32_t ta_sum = tmem_base + tlane + (uint32_t)(ab * BN + half * 128);
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc) tmem_st16(ta_sum + 16 * cc, sum + 16 * cc);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+
+      const int64_t Np = gi.Np;
+      const size_t mat = (size_t)Np * Np;
+      int I2, J;
+      pair_tile_banded(itm.t, (int)(Np / BN), band, &I2, &J);
+      const int cur0 = sti->cur0;
+      const int curj = job == 0 ? cur0 : sti->cur1[job - 1];
+      const int e_new = job == 0 ? s0e : sti->s1_exp_next[job - 1];
+      const float scale_new = ldexpf(1.0f, e_new);   // exact power of two
+      const float sigma = (float)sti->sigma_cur;
+      const float sg = sigma, om = 1.0f - sigma;
+      const bool write = job != 0 || sti->plan_write0;
+      const int r = I2 * 2 * BM + (int)rank * BM + rloc;
+      const int c0 = J * BN + half * 128;
+      const size_t row_off = (size_t)r * Np;
+      float* master = gi.master;
+      const float* Sold = master + (size_t)(curj * (1 + k) + job) * mat + row_off;
+      float* Snew = master + (size_t)((curj ^ 1) * (1 + k) + job) * mat;
+      const int zh_new = job == 0 ? sti->z0_next : zslice(curj ^ 1, job, 0, k);
+      H16* hi_new = reinterpret_cast<H16*>(gi.ops) + (size_t)zh_new * mat;
+      H16* lo_new = reinterpret_cast<H16*>(gi.ops) + (size_t)(zh_new + 1) * mat;
+
+      float fn_s = 0.0f, fn_c = 0.0f, fd = 0.0f, trf = 0.0f;
+      int bad = 0;
+#pragma unroll 1
+      for (int g16 = 0; g16 < 8; ++g16) {
+        uint32_t xs[16];
+        tmem_ld16(ta_sum + 16 * g16, xs);
+#pragma unroll
+        for (int gg = 0; gg < 4; ++gg) {
+          const int cb = c0 + 16 * g16 + 4 * gg;
+          if (r > cb + 3) continue;
+          const float4 o4 = *reinterpret_cast<const float4*>(Sold + cb);
+          const float old[4] = {o4.x, o4.y, o4.z, o4.w};
+          float nw[4];
+          H16 nh[4], nl[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float xv = __uint_as_float(xs[4 * gg + i]);
+            const int c = cb + i;
+            const bool own = c >= r;
+            const float w = (c == r) ? 1.0f : 2.0f;
+            bad += (own && !isfinite(xv)) ? 1 : 0;
+            const float dd = old[i] - xv;
+            fd = own ? fmaf(w * dd, dd, fd) : fd;
+            const float n1 = sg * xv + om * old[i];
+            nw[i] = n1;
+            if (own && write) {
+              const float p = w * n1 * n1;
+              const float e = w * fmaf(n1, n1, -n1 * n1);
+              const float tt = fn_s + p;
+              const float bp = tt - fn_s;
+              fn_c += (fn_s - (tt - bp)) + (p - bp) + e;
+              fn_s = tt;
+              if (c == r) trf += n1;
+            }
+            const float y = n1 * scale_new;
+            nh[i] = CV::to(y);
+            nl[i] = CV::to(y - CV::from(nh[i]));
+          }
+          if (!write) continue;
+          if (r <= cb) {
+            *reinterpret_cast<float4*>(Snew + row_off + cb) =
+                make_float4(nw[0], nw[1], nw[2], nw[3]);
+            uint2 ph, pl2;
+            ph.x = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[0])) |
+                   ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[1])) << 16);
+            ph.y = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[2])) |
+                   ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[3])) << 16);
+            pl2.x = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[0])) |
+                    ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[1])) << 16);
+            pl2.y = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[2])) |
+                    ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[3])) << 16);
+            *reinterpret_cast<uint2*>(hi_new + row_off + cb) = ph;
+            *reinterpret_cast<uint2*>(lo_new + row_off + cb) = pl2;
+          } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              if (cb + i >= r) {
+                Snew[row_off + cb + i] = nw[i];
+                hi_new[row_off + cb + i] = nh[i];
+                lo_new[row_off + cb + i] = nl[i];
+              }
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int c = cb + i;
+            if (c > r) {
+              const size_t m = (size_t)c * Np + r;
+              Snew[m] = nw[i];
+              hi_new[m] = nh[i];
+              lo_new[m] = nl[i];
+            }
+          }
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(lead_tempty + 8 * ab);
+      if (++ab == 2) {
+        ab = 0;
+        abphase ^= 1;
+      }
+      red[0 * EPI_THREADS + et] = (double)trf;
+      red[1 * EPI_THREADS + et] = (double)fn_s + (double)fn_c;
+      red[2 * EPI_THREADS + et] = (double)fd;
+      red[3 * EPI_THREADS + et] = (double)bad;
+      epi_sync();
+      for (int s2 = EPI_THREADS / 2; s2 > 0; s2 >>= 1) {
+        if (et < s2) {
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) red[qq * EPI_THREADS + et] += red[qq * EPI_THREADS + et + s2];
+        }
+        epi_sync();
+      }
+      if (et == 0) {
+        double* pp = gi.partials + ((size_t)job * gi.ptiles + 2 * itm.t + rank) * kNQ;
+        pp[kQTrace] = red[0];
+        pp[kQFroNew] = red[EPI_THREADS];
+        pp[kQFroDiff] = red[2 * EPI_THREADS];
+        pp[kQBad] = red[3 * EPI_THREADS];
+      }
+      epi_sync();
+    }
+  }
+
+  // ---- teardown: both CTAs done (or aborted); free TMEM of the pair
+  fence_before();
+  __syncthreads();
+  cluster_sync_all();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(TMEM_COLS));
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
@@ -1328,6 +1798,61 @@ bool make_map(CUtensorMap* map, void* base, int64_t Np, int slices, int box_rows
 }  // namespace tc
 
 int tc_tile() { return tc::BN; }
+
+void pair_tile_info(const Layout& L, int64_t* entries, double* pass_flops) {
+  const int64_t tiles = tc::num_pair_tiles(L.Np);
+  if (entries) *entries = 2 * tiles;
+  if (pass_flops) *pass_flops = (double)tiles * 2 * tc::BM * tc::BN * (double)L.Np * 2.0;
+}
+
+bool make_group_inst(const Layout& L, void* ws, int sm_count, GroupInst* gi) {
+  using namespace tc;
+  char* base = (char*)ws;
+  const bool bf16 = L.precision == DMPT_DUAL_BF16;
+  const int slices = 2 * (1 + L.k) * 2 + 2 * L.tape_states;
+  if (!make_map(&gi->map, base + L.off_ops16, L.Np, slices, BM, bf16)) return false;
+  gi->st = (State*)(base + L.off_state);
+  gi->master = (float*)(base + L.off_master);
+  gi->ops = (uint16_t*)(base + L.off_ops16);
+  gi->partials = (double*)(base + L.off_partials);
+  gi->Np = L.Np;
+  gi->ptiles = L.partial_tiles;
+  gi->k = L.k;
+  const int64_t max_items = num_pair_tiles(L.Np) * (1 + L.k);
+  int64_t pairs = sm_count / 2;
+  if (pairs > max_items) pairs = max_items;
+  gi->npairs = (int)pairs;
+  return true;
+}
+
+cudaError_t launch_layer_tc_group(const GroupInst* inst, int count, bool bf16, int* group_timeout,
+                                  double timeout_s, int accum_chunk_k, int k_snake, int band,
+                                  int sm_count, cudaStream_t s) {
+  using namespace tc;
+  if (count < 1 || count > kGroupMax) return cudaErrorInvalidValue;
+  const int smem = P_SMEM_BYTES + (count + 1) * (int)sizeof(int64_t) + count * (int)sizeof(uint32_t);
+  static bool attr = false;
+  if (!attr) {
+    const int max_smem = P_SMEM_BYTES + (kGroupMax + 1) * (int)sizeof(int64_t) +
+                         kGroupMax * (int)sizeof(uint32_t);
+    cudaFuncSetAttribute(layer_tc2_group_kernel<false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    cudaFuncSetAttribute(layer_tc2_group_kernel<true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    attr = true;
+  }
+  const uint64_t limit_ns = (uint64_t)(timeout_s * 1e9);
+  const int ck = accum_chunk_k > 0 ? accum_chunk_k : DEFAULT_CHUNK_K;
+  const int chunk = ck / BK < 1 ? 1 : ck / BK;
+  const int grid = 2 * (sm_count / 2);
+  if (bf16)
+    layer_tc2_group_kernel<true><<<grid, NUM_THREADS, smem, s>>>(inst, count, group_timeout,
+                                                                 limit_ns, chunk, k_snake, band);
+  else
+    layer_tc2_group_kernel<false><<<grid, NUM_THREADS, smem, s>>>(inst, count, group_timeout,
+                                                                  limit_ns, chunk, k_snake, band);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double timeout_s,
                             int accum_chunk_k, int cta_pair, int k_snake, int band,
