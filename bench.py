@@ -271,7 +271,10 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--k", type=int, default=K_DEFAULT)
     ap.add_argument("--precision", default="dual_fp16")
-    ap.add_argument("--forms", default="fp32", help="extra precision forms timed once (comma list)")
+    ap.add_argument("--forms", default="fp32,fp64",
+                    help="extra precision forms timed once (comma list); fp64 on a bounded sample")
+    ap.add_argument("--fp64-layers", type=int, default=2,
+                    help="layers of the FP64 form timed (its full solve takes minutes at n = 8192)")
     ap.add_argument("--oracle-layers", type=int, default=1)
     ap.add_argument("--oracle-n", type=int, default=4096,
                     help="size of the bounded oracle sample (same recipe)")
@@ -379,7 +382,7 @@ def main():
 
     # ---- other precision forms, one timed solve each (time-to-solution)
     forms = {}
-    for f in [x for x in args.forms.split(",") if x]:
+    for f in [x for x in args.forms.split(",") if x and x != "fp64"]:
         kwf = dict(kw, precision=f)
         ctx.sp2_response(H, H1, inst.n_occ, **kwf)  # warm-up
         torch.cuda.synchronize()
@@ -391,6 +394,19 @@ def main():
         fms = a.elapsed_time(b)
         forms[f] = {"ms": fms, "tflops": fi.alg_flops / (fms * 1e-3) / 1e12,
                     "layers": fi.layers, "d0_layer": fi.d0_layer}
+    if "fp64" in args.forms.split(",") and args.fp64_layers > 0:
+        # bounded sample: the first layers of the FP64 form (each a full D0
+        # layer), per-launch times by CUDA events; the time to solution is
+        # extrapolated to the dual form's layer count
+        kwf = dict(kw, precision="fp64", max_layers=args.fp64_layers, timing=True)
+        _, _, fi = ctx.sp2_response(H, H1, inst.n_occ, raise_on_error=False, **kwf)
+        torch.cuda.synchronize()
+        per_layer = fi.ms_layers / max(1, fi.timed_launches)
+        lay = infos[0].layers
+        forms["fp64"] = {"ms_per_layer": per_layer, "layers_timed": fi.timed_launches,
+                         "tflops": fi.alg_flops / (fi.ms_layers * 1e-3) / 1e12 if fi.ms_layers else None,
+                         "extrapolated_ms": per_layer * lay, "extrapolated_to_layers": lay,
+                         "sample": f"first {fi.timed_launches} layer(s) of the FP64 form at n={n}, k={k}"}
     # restore the dual-FP16 result in P1 for the accuracy check
     _, _, info = ctx.sp2_response(H, H1, inst.n_occ, **kw)
     torch.cuda.synchronize()

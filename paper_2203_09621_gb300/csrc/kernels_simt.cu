@@ -701,8 +701,18 @@ __device__ __forceinline__ int frag_index(int t, int m) {
   return m < H ? t * H + m : BT / 2 + t * H + (m - H);
 }
 
+// Two blocks per SM for the FP32 form (registers <= 128), one for FP64.
+template <typename T>
+struct SimtBlocks {
+  static constexpr int value = 2;
+};
+template <>
+struct SimtBlocks<double> {
+  static constexpr int value = 1;
+};
+
 template <typename T, int TM, int BK>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, SimtBlocks<T>::value)
     layer_simt_kernel(State* st, T* __restrict__ master, int64_t Np, int k,
                       double* __restrict__ partials, int64_t ptiles) {
   constexpr int BT = 16 * TM;
@@ -712,8 +722,9 @@ __global__ void __launch_bounds__(256)
   constexpr int NV = BT * BK / (256 * VW);     // vectors per thread per operand
   constexpr int PAD = VW;
 
-  __shared__ __align__(16) T As[BK][BT + PAD];
-  __shared__ __align__(16) T Bs[BK][BT + PAD];
+  // two stages: the next K block is stored while the current one is used
+  __shared__ __align__(16) T As[2][BK][BT + PAD];
+  __shared__ __align__(16) T Bs[2][BK][BT + PAD];
   __shared__ double red[4 * 256];
 
   if (st->done) return;
@@ -761,7 +772,7 @@ __global__ void __launch_bounds__(256)
         rb[v] = *reinterpret_cast<const V*>(B + (size_t)row * Np + kb + cq * VW);
       }
     };
-    auto sstore = [&]() {
+    auto sstore = [&](int buf) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const int idx = tid + 256 * v;
@@ -770,29 +781,34 @@ __global__ void __launch_bounds__(256)
         const T* pb = reinterpret_cast<const T*>(&rb[v]);
 #pragma unroll
         for (int e = 0; e < VW; ++e) {
-          As[cq * VW + e][row] = pa[e];
-          Bs[cq * VW + e][row] = pb[e];
+          As[buf][cq * VW + e][row] = pa[e];
+          Bs[buf][cq * VW + e][row] = pb[e];
         }
       }
     };
+    __syncthreads();   // the previous pass's last stage has been read
     gload(0);
+    sstore(0);
+    __syncthreads();
+    int buf = 0;
     for (int kb = 0; kb < Np; kb += BK) {
-      __syncthreads();
-      sstore();
-      __syncthreads();
-      if (kb + BK < Np) gload(kb + BK);
+      const bool more = kb + BK < Np;
+      if (more) gload(kb + BK);
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
         T a[TM], b[TM];
 #pragma unroll
-        for (int m = 0; m < TM; ++m) a[m] = As[kk][frag_index<T, TM>(ty, m)];
+        for (int m = 0; m < TM; ++m) a[m] = As[buf][kk][frag_index<T, TM>(ty, m)];
 #pragma unroll
-        for (int m = 0; m < TM; ++m) b[m] = Bs[kk][frag_index<T, TM>(tx, m)];
+        for (int m = 0; m < TM; ++m) b[m] = Bs[buf][kk][frag_index<T, TM>(tx, m)];
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
           for (int j = 0; j < TM; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
       }
+      if (more) sstore(buf ^ 1);   // the other stage was last read one step ago
+      __syncthreads();
+      buf ^= 1;
     }
   }
 
@@ -800,7 +816,12 @@ __global__ void __launch_bounds__(256)
   const T sg = (T)st->sigma_cur;
   const T om = (T)1 - sg;
   const bool write = job == 0 ? st->plan_write0 != 0 : true;
-  double tr = 0.0, fnew = 0.0, fdiff = 0.0, bad = 0.0;
+  double tr = 0.0, bad = 0.0;
+  // ||S_new||_F^2 and ||S_old - X||_F^2: in FP64 for the FP64 form; for the
+  // FP32 form as exact FP32 products summed with TwoSum compensation (the
+  // FP64 rate of the part is low), converted to FP64 once per thread
+  double fnew = 0.0, fdiff = 0.0;
+  float fn_s = 0.0f, fn_c = 0.0f, fd_s = 0.0f, fd_c = 0.0f;
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
     const int64_t r = (int64_t)I * BT + frag_index<T, TM>(ty, i);
@@ -810,19 +831,47 @@ __global__ void __launch_bounds__(256)
       if (r > c) continue;  // owned by the mirrored element
       const T x = acc[i][j];
       const T old = Sj[(size_t)r * Np + c];
-      const double w = (r == c) ? 1.0 : 2.0;
-      const double dd = (double)old - (double)x;
-      fdiff += w * dd * dd;
       if (!isfinite((double)x)) bad += 1.0;
+      const T nw = sg * x + om * old;
+      if constexpr (sizeof(T) == 8) {
+        const double w = (r == c) ? 1.0 : 2.0;
+        const double dd = (double)old - (double)x;
+        fdiff += w * dd * dd;
+        if (write) {
+          const double dn = (double)nw;
+          fnew += w * dn * dn;
+        }
+      } else {
+        const float w = (r == c) ? 1.0f : 2.0f;
+        const float dd = (float)old - (float)x;
+        {
+          const float p = w * dd * dd;
+          const float e = w * fmaf(dd, dd, -dd * dd);
+          const float tt = fd_s + p;
+          const float bp = tt - fd_s;
+          fd_c += (fd_s - (tt - bp)) + (p - bp) + e;
+          fd_s = tt;
+        }
+        if (write) {
+          const float n1 = (float)nw;
+          const float p = w * n1 * n1;
+          const float e = w * fmaf(n1, n1, -n1 * n1);
+          const float tt = fn_s + p;
+          const float bp = tt - fn_s;
+          fn_c += (fn_s - (tt - bp)) + (p - bp) + e;
+          fn_s = tt;
+        }
+      }
       if (write) {
-        const T nw = sg * x + om * old;
         out[(size_t)r * Np + c] = nw;
         if (r != c) out[(size_t)c * Np + r] = nw;
-        const double dn = (double)nw;
-        fnew += w * dn * dn;
-        if (r == c) tr += dn;
+        if (r == c) tr += (double)nw;
       }
     }
+  }
+  if constexpr (sizeof(T) != 8) {
+    fnew = (double)fn_s + (double)fn_c;
+    fdiff = (double)fd_s + (double)fd_c;
   }
   double v[4] = {tr, fnew, fdiff, bad};
   block_sum<4, 256>(v, red);

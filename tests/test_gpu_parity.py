@@ -246,3 +246,24 @@ def test_full_size_dipole3_n8192(ctx):
     for j in range(inst.k):
         assert abs(torch.trace(P1[j]).item()) < 1e-2
         assert torch.equal(P1[j], P1[j].T)
+
+
+@pytest.mark.parametrize("precision", ["dual_fp16", "dual_bf16"])
+def test_full_size_cfg2_n4096(ctx, precision):
+    """Config 2 at its full size (n = 4096, n_occ = 2048, gap 0.2, one H1): the
+    largest size on the rolled tile epilogue.  Whole P and P1 against the
+    oracle evaluated from the known eigendecomposition, plus the idempotency
+    identities P P = P and P P1 + P1 P = P1 on the GPU result."""
+    inst = make_workload(2, backend="torch", device="cuda")
+    assert inst.H.shape[0] == 4096
+    P, P1, info = ctx.sp2_response(inst.H, inst.H1, inst.n_occ, precision=precision)
+    torch.cuda.synchronize()
+    assert info.converged, info
+    Pr, P1r = oracle.response_from_eigs(inst.eps.cpu().numpy(), inst.Q.cpu().numpy(),
+                                        inst.H1[0].cpu().numpy(), inst.n_occ)
+    assert rel(P1[0].cpu().numpy(), P1r) < TOL[precision]
+    assert rel(P.cpu().numpy(), Pr) < TOL[precision]
+    PP = P @ P
+    assert (torch.linalg.norm(PP - P) / torch.linalg.norm(P)).item() < TOL[precision]
+    X1 = P @ P1[0] + P1[0] @ P
+    assert (torch.linalg.norm(X1 - P1[0]) / torch.linalg.norm(P1[0])).item() < TOL[precision]
