@@ -147,7 +147,11 @@ __global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const d
   // 32 x 32 tile pairs (bi <= bj): the upper tile is read row-wise (coalesced),
   // written in place and, through shared memory, transposed into the mirror
   // tile, so both triangles of S come from the upper triangle of the input.
-  __shared__ double tile[32][33];
+  // Each value is formed in FP64 and rounded once to T.  The squared norms
+  // are summed in FP64 for the FP64 form; for T = float, as exact FP32
+  // products with TwoSum compensation (the FP64 rate of the part is low).
+  constexpr bool F32 = sizeof(T) == 4;
+  __shared__ T tile[32][33];
   __shared__ double red[3 * 256];
   const double e1 = st->eps1, eN = st->epsN;
   const double w = 1.0 / (eN - e1);
@@ -157,15 +161,24 @@ __global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const d
   const int64_t pairs = TB * (TB + 1) / 2;
   double tr = 0.0, f0 = 0.0, bad = 0.0;
   double f1[kMaxK];
+  float f0s = 0.0f, f0c = 0.0f;
+  float f1s[kMaxK], f1c[kMaxK];
 #pragma unroll
-  for (int j = 0; j < kMaxK; ++j) f1[j] = 0.0;
+  for (int j = 0; j < kMaxK; ++j) {
+    f1[j] = 0.0;
+    f1s[j] = 0.0f;
+    f1c[j] = 0.0f;
+  }
   for (int64_t tp = blockIdx.x; tp < pairs; tp += gridDim.x) {
     // tile pair index -> (bi, bj), bj-major: tp = bj (bj + 1) / 2 + bi
     int64_t bj = (int64_t)((sqrt(8.0 * (double)tp + 1.0) - 1.0) * 0.5);
     while ((bj + 1) * (bj + 2) / 2 <= tp) ++bj;
     while (bj * (bj + 1) / 2 > tp) --bj;
     const int64_t bi = tp - bj * (bj + 1) / 2;
-    for (int m = first_m; m <= k; ++m) {
+    // m runs over a compile-time range so that the per-direction sums stay in registers
+#pragma unroll
+    for (int m = 0; m <= kMaxK; ++m) {
+      if (m < first_m || m > k) continue;   // uniform across the block
       const double* src = m == 0 ? H : H1 + (size_t)(m - 1) * n * ld;
       for (int i = 0; i < 4; ++i) {
         const int rl = ty + 8 * i;
@@ -176,7 +189,7 @@ __global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const d
           if (m > 0 && shift != nullptr && r == c) h += shift[(size_t)(m - 1) * n + r];
           v = m == 0 ? ((r == c ? eN : 0.0) - h) * w : -h * w;
         }
-        tile[rl][tx] = (double)(T)v;   // the stored (rounded) value
+        tile[rl][tx] = (T)v;   // the stored (rounded) value
       }
       __syncthreads();
       T* dst = master + (size_t)m * mat;   // buffer 0 (slots 0 .. lk)
@@ -185,20 +198,37 @@ __global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const d
         const int rl = ty + 8 * i;
         const int64_t r = bi * 32 + rl, c = bj * 32 + tx;
         // diagonal tile: the lower half mirrors the upper half
-        const double v = (bi < bj || rl <= tx) ? tile[rl][tx] : tile[tx][rl];
-        dst[(size_t)r * Np + c] = (T)v;
-        const double wgt = bi < bj ? 2.0 : 1.0;   // the mirror tile holds the same values
-        if (m == 0) {
-          if (r == c) tr += v;
-          f0 += wgt * v * v;
+        const T v = (bi < bj || rl <= tx) ? tile[rl][tx] : tile[tx][rl];
+        dst[(size_t)r * Np + c] = v;
+        if (m == 0 && r == c) tr += (double)v;
+        if constexpr (F32) {
+          const float wgt = bi < bj ? 2.0f : 1.0f;   // the mirror tile holds the same values
+          const float p = wgt * v * v;
+          const float e = wgt * fmaf(v, v, -v * v);
+          float& fs = m == 0 ? f0s : f1s[m - 1];
+          float& fc = m == 0 ? f0c : f1c[m - 1];
+          const float tt = fs + p;
+          const float bp = tt - fs;
+          fc += (fs - (tt - bp)) + (p - bp) + e;
+          fs = tt;
+          if (!isfinite(v)) bad += 1.0;
         } else {
-          f1[m - 1] += wgt * v * v;
+          const double wgt = bi < bj ? 2.0 : 1.0;
+          if (m == 0)
+            f0 += wgt * (double)v * (double)v;
+          else
+            f1[m - 1] += wgt * (double)v * (double)v;
+          if (!isfinite((double)v)) bad += 1.0;
         }
-        if (!isfinite(v)) bad += 1.0;
-        if (bi < bj) dst[(size_t)(bj * 32 + rl) * Np + bi * 32 + tx] = (T)tile[tx][rl];
+        if (bi < bj) dst[(size_t)(bj * 32 + rl) * Np + bi * 32 + tx] = tile[tx][rl];
       }
       __syncthreads();
     }
+  }
+  if constexpr (F32) {
+    f0 = (double)f0s + (double)f0c;
+#pragma unroll
+    for (int j = 0; j < kMaxK; ++j) f1[j] = (double)f1s[j] + (double)f1c[j];
   }
   // second-order slots start at zero (a linear perturbation has H2 = 0)
   for (int m = k + 1; m <= k + k_zero; ++m) {
