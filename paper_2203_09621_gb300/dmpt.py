@@ -269,14 +269,28 @@ class Context:
         if H1.dim() == 2:
             H1 = H1.unsqueeze(0)
         k = H1.shape[0]
-        H = H.contiguous()
-        H1 = H1.contiguous()
+        # a row-major view with a row stride ld >= n is passed as it is (the C
+        # ABI's leading dimension); H1 must then hold its k blocks n * ld apart
+        ld = H.stride(0)
+        strided = (H.stride(1) == 1 and ld >= n and
+                   (k == 0 or (H1.stride(2) == 1 and H1.stride(1) == ld and
+                               H1.stride(0) == n * ld)))
+        if not strided:
+            H = H.contiguous()
+            H1 = H1.contiguous()
+            ld = n
         opts = options(precision=precision, **kw)
         if out is None:
-            P1 = torch.empty(k, n, n, dtype=torch.float64, device=H.device) if k else None
-            P = torch.empty(n, n, dtype=torch.float64, device=H.device) if (want_P or k == 0) else None
+            def alloc(*shape):   # outputs share the inputs' leading dimension
+                full = torch.empty(*shape[:-1], ld, dtype=torch.float64, device=H.device)
+                return full[..., :shape[-1]]
+            P1 = alloc(k, n, n) if k else None
+            P = alloc(n, n) if (want_P or k == 0) else None
         else:
             P, P1 = out
+            for t, want in ((P, (ld, 1)), (P1, (n * ld, ld, 1))):
+                if t is not None and tuple(t.stride()) != want:
+                    raise ValueError("out tensors must have the inputs' leading dimension")
         nbytes = self.workspace_size(n, k, opts)
         if nbytes == 0:
             raise DmptError(1, "invalid sizes or options")
@@ -290,7 +304,7 @@ class Context:
         info = DmptInfo()
         s = stream if stream is not None else torch.cuda.current_stream(H.device)
         st = self.lib.dmpt_sp2_response(
-            self.h, H.data_ptr(), H1.data_ptr() if k else None, k, n, n, int(n_occ),
+            self.h, H.data_ptr(), H1.data_ptr() if k else None, k, n, ld, int(n_occ),
             ctypes.byref(opts), P.data_ptr() if P is not None else None,
             P1.data_ptr() if P1 is not None else None, ctypes.byref(info),
             ctypes.c_void_p(ws_ptr), ws_len, ctypes.c_void_p(s.cuda_stream))

@@ -70,3 +70,23 @@ def test_uneven_batch_64_instances(ctx):
         assert rel(P1s[i][0].cpu().numpy(), P1r) < 1e-3
         _, P1_single, _ = ctx.sp2_response(Hs[i], H1s[i], x.n_occ)
         assert torch.equal(P1s[i], P1_single)
+
+
+def test_grouped_bf16_matches_single_calls(ctx):
+    """The grouped batch kernel with BF16 operands: bit-exact against single
+    calls and within the BF16 tolerance of the oracle."""
+    sizes = [256, 300, 777, 1024, 513]
+    insts = [make_instance(f"g{i}", n, n // 2, (-2.0, -0.1), (0.1, 2.0), seed=9300 + i, k=2)
+             for i, n in enumerate(sizes)]
+    Hs = [torch.from_numpy(x.H).to(DEV) for x in insts]
+    H1s = [torch.from_numpy(x.H1).to(DEV) for x in insts]
+    Ps, P1s, infos = ctx.sp2_response_batch(Hs, H1s, [x.n_occ for x in insts], precision="dual_bf16")
+    torch.cuda.synchronize()
+    for i, x in enumerate(insts):
+        P, P1, info = ctx.sp2_response(Hs[i], H1s[i], x.n_occ, precision="dual_bf16")
+        torch.cuda.synchronize()
+        assert torch.equal(Ps[i], P) and torch.equal(P1s[i], P1), i
+        assert infos[i].converged and infos[i].layers == info.layers
+        for j in range(2):
+            _, P1r = oracle.response_sos(x.H, x.H1[j], x.n_occ)
+            assert rel(P1s[i][j].cpu().numpy(), P1r) < 5e-3

@@ -267,3 +267,39 @@ def test_full_size_cfg2_n4096(ctx, precision):
     assert (torch.linalg.norm(PP - P) / torch.linalg.norm(P)).item() < TOL[precision]
     X1 = P @ P1[0] + P1[0] @ P
     assert (torch.linalg.norm(X1 - P1[0]) / torch.linalg.norm(P1[0])).item() < TOL[precision]
+
+
+def test_max_directions_k8(ctx):
+    """DMPT_MAX_K = 8 responses sharing one S0 recursion (one square and
+    eight response jobs per D0 layer), each against the oracle."""
+    inst = make_workload(2, n=300)
+    n = inst.H.shape[0]
+    H1 = np.stack([sym_gauss(n, 8181 + j, 0.01) for j in range(8)])
+    P, P1, info = ctx.sp2_response(torch.from_numpy(inst.H).to(DEV), torch.from_numpy(H1).to(DEV),
+                                   inst.n_occ)
+    torch.cuda.synchronize()
+    assert info.converged
+    eps, V = np.linalg.eigh(inst.H)
+    for j in range(8):
+        _, P1r = oracle.response_from_eigs(eps, V, H1[j], inst.n_occ)
+        assert rel(P1[j].cpu().numpy(), P1r) < TOL["dual_fp16"], j
+
+
+@pytest.mark.parametrize("precision", ["dual_fp16", "fp32"])
+def test_leading_dimension(ctx, precision):
+    """Row-major inputs and outputs with ld > n (views into wider buffers)
+    give the same result as the contiguous call, bit for bit."""
+    inst = make_workload(2, n=520, k=2)
+    n, ld = 520, 537
+    Hb = torch.zeros(n, ld, dtype=torch.float64, device=DEV)
+    H1b = torch.zeros(2, n, ld, dtype=torch.float64, device=DEV)
+    Hb[:, :n] = torch.from_numpy(inst.H).to(DEV)
+    H1b[:, :, :n] = torch.from_numpy(inst.H1).to(DEV)
+    Hv, H1v = Hb[:, :n], H1b[:, :, :n]
+    assert Hv.stride(0) == ld
+    Pc, P1c, _ = ctx.sp2_response(torch.from_numpy(inst.H).to(DEV), torch.from_numpy(inst.H1).to(DEV),
+                                  inst.n_occ, precision=precision)
+    Pv, P1v, info = ctx.sp2_response(Hv, H1v, inst.n_occ, precision=precision)
+    torch.cuda.synchronize()
+    assert info.converged
+    assert torch.equal(Pc, Pv.contiguous()) and torch.equal(P1c, P1v.contiguous())
