@@ -810,6 +810,105 @@ __host__ __device__ constexpr uint32_t make_idesc_m256(int ab_type) {
          ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
 }
 
+// Rolled tile epilogue of one thread: its row r, columns c0 .. c0 + 127 of a
+// pair tile, whose sums the caller has written to tensor memory at ta_sum.
+// Reads the old master 32 columns at a time (eight float4 through the
+// read-only path: the old master is not written during the layer), so a tile
+// waits on four memory round trips instead of one per 4-column group; then
+// forms S_new = sigma X + (1 - sigma) S_old (Eq. (eq:Sn) / Eq. (dB)), its
+// FP16/BF16 hi/lo split (Sec. II C), the partial sums (||S_new||_F^2 with
+// TwoSum compensation, ||S_old - X||_F^2, trace, non-finite count) and stores
+// each owned element (column >= row) at (r, c) and (c, r).  OFF: the tile is
+// off the diagonal (every column > every row).
+template <class CV, bool OFF>
+__device__ __forceinline__ void rolled_tile_epilogue(
+    const uint32_t ta_sum, const float* __restrict__ Sold, float* Snew, typename CV::T* hi_new,
+    typename CV::T* lo_new, const size_t row_off, const int64_t Np, const int r, const int c0,
+    const float sg, const float om, const float scale_new, const bool write, float& fn_s,
+    float& fn_c, float& fd, float& trf, int& bad) {
+  using H16 = typename CV::T;
+#pragma unroll 1
+  for (int g32 = 0; g32 < 4; ++g32) {
+    float4 o4s[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      o4s[q] = __ldg(reinterpret_cast<const float4*>(Sold + c0 + 32 * g32 + 4 * q));
+#pragma unroll
+    for (int g2 = 0; g2 < 2; ++g2) {
+      uint32_t xs[16];
+      tmem_ld16(ta_sum + 32 * g32 + 16 * g2, xs);
+#pragma unroll
+      for (int gg = 0; gg < 4; ++gg) {
+        const int cb = c0 + 32 * g32 + 16 * g2 + 4 * gg;
+        if (!OFF && r > cb + 3) continue;
+        const float4 o4 = o4s[4 * g2 + gg];
+        const float old[4] = {o4.x, o4.y, o4.z, o4.w};
+        float nw[4];
+        H16 nh[4], nl[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float xv = __uint_as_float(xs[4 * gg + i]);
+          const int c = cb + i;
+          const bool own = OFF || c >= r;
+          const float w = (!OFF && c == r) ? 1.0f : 2.0f;
+          bad += (own && !isfinite(xv)) ? 1 : 0;
+          const float dd = old[i] - xv;
+          fd = own ? fmaf(w * dd, dd, fd) : fd;
+          const float n1 = sg * xv + om * old[i];
+          nw[i] = n1;
+          if (own && write) {
+            const float p = w * n1 * n1;
+            const float e = w * fmaf(n1, n1, -n1 * n1);
+            const float tt = fn_s + p;
+            const float bp = tt - fn_s;
+            fn_c += (fn_s - (tt - bp)) + (p - bp) + e;
+            fn_s = tt;
+            if (!OFF && c == r) trf += n1;
+          }
+          const float y = n1 * scale_new;
+          nh[i] = CV::to(y);
+          nl[i] = CV::to(y - CV::from(nh[i]));
+        }
+        if (!write) continue;
+        if (OFF || r <= cb) {
+          *reinterpret_cast<float4*>(Snew + row_off + cb) =
+              make_float4(nw[0], nw[1], nw[2], nw[3]);
+          uint2 ph, pl2;
+          ph.x = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[0])) |
+                 ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[1])) << 16);
+          ph.y = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[2])) |
+                 ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[3])) << 16);
+          pl2.x = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[0])) |
+                  ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[1])) << 16);
+          pl2.y = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[2])) |
+                  ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[3])) << 16);
+          *reinterpret_cast<uint2*>(hi_new + row_off + cb) = ph;
+          *reinterpret_cast<uint2*>(lo_new + row_off + cb) = pl2;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            if (cb + i >= r) {
+              Snew[row_off + cb + i] = nw[i];
+              hi_new[row_off + cb + i] = nh[i];
+              lo_new[row_off + cb + i] = nl[i];
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int c = cb + i;
+          if (OFF || c > r) {
+            const size_t m = (size_t)c * Np + r;
+            Snew[m] = nw[i];
+            hi_new[m] = nh[i];
+            lo_new[m] = nl[i];
+          }
+        }
+      }
+    }
+  }
+}
+
 // ROLLED selects how the tile epilogue reads the tile's sums.  false: from
 // the registers that accumulated the chunks, in a loop unrolled over the
 // 128 columns.  true: the sums are written back into the tensor-memory
@@ -1113,78 +1212,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
       // shared through a function: either form's register allocation depends
       // on it, and both were measured in exactly this shape.
       if constexpr (ROLLED) {
-#pragma unroll 1
-      for (int g16 = 0; g16 < 8; ++g16) {
-        uint32_t xs[16];
-        tmem_ld16(ta_sum + 16 * g16, xs);
-#pragma unroll
-      for (int gg = 0; gg < 4; ++gg) {
-        const int cb = c0 + 16 * g16 + 4 * gg;
-        if (r > cb + 3) continue;
-        const float4 o4 = *reinterpret_cast<const float4*>(Sold + cb);
-        const float old[4] = {o4.x, o4.y, o4.z, o4.w};
-        float nw[4];
-        H16 nh[4], nl[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const float xv = __uint_as_float(xs[4 * gg + i]);
-          const int c = cb + i;
-          const bool own = c >= r;
-          const float w = (c == r) ? 1.0f : 2.0f;
-          bad += (own && !isfinite(xv)) ? 1 : 0;
-          const float dd = old[i] - xv;
-          fd = own ? fmaf(w * dd, dd, fd) : fd;
-          const float n1 = sg * xv + om * old[i];
-          nw[i] = n1;
-          if (own && write) {
-            const float p = w * n1 * n1;
-            const float e = w * fmaf(n1, n1, -n1 * n1);
-            const float tt = fn_s + p;
-            const float bp = tt - fn_s;
-            fn_c += (fn_s - (tt - bp)) + (p - bp) + e;
-            fn_s = tt;
-            if (c == r) trf += n1;
-          }
-          const float y = n1 * scale_new;
-          nh[i] = CV::to(y);
-          nl[i] = CV::to(y - CV::from(nh[i]));
-        }
-        if (!write) continue;
-        if (r <= cb) {
-          *reinterpret_cast<float4*>(Snew + row_off + cb) = make_float4(nw[0], nw[1], nw[2], nw[3]);
-          uint2 ph, pl2;
-          ph.x = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[0])) |
-                 ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[1])) << 16);
-          ph.y = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[2])) |
-                 ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[3])) << 16);
-          pl2.x = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[0])) |
-                  ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[1])) << 16);
-          pl2.y = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[2])) |
-                  ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[3])) << 16);
-          *reinterpret_cast<uint2*>(hi_new + row_off + cb) = ph;
-          *reinterpret_cast<uint2*>(lo_new + row_off + cb) = pl2;
-        } else {
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            if (cb + i >= r) {
-              Snew[row_off + cb + i] = nw[i];
-              hi_new[row_off + cb + i] = nh[i];
-              lo_new[row_off + cb + i] = nl[i];
-            }
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int c = cb + i;
-          if (c > r) {
-            const size_t m = (size_t)c * Np + r;
-            Snew[m] = nw[i];
-            hi_new[m] = nh[i];
-            lo_new[m] = nl[i];
-          }
-        }
-      }
-      }
+        if (I2 < J)
+          rolled_tile_epilogue<CV, true>(ta_sum, Sold, Snew, hi_new, lo_new, row_off, Np, r, c0, sg,
+                                         om, scale_new, write, fn_s, fn_c, fd, trf, bad);
+        else
+          rolled_tile_epilogue<CV, false>(ta_sum, Sold, Snew, hi_new, lo_new, row_off, Np, r, c0,
+                                          sg, om, scale_new, write, fn_s, fn_c, fd, trf, bad);
         fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive_cluster(lead_tempty + 8 * ab);
@@ -1651,79 +1684,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 
       float fn_s = 0.0f, fn_c = 0.0f, fd = 0.0f, trf = 0.0f;
       int bad = 0;
-#pragma unroll 1
-      for (int g16 = 0; g16 < 8; ++g16) {
-        uint32_t xs[16];
-        tmem_ld16(ta_sum + 16 * g16, xs);
-#pragma unroll
-        for (int gg = 0; gg < 4; ++gg) {
-          const int cb = c0 + 16 * g16 + 4 * gg;
-          if (r > cb + 3) continue;
-          const float4 o4 = *reinterpret_cast<const float4*>(Sold + cb);
-          const float old[4] = {o4.x, o4.y, o4.z, o4.w};
-          float nw[4];
-          H16 nh[4], nl[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const float xv = __uint_as_float(xs[4 * gg + i]);
-            const int c = cb + i;
-            const bool own = c >= r;
-            const float w = (c == r) ? 1.0f : 2.0f;
-            bad += (own && !isfinite(xv)) ? 1 : 0;
-            const float dd = old[i] - xv;
-            fd = own ? fmaf(w * dd, dd, fd) : fd;
-            const float n1 = sg * xv + om * old[i];
-            nw[i] = n1;
-            if (own && write) {
-              const float p = w * n1 * n1;
-              const float e = w * fmaf(n1, n1, -n1 * n1);
-              const float tt = fn_s + p;
-              const float bp = tt - fn_s;
-              fn_c += (fn_s - (tt - bp)) + (p - bp) + e;
-              fn_s = tt;
-              if (c == r) trf += n1;
-            }
-            const float y = n1 * scale_new;
-            nh[i] = CV::to(y);
-            nl[i] = CV::to(y - CV::from(nh[i]));
-          }
-          if (!write) continue;
-          if (r <= cb) {
-            *reinterpret_cast<float4*>(Snew + row_off + cb) =
-                make_float4(nw[0], nw[1], nw[2], nw[3]);
-            uint2 ph, pl2;
-            ph.x = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[0])) |
-                   ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[1])) << 16);
-            ph.y = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[2])) |
-                   ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[3])) << 16);
-            pl2.x = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[0])) |
-                    ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[1])) << 16);
-            pl2.y = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[2])) |
-                    ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[3])) << 16);
-            *reinterpret_cast<uint2*>(hi_new + row_off + cb) = ph;
-            *reinterpret_cast<uint2*>(lo_new + row_off + cb) = pl2;
-          } else {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              if (cb + i >= r) {
-                Snew[row_off + cb + i] = nw[i];
-                hi_new[row_off + cb + i] = nh[i];
-                lo_new[row_off + cb + i] = nl[i];
-              }
-            }
-          }
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int c = cb + i;
-            if (c > r) {
-              const size_t m = (size_t)c * Np + r;
-              Snew[m] = nw[i];
-              hi_new[m] = nh[i];
-              lo_new[m] = nl[i];
-            }
-          }
-        }
-      }
+      if (I2 < J)
+        rolled_tile_epilogue<CV, true>(ta_sum, Sold, Snew, hi_new, lo_new, row_off, Np, r, c0, sg,
+                                       om, scale_new, write, fn_s, fn_c, fd, trf, bad);
+      else
+        rolled_tile_epilogue<CV, false>(ta_sum, Sold, Snew, hi_new, lo_new, row_off, Np, r, c0,
+                                        sg, om, scale_new, write, fn_s, fn_c, fd, trf, bad);
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(lead_tempty + 8 * ab);
