@@ -27,6 +27,10 @@
  *    DMPT_ECUDA; the text is available from dmpt_last_error().
  *  - The library only runs on an sm_103 device (GB300); other devices give
  *    DMPT_EUNSUPPORTED from dmpt_create().
+ *  - Threads: a handle (its error text, events and internal streams) is
+ *    used by one host thread at a time; separate handles, also on separate
+ *    devices of one process, may be used from separate threads.  One-time
+ *    per-device setup inside the library is thread-safe.
  */
 #ifndef DMPT_H
 #define DMPT_H

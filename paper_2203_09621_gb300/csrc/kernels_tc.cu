@@ -44,6 +44,7 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include <mutex>
 #include <type_traits>
 
 #include "dmpt_internal.cuh"
@@ -1734,16 +1735,54 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 // ---------------------------------------------------------------------------
 // Host side
 
+// Per-device one-time setup of the tensor-core kernels (their shared-memory
+// attribute is set in each device's context) and the device's SM count;
+// thread-safe.
+constexpr int kMaxDevices = 64;
+struct DeviceSetup {
+  std::once_flag once;
+  int sms = 0;
+};
+int device_setup() {
+  static DeviceSetup tab[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
+  DeviceSetup& d = tab[dev];
+  std::call_once(d.once, [&] {
+    cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(layer_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         SMEM_BYTES);
+    cudaFuncSetAttribute(layer_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         SMEM_BYTES);
+    cudaFuncSetAttribute(layer_tc2_kernel<false, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
+    cudaFuncSetAttribute(layer_tc2_kernel<true, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
+    cudaFuncSetAttribute(layer_tc2_kernel<false, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
+    cudaFuncSetAttribute(layer_tc2_kernel<true, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
+    const int group_smem = P_SMEM_BYTES + (kGroupMax + 1) * (int)sizeof(int64_t) +
+                           kGroupMax * (int)sizeof(uint32_t);
+    cudaFuncSetAttribute(layer_tc2_group_kernel<false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, group_smem);
+    cudaFuncSetAttribute(layer_tc2_group_kernel<true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, group_smem);
+  });
+  return d.sms;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  // looked up once per process (thread-safe static initialisation)
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
+      return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+  }();
   return fn;
 }
 
@@ -1797,16 +1836,7 @@ cudaError_t launch_layer_tc_group(const GroupInst* inst, int count, bool bf16, i
   using namespace tc;
   if (count < 1 || count > kGroupMax) return cudaErrorInvalidValue;
   const int smem = P_SMEM_BYTES + (count + 1) * (int)sizeof(int64_t) + count * (int)sizeof(uint32_t);
-  static bool attr = false;
-  if (!attr) {
-    const int max_smem = P_SMEM_BYTES + (kGroupMax + 1) * (int)sizeof(int64_t) +
-                         kGroupMax * (int)sizeof(uint32_t);
-    cudaFuncSetAttribute(layer_tc2_group_kernel<false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-    cudaFuncSetAttribute(layer_tc2_group_kernel<true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-    attr = true;
-  }
+  if (device_setup() == 0) return cudaErrorInvalidDevice;
   const uint64_t limit_ns = (uint64_t)(timeout_s * 1e9);
   const int ck = accum_chunk_k > 0 ? accum_chunk_k : DEFAULT_CHUNK_K;
   const int chunk = ck / BK < 1 ? 1 : ck / BK;
@@ -1831,24 +1861,8 @@ cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double ti
   if (!make_map(&mA, base + L.off_ops16, L.Np, slices, BM, bf16) ||
       !make_map(&mB, base + L.off_ops16, L.Np, slices, BN, bf16))
     return cudaErrorInvalidValue;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(layer_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         SMEM_BYTES);
-    cudaFuncSetAttribute(layer_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         SMEM_BYTES);
-    cudaFuncSetAttribute(layer_tc2_kernel<false, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
-    cudaFuncSetAttribute(layer_tc2_kernel<true, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
-    cudaFuncSetAttribute(layer_tc2_kernel<false, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
-    cudaFuncSetAttribute(layer_tc2_kernel<true, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
-  }
+  const int sms = device_setup();
+  if (sms == 0) return cudaErrorInvalidDevice;
   const uint64_t limit_ns = (uint64_t)(timeout_s * 1e9);
   int ck = accum_chunk_k > 0 ? accum_chunk_k : DEFAULT_CHUNK_K;
   int chunk = ck / BK;
