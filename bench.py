@@ -394,6 +394,25 @@ def main():
         fms = a.elapsed_time(b)
         forms[f] = {"ms": fms, "tflops": fi.alg_flops / (fms * 1e-3) / 1e12,
                     "layers": fi.layers, "d0_layer": fi.d0_layer}
+    if "fp32" in forms:
+        # context only: cuBLAS SGEMM (TF32 off) at the same n, one product
+        # (2 n^3 flops), beside the SIMT form's per-layer rate
+        prev_tf32 = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = False
+        a32 = torch.randn(n, n, dtype=torch.float32, device=dev)
+        b32 = torch.randn(n, n, dtype=torch.float32, device=dev)
+        for _ in range(2):
+            torch.matmul(a32, b32)
+        torch.cuda.synchronize()
+        ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ga.record(stream)
+        for _ in range(3):
+            torch.matmul(a32, b32)
+        gb.record(stream)
+        torch.cuda.synchronize()
+        torch.backends.cuda.matmul.allow_tf32 = prev_tf32
+        forms["fp32"]["cublas_sgemm_tflops"] = 3 * 2.0 * n ** 3 / (ga.elapsed_time(gb) * 1e-3) / 1e12
+        del a32, b32
     if "fp64" in args.forms.split(",") and args.fp64_layers > 0:
         # bounded sample: the first layers of the FP64 form (each a full D0
         # layer), per-launch times by CUDA events; the time to solution is
