@@ -3,6 +3,8 @@
 import ctypes
 import os
 import re
+
+import numpy as np
 import subprocess
 
 import pytest
@@ -116,3 +118,35 @@ def test_host_pipeline_sizes_and_argument_errors(lib):
     # null handle
     assert lib.dmpt_sp2_response_host(None, 1, None, None, 1, 4, 2, None, None, None, None,
                                       None, 0, None) == 1
+
+
+def test_c_caller_builds_and_reports_missing_gpu(lib, tmp_path):
+    """The plain-C caller (tests/c_abi/dmpt_host_solve.c) compiles against
+    include/dmpt.h and links to the in-tree library; without a GPU,
+    dmpt_create returns a status and the program exits 1 with a message."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    if cc is None or not os.path.exists(os.path.join(cuda, "include", "cuda_runtime.h")):
+        pytest.skip("no C compiler or CUDA headers")
+    pkg = os.path.join(ROOT, "paper_2203_09621_gb300")
+    exe = str(tmp_path / "dmpt_host_solve")
+    r = subprocess.run([cc, "-O2", "-std=c99", os.path.join(ROOT, "tests", "c_abi", "dmpt_host_solve.c"),
+                        "-I", os.path.join(ROOT, "include"), "-I", os.path.join(cuda, "include"),
+                        "-L", pkg, "-ldmpt", "-Wl,-rpath," + pkg,
+                        "-L", os.path.join(cuda, "lib64"), "-lcudart",
+                        "-Wl,-rpath," + os.path.join(cuda, "lib64"), "-o", exe],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present: tests/test_gpu_c_abi.py runs the program")
+    except ImportError:
+        pass
+    src = tmp_path / "in.bin"
+    np.zeros(2 * 16, dtype=np.float64).tofile(src)
+    r = subprocess.run([exe, "4", "2", "1", str(src), str(tmp_path / "out.bin")],
+                       capture_output=True, text=True, timeout=60)
+    assert r.returncode == 1 and "dmpt_create" in r.stderr, (r.returncode, r.stderr)
