@@ -103,7 +103,12 @@ typedef struct {
                            the layer product wait on a barrier nothing arrives
                            on, so its bounded waits expire and the call returns
                            DMPT_ETIMEOUT after about timeout_s; 0 (default)    */
-  int reserved[1];
+  int autotune;         /* dual forms: 1 = take cta_pair, tile_band and k_snake
+                           from the handle's tuning table (see dmpt_autotune),
+                           tuning on first use of a (padded n, k, precision)
+                           with the call's own inputs; in a batch, choose the
+                           grouped or per-instance path the same way.  0
+                           (default) = use the fields as given              */
 } dmpt_options;
 
 /* Filled on the host by dmpt_sp2_response (when info != NULL). */
@@ -304,6 +309,28 @@ dmpt_status dmpt_sp2_response_host(dmpt_handle h, int count, const double* const
                                    double* const* P_host, double* const* P1_host,
                                    dmpt_info* info, void* workspace, size_t ws_bytes,
                                    void* stream);
+
+/* Autotuning of the layer products (dual forms; the paper has no
+ * counterpart -- a library feature).  Times short probe solves of
+ * (H, H1) -- the first `probe_layers` layers (default 3 when <= 0), all
+ * full D0 layers -- under each candidate configuration:
+ *   tile shape    256 x 256 on CTA pairs (cta_pair = 1) or 128 x 256 on
+ *                 single CTAs (cta_pair = 0),
+ *   rasterisation tile_band in {0, 4, 8, 16} for CTA pairs,
+ * with the other options of `o` (K-snake as given), and keeps the
+ * configuration with the least layer-product time per layer.  The winner is
+ * stored in the handle's table under (padded n, k, precision) and, when
+ * `best` is not NULL, returned as a copy of *o with those fields set
+ * (best->autotune = 0); *best_layer_ms receives its time per layer.  The
+ * candidates differ in tile order and shape only, so any of them gives the
+ * method's results within its accuracy (tile order alone: bit-identical).
+ *   P, P1  device outputs of the probe solves (overwritten; as for
+ *          dmpt_sp2_response), workspace as for dmpt_sp2_response.
+ * FP32/FP64 forms have no candidates: *best = *o.  Synchronises `stream`. */
+dmpt_status dmpt_autotune(dmpt_handle h, const double* H, const double* H1, int k, int64_t n,
+                          int64_t ld, int64_t n_occ, const dmpt_options* o, int probe_layers,
+                          double* P, double* P1, dmpt_options* best, double* best_layer_ms,
+                          void* workspace, size_t ws_bytes, void* stream);
 
 /* Static-scratch variant of dmpt_sp2_response for callers that cannot
  * allocate device memory (a host framework that owns every allocation, code

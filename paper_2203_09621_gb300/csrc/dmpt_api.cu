@@ -28,6 +28,21 @@ struct dmpt_ctx {
   cudaStream_t copy_in = nullptr, copy_out = nullptr;
   cudaEvent_t ev_start = nullptr, ev_in[2] = {nullptr, nullptr}, ev_solved[2] = {nullptr, nullptr},
               ev_out[2] = {nullptr, nullptr}, ev_end[2] = {nullptr, nullptr};
+  // autotuning: the winning layer-product configuration per (padded n, k,
+  // precision), and the winning path per batch signature
+  struct TuneEntry {
+    int64_t Np;
+    int k, precision;
+    int cta_pair, tile_band, k_snake;
+    double ms;
+  };
+  std::vector<TuneEntry> tune;
+  struct BatchTune {
+    std::vector<int64_t> Np;   // sorted padded sizes
+    int k, precision;
+    int path;                  // 0 grouped, 1 per-instance CTA pairs, 2 per-instance single CTAs
+  };
+  std::vector<BatchTune> batch_tune;
 };
 
 namespace {
@@ -69,6 +84,7 @@ bool valid_options(const dmpt_options* o) {
   if (o->order < 1 || o->order > 2) return false;
   if (o->tile_band < 0 || o->tile_band > 1024) return false;
   if (o->inject_stall < 0 || o->inject_stall > 1) return false;
+  if (o->autotune < 0 || o->autotune > 1) return false;
   return true;
 }
 
@@ -494,6 +510,12 @@ static dmpt_status forward_impl(dmpt_handle h, const double* H, const double* H1
   return status;
 }
 
+static const dmpt_ctx::TuneEntry* find_tune(dmpt_handle h, int64_t Np, int k, int precision) {
+  for (const auto& x : h->tune)
+    if (x.Np == Np && x.k == k && x.precision == precision) return &x;
+  return nullptr;
+}
+
 dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, int k,
                               int64_t n, int64_t ld, int64_t n_occ, const dmpt_options* o,
                               double* P, double* P1, dmpt_info* info, void* workspace,
@@ -506,8 +528,88 @@ dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1, 
   if (info) memset(info, 0, sizeof(*info));
   if (o->order != 1)
     return fail(h, DMPT_EINVAL, "dmpt_sp2_response: o->order must be 1 (use dmpt_sp2_response2)%s");
+  if (o->autotune && valid_options(o) && o->precision >= DMPT_DUAL_FP16 && n >= 1 &&
+      n_occ > 0 && n_occ < n && k >= 0 && k <= DMPT_MAX_K) {
+    const int64_t Np = layout_for(n, k, o).Np;
+    const dmpt_ctx::TuneEntry* e = find_tune(h, Np, k, o->precision);
+    if (!e) {
+      const dmpt_status st = dmpt_autotune(h, H, H1, k, n, ld, n_occ, o, 0, P, P1, nullptr,
+                                           nullptr, workspace, ws_bytes, stream);
+      if (st != DMPT_OK) return st;
+      e = find_tune(h, Np, k, o->precision);
+      if (!e) return fail(h, DMPT_EINVAL, "dmpt_sp2_response: autotuning stored no entry%s");
+    }
+    dmpt_options t = *o;
+    t.autotune = 0;
+    t.cta_pair = e->cta_pair;
+    t.tile_band = e->tile_band;
+    t.k_snake = e->k_snake;
+    return forward_impl(h, H, H1, k, n, ld, n_occ, &t, P, P1, nullptr, info, workspace, ws_bytes,
+                        stream);
+  }
   return forward_impl(h, H, H1, k, n, ld, n_occ, o, P, P1, nullptr, info, workspace, ws_bytes,
                       stream);
+}
+
+dmpt_status dmpt_autotune(dmpt_handle h, const double* H, const double* H1, int k, int64_t n,
+                          int64_t ld, int64_t n_occ, const dmpt_options* o, int probe_layers,
+                          double* P, double* P1, dmpt_options* best, double* best_layer_ms,
+                          void* workspace, size_t ws_bytes, void* stream) {
+  if (!h) return DMPT_EINVAL;
+  h->err[0] = 0;
+  dmpt_options defaults;
+  dmpt_default_options(&defaults);
+  if (!o) o = &defaults;
+  if (!valid_options(o) || o->order != 1 || n < 1 || k < 0 || k > DMPT_MAX_K)
+    return fail(h, DMPT_EINVAL, "dmpt_autotune: invalid arguments (first order only)%s");
+  dmpt_options b = *o;
+  b.autotune = 0;
+  if (best) *best = b;
+  if (best_layer_ms) *best_layer_ms = 0.0;
+  if (o->precision < DMPT_DUAL_FP16 || n_occ <= 0 || n_occ >= n) return DMPT_OK;  // no candidates
+  struct Cand {
+    int pair, band;
+  };
+  static const Cand cands[] = {{1, 8}, {1, 0}, {1, 4}, {1, 16}, {0, 8}};
+  dmpt_options t = b;
+  t.max_layers = probe_layers > 0 ? probe_layers : 3;
+  t.timing = 1;
+  t.ckpt_every = 0;
+  dmpt_info info;
+  // warm-up: first launches of the kernels and tensor maps on this device
+  dmpt_status st = forward_impl(h, H, H1, k, n, ld, n_occ, &t, P, P1, nullptr, &info, workspace,
+                                ws_bytes, stream);
+  if (st != DMPT_OK && st != DMPT_ENOTCONV) return st;
+  double best_t = 1e300;
+  Cand win = cands[0];
+  for (const Cand& c : cands) {
+    t.cta_pair = c.pair;
+    t.tile_band = c.band;
+    st = forward_impl(h, H, H1, k, n, ld, n_occ, &t, P, P1, nullptr, &info, workspace, ws_bytes,
+                      stream);
+    if (st != DMPT_OK && st != DMPT_ENOTCONV) return st;
+    const double per = info.timed_launches > 0 ? info.ms_layers / info.timed_launches : 1e300;
+    if (per < best_t) {
+      best_t = per;
+      win = c;
+    }
+  }
+  h->err[0] = 0;   // the probes end at their layer cap by design
+  const int64_t Np = layout_for(n, k, &b).Np;
+  dmpt_ctx::TuneEntry e{Np, k, b.precision, win.pair, win.band, b.k_snake, best_t};
+  bool stored = false;
+  for (auto& x : h->tune)
+    if (x.Np == Np && x.k == k && x.precision == b.precision) {
+      x = e;
+      stored = true;
+    }
+  if (!stored) h->tune.push_back(e);
+  if (best) {
+    best->cta_pair = win.pair;
+    best->tile_band = win.band;
+  }
+  if (best_layer_ms) *best_layer_ms = best_t;
+  return DMPT_OK;
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -736,17 +838,13 @@ size_t dmpt_workspace_size_batch(int count, const int64_t* n, int k, const dmpt_
   return total;
 }
 
-dmpt_status dmpt_sp2_response_batch(dmpt_handle h, int count, const double* const* H,
-                                    const double* const* H1, int k, const int64_t* n,
-                                    const int64_t* ld, const int64_t* n_occ,
-                                    const dmpt_options* o, double* const* P, double* const* P1,
-                                    dmpt_info* info, void* workspace, size_t ws_bytes,
-                                    void* stream) {
-  if (!h) return DMPT_EINVAL;
-  h->err[0] = 0;
-  dmpt_options defaults;
-  dmpt_default_options(&defaults);
-  if (!o) o = &defaults;
+// path: -1 = the default rule (grouped launch for dual forms on CTA pairs),
+// 0 = grouped, 1 = one launch per instance on its own stream.
+static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
+                              const double* const* H1, int k, const int64_t* n,
+                              const int64_t* ld, const int64_t* n_occ, const dmpt_options* o,
+                              double* const* P, double* const* P1, dmpt_info* info,
+                              void* workspace, size_t ws_bytes, void* stream, int path) {
   if (count < 1 || !H || !n || !ld || !n_occ || (k > 0 && (!H1 || !P1)) || (k == 0 && !P))
     return fail(h, DMPT_EINVAL, "dmpt_sp2_response_batch: bad arguments%s");
   if (k < 0 || k > DMPT_MAX_K || !valid_options(o) || o->ckpt_every != 0 || o->timing)
@@ -805,7 +903,7 @@ dmpt_status dmpt_sp2_response_batch(dmpt_handle h, int count, const double* cons
   // dual precision on CTA pairs: one grouped launch per layer step for all
   // instances (GroupInst table, batched decide); otherwise one launch per
   // instance on its own stream
-  const bool grouped = dual && o->cta_pair && o->order == 1 && n_active > 0 &&
+  const bool grouped = path != 1 && dual && o->cta_pair && o->order == 1 && n_active > 0 &&
                        n_active <= kGroupMax;
   GroupInst* d_ginst = (GroupInst*)(base + batch_poll_bytes(count));
   GroupDecide* d_gdec = (GroupDecide*)((char*)d_ginst + batch_ginst_bytes(count));
@@ -981,6 +1079,72 @@ dmpt_status dmpt_sp2_response_batch(dmpt_handle h, int count, const double* cons
   if (e != cudaSuccess) return cuda_fail(h, e, "batch join");
   if (worst != DMPT_OK) return fail(h, worst, "dmpt_sp2_response_batch: an instance failed%s");
   return DMPT_OK;
+}
+
+dmpt_status dmpt_sp2_response_batch(dmpt_handle h, int count, const double* const* H,
+                                    const double* const* H1, int k, const int64_t* n,
+                                    const int64_t* ld, const int64_t* n_occ,
+                                    const dmpt_options* o, double* const* P, double* const* P1,
+                                    dmpt_info* info, void* workspace, size_t ws_bytes,
+                                    void* stream) {
+  if (!h) return DMPT_EINVAL;
+  h->err[0] = 0;
+  dmpt_options defaults;
+  dmpt_default_options(&defaults);
+  if (!o) o = &defaults;
+  if (!(o->autotune && valid_options(o) && o->precision >= DMPT_DUAL_FP16 && o->order == 1 &&
+        count >= 1 && n != nullptr))
+    return batch_impl(h, count, H, H1, k, n, ld, n_occ, o, P, P1, info, workspace, ws_bytes,
+                      stream, -1);
+  // autotuned batch: the grouped launch on CTA pairs, or one launch per
+  // instance with 256 x 256 (CTA-pair) or 128 x 256 (single-CTA) tiles;
+  // chosen once per batch signature by timing a short probe of each
+  std::vector<int64_t> sig(count);
+  for (int i = 0; i < count; ++i) sig[i] = n[i] >= 1 ? make_layout(n[i], k, o->precision).Np : 0;
+  std::sort(sig.begin(), sig.end());
+  int path = -1;
+  for (const auto& b : h->batch_tune)
+    if (b.k == k && b.precision == o->precision && b.Np == sig) path = b.path;
+  dmpt_options t = *o;
+  t.autotune = 0;
+  if (path < 0) {
+    DeviceGuard g(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+      return cuda_fail(h, cudaGetLastError(), "batch autotune events");
+    dmpt_options p = t;
+    p.max_layers = 3;
+    double best_ms = 1e300;
+    for (int rep = 0; rep < 2; ++rep) {   // the first round warms every path up
+      for (int cand = 0; cand < 3; ++cand) {
+        p.cta_pair = cand == 2 ? 0 : 1;
+        cudaEventRecord(e0, s);
+        const dmpt_status st = batch_impl(h, count, H, H1, k, n, ld, n_occ, &p, P, P1, info,
+                                          workspace, ws_bytes, stream, cand == 0 ? 0 : 1);
+        cudaEventRecord(e1, s);
+        if (st != DMPT_OK && st != DMPT_ENOTCONV) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return st;
+        }
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && rep == 1 && ms < best_ms) {
+          best_ms = ms;
+          path = cand;
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (path < 0) path = 0;
+    h->batch_tune.push_back({sig, k, o->precision, path});
+    h->err[0] = 0;
+  }
+  t.cta_pair = path == 2 ? 0 : 1;
+  return batch_impl(h, count, H, H1, k, n, ld, n_occ, &t, P, P1, info, workspace, ws_bytes, stream,
+                    path == 0 ? 0 : 1);
 }
 
 dmpt_status dmpt_response_replay(dmpt_handle h, const double* H1, int k, int64_t n,

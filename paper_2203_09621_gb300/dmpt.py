@@ -43,7 +43,7 @@ class DmptOptions(ctypes.Structure):
         ("order", ctypes.c_int),
         ("tile_band", ctypes.c_int),
         ("inject_stall", ctypes.c_int),
-        ("reserved", ctypes.c_int * 1),
+        ("autotune", ctypes.c_int),
     ]
 
 
@@ -113,6 +113,10 @@ def load_library(path: str = LIB_PATH):
                                       ctypes.POINTER(DmptInfo), ctypes.POINTER(c_int),
                                       ctypes.POINTER(ctypes.c_double), vp, ctypes.c_size_t, vp]
     lib.dmpt_scc_response.restype = c_int
+    lib.dmpt_autotune.argtypes = [vp, vp, vp, c_int, i64, i64, i64, ctypes.POINTER(DmptOptions),
+                                  c_int, vp, vp, ctypes.POINTER(DmptOptions),
+                                  ctypes.POINTER(ctypes.c_double), vp, ctypes.c_size_t, vp]
+    lib.dmpt_autotune.restype = c_int
     lib.dmpt_workspace_size_host.argtypes = [i64, c_int, ctypes.POINTER(DmptOptions)]
     lib.dmpt_workspace_size_host.restype = ctypes.c_size_t
     lib.dmpt_sp2_response_host.argtypes = [vp, c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int,
@@ -175,7 +179,7 @@ class Info:
 def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_scaling=1,
             sync_every=4, timing=False, timeout_s=2.0, accum_chunk=0,
             cta_pair=1, k_snake=1, ckpt_every=0, order=1, tile_band=8,
-            inject_stall=0) -> DmptOptions:
+            inject_stall=0, autotune=0) -> DmptOptions:
     lib = load_library()
     o = DmptOptions()
     lib.dmpt_default_options(ctypes.byref(o))
@@ -194,6 +198,7 @@ def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_s
     o.order = int(order)
     o.tile_band = int(tile_band)
     o.inject_stall = int(inject_stall)
+    o.autotune = int(autotune)
     return o
 
 
@@ -312,6 +317,32 @@ class Context:
         if st != 0 and raise_on_error:
             self._check(st)
         return P, P1, inf
+
+    def autotune(self, H, H1, n_occ: int, precision="dual_fp16", probe_layers=0, stream=None,
+                 **kw):
+        """Tune the layer-product configuration for (H, H1) (dmpt_autotune):
+        returns (dict of the chosen cta_pair / tile_band / k_snake, ms per
+        layer).  The handle keeps the result; calls with autotune=1 use it."""
+        import torch
+        if H1.dim() == 2:
+            H1 = H1.unsqueeze(0)
+        H, H1 = H.contiguous(), H1.contiguous()
+        n, k = H.shape[0], H1.shape[0]
+        opts = options(precision=precision, **kw)
+        P = torch.empty(n, n, dtype=torch.float64, device=H.device)
+        P1 = torch.empty(k, n, n, dtype=torch.float64, device=H.device) if k else None
+        ws_ptr, ws_len = self.workspace(self.workspace_size(n, k, opts))
+        best = DmptOptions()
+        ms = ctypes.c_double(0.0)
+        s = stream if stream is not None else torch.cuda.current_stream(H.device)
+        st = self.lib.dmpt_autotune(self.h, H.data_ptr(), H1.data_ptr() if k else None, k, n, n,
+                                    int(n_occ), ctypes.byref(opts), int(probe_layers), P.data_ptr(),
+                                    P1.data_ptr() if k else None, ctypes.byref(best),
+                                    ctypes.byref(ms), ctypes.c_void_p(ws_ptr), ws_len,
+                                    ctypes.c_void_p(s.cuda_stream))
+        self._check(st)
+        return {"cta_pair": best.cta_pair, "tile_band": best.tile_band,
+                "k_snake": best.k_snake}, ms.value
 
     def sp2_response2(self, H, H1, n_occ, precision="dual_fp16", stream=None,
                       raise_on_error=True, **kw):
