@@ -811,6 +811,118 @@ __host__ __device__ constexpr uint32_t make_idesc_m256(int ab_type) {
          ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
 }
 
+// Position in the shared-memory stage ring (stage index and phase bit) or
+// in the two tensor-memory accumulators (buffer and phase bit).
+struct RingPos {
+  int idx = 0;
+  uint32_t phase = 0;
+  __device__ __forceinline__ void next(int size) {
+    if (++idx == size) {
+      idx = 0;
+      phase ^= 1;
+    }
+  }
+};
+
+// TMA producer of a pair kernel, one work item: the item's passes over its
+// K blocks (backwards when `rev`), each stage the hi and lo halves of this
+// CTA's A rows and B rows, signalled on the pair leader's full barrier.
+// False when a bounded wait expired or the CTA aborted.
+__device__ __forceinline__ bool produce_item(RingPos& rg, const CUtensorMap* map,
+                                             const State* st, int job, int passes, int k,
+                                             int k1, int cur0, int z0c, int rowA, int rowB,
+                                             int kblocks, bool rev, bool leader, uint32_t ring,
+                                             uint32_t bar_full, uint32_t bar_empty,
+                                             uint32_t lead_full, uint64_t limit_ns,
+                                             volatile int* abort_flag, int* timeout_global) {
+  for (int pp = 0; pp < passes; ++pp) {
+    const int pass = rev ? passes - 1 - pp : pp;
+    int mA, mB;
+    job_operands(job, pass, k1, &mA, &mB);
+    const int bufA = mA == 0 ? cur0 : st->cur1[mA - 1];
+    const int bufB = mB == 0 ? cur0 : st->cur1[mB - 1];
+    const int zAh = zop(mA, bufA, 0, k, z0c), zAl = zop(mA, bufA, 1, k, z0c);
+    const int zBh = zop(mB, bufB, 0, k, z0c), zBl = zop(mB, bufB, 1, k, z0c);
+    for (int kq = 0; kq < kblocks; ++kq) {
+      const int kb = rev ? kblocks - 1 - kq : kq;
+      if (!mbar_wait(bar_empty + 8 * rg.idx, rg.phase ^ 1, limit_ns, abort_flag, timeout_global))
+        return false;
+      const uint32_t sA = ring + rg.idx * P_STAGE_BYTES;
+      if (leader) mbar_expect_tx(bar_full + 8 * rg.idx, 2 * P_STAGE_BYTES);
+      const uint32_t fb = lead_full + 8 * rg.idx;
+      tma_load_3d_pair(sA, map, kb * BK, rowA, zAh, fb);
+      tma_load_3d_pair(sA + A_BYTES, map, kb * BK, rowA, zAl, fb);
+      tma_load_3d_pair(sA + 2 * A_BYTES, map, kb * BK, rowB, zBh, fb);
+      tma_load_3d_pair(sA + 3 * A_BYTES, map, kb * BK, rowB, zBl, fb);
+      rg.next(P_STAGES);
+    }
+  }
+  return true;
+}
+
+// Before a CTA exits, wait (bounded) for the copies it issued to land: the
+// last P_STAGES stages were released by MMA commits or are pending.
+__device__ __forceinline__ void producer_drain(RingPos rg, uint32_t bar_empty, uint64_t limit_ns) {
+  for (int i = 0; i < P_STAGES; ++i) {
+    const uint64_t t0 = gtimer();
+    while (!mbar_try_wait(bar_empty + 8 * rg.idx, rg.phase ^ 1) && gtimer() - t0 < limit_ns) {
+    }
+    rg.next(P_STAGES);
+  }
+}
+
+// MMA issuer of a pair kernel (leader CTA, one thread), one work item of
+// `nst` stages: per stage the three products hi*hi, hi*lo, lo*hi for two K16
+// steps into the current accumulation chunk; a chunk ends every `chunk`
+// stages and at the end of each K pass (so chunks never straddle a pass),
+// and is then published to both CTAs.  False when a bounded wait expired.
+template <bool BF16>
+__device__ __forceinline__ bool mma_item(RingPos& rg, RingPos& tb, int nst, int kblocks,
+                                         int chunk, uint32_t tmem_base, uint32_t ring,
+                                         uint32_t bar_full, uint32_t bar_empty,
+                                         uint32_t bar_tfull, uint32_t bar_tempty,
+                                         uint64_t limit_ns, volatile int* abort_flag,
+                                         int* timeout_global) {
+  constexpr uint32_t idesc = make_idesc_m256(BF16 ? 1 : 0);
+  uint32_t d = 0, acc = 0;
+  int sp = 0;   // stage within its K pass
+  int cp = 0;   // stage within its accumulation chunk
+  for (int si = 0; si < nst; ++si) {
+    if (cp == 0) {
+      if (!mbar_wait(bar_tempty + 8 * tb.idx, tb.phase ^ 1, limit_ns, abort_flag, timeout_global))
+        return false;
+      fence_after();
+      d = tmem_base + (uint32_t)(tb.idx * BN);
+      acc = 0;
+    }
+    if (!mbar_wait(bar_full + 8 * rg.idx, rg.phase, limit_ns, abort_flag, timeout_global))
+      return false;
+    fence_after();
+    const uint32_t sA = ring + rg.idx * P_STAGE_BYTES;
+    const uint64_t ah = sw64_desc(sA), al = sw64_desc(sA + A_BYTES);
+    const uint64_t bh = sw64_desc(sA + 2 * A_BYTES);
+    const uint64_t bl = sw64_desc(sA + 3 * A_BYTES);
+#pragma unroll
+    for (int kk = 0; kk < BK / 16; ++kk) {
+      const uint64_t off = (uint64_t)((kk * 32) >> 4);
+      mma_f16_pair(d, ah + off, bh + off, idesc, acc);   // hi * hi
+      acc = 1;
+      mma_f16_pair(d, ah + off, bl + off, idesc, 1);     // hi * lo
+      mma_f16_pair(d, al + off, bh + off, idesc, 1);     // lo * hi
+    }
+    mma_commit_pair(bar_empty + 8 * rg.idx);   // frees the stage in both CTAs
+    rg.next(P_STAGES);
+    const bool chunk_end = cp == chunk - 1 || sp == kblocks - 1;
+    if (++cp == chunk || sp == kblocks - 1) cp = 0;
+    if (++sp == kblocks) sp = 0;
+    if (chunk_end) {
+      mma_commit_pair(bar_tfull + 8 * tb.idx);    // chunk ready in both CTAs
+      tb.next(2);
+    }
+  }
+  return true;
+}
+
 // Rolled tile epilogue of one thread: its row r, columns c0 .. c0 + 127 of a
 // pair tile, whose sums the caller has written to tensor memory at ta_sum.
 // Reads the old master 32 columns at a time (eight float4 through the
@@ -999,124 +1111,37 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
   if (warp == 0) {
     // ================= TMA producer (both CTAs load their own halves) ======
     if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
+      RingPos rg;
       bool ok = true;
       int64_t round = 0;
       for (int64_t it = pair; it < items && ok; it += npairs, ++round) {
         const int job = job_at(jmask, (int)(it / tiles));
         int I2, J;
         pair_tile_banded(it % tiles, (int)(Np / BN), band, &I2, &J);
-        const int passes = job_passes(job, k1);
-        const int rowA = I2 * 2 * BM + (int)rank * BM;
-        const int rowB = J * BN + (int)rank * BM;
         // all pairs move through their tiles' K ranges in near lockstep; in
         // odd rounds the sweep runs backwards (passes and K blocks), so a
         // round starts on the panel slices the previous round loaded last,
         // which are still in L2
         const bool rev = k_snake && (round & 1);
-        for (int pp = 0; pp < passes && ok; ++pp) {
-          const int pass = rev ? passes - 1 - pp : pp;
-          int mA, mB;
-          job_operands(job, pass, k1, &mA, &mB);
-          const int bufA = mA == 0 ? cur0 : st->cur1[mA - 1];
-          const int bufB = mB == 0 ? cur0 : st->cur1[mB - 1];
-          const int zAh = zop(mA, bufA, 0, k, z0c), zAl = zop(mA, bufA, 1, k, z0c);
-          const int zBh = zop(mB, bufB, 0, k, z0c), zBl = zop(mB, bufB, 1, k, z0c);
-          for (int kq = 0; kq < kblocks; ++kq) {
-            const int kb = rev ? kblocks - 1 - kq : kq;
-            if (!mbar_wait(bar_empty + 8 * stage, phase ^ 1, limit_ns, abort_flag,
-                           timeout_global)) {
-              ok = false;
-              break;
-            }
-            const uint32_t sA = ring + stage * P_STAGE_BYTES;
-            if (leader) mbar_expect_tx(bar_full + 8 * stage, 2 * P_STAGE_BYTES);
-            const uint32_t fb = lead_full + 8 * stage;
-            tma_load_3d_pair(sA, &mapA, kb * BK, rowA, zAh, fb);
-            tma_load_3d_pair(sA + A_BYTES, &mapA, kb * BK, rowA, zAl, fb);
-            tma_load_3d_pair(sA + 2 * A_BYTES, &mapA, kb * BK, rowB, zBh, fb);
-            tma_load_3d_pair(sA + 3 * A_BYTES, &mapA, kb * BK, rowB, zBl, fb);
-            if (++stage == P_STAGES) {
-              stage = 0;
-              phase ^= 1;
-            }
-          }
-        }
+        ok = produce_item(rg, &mapA, st, job, job_passes(job, k1), k, k1, cur0, z0c,
+                          I2 * 2 * BM + (int)rank * BM, J * BN + (int)rank * BM, kblocks, rev,
+                          leader, ring, bar_full, bar_empty, lead_full, limit_ns, abort_flag,
+                          timeout_global);
       }
-      // wait (bounded) for this CTA's copies to land before the CTA may exit:
-      // the last P_STAGES stages were released by MMA commits or are pending
-      for (int i = 0; i < P_STAGES; ++i) {
-        const uint64_t t0 = gtimer();
-        while (!mbar_try_wait(bar_empty + 8 * stage, phase ^ 1) && gtimer() - t0 < limit_ns) {
-        }
-        if (++stage == P_STAGES) {
-          stage = 0;
-          phase ^= 1;
-        }
-      }
+      producer_drain(rg, bar_empty, limit_ns);
     }
   } else if (warp == 1) {
     // ================= MMA issuer (leader CTA only) =================
     if (leader && lane == 0) {
-      constexpr uint32_t idesc = make_idesc_m256(BF16 ? 1 : 0);
-      int stage = 0;
-      uint32_t phase = 0;
-      int ab = 0;
-      uint32_t abphase = 0;
+      RingPos rg, tb;
       // test hook (see the single-CTA kernel)
       bool ok = !(inject_stall &&
                   !mbar_wait(bar_drain, 0, limit_ns, abort_flag, timeout_global));
       for (int64_t it = pair; it < items && ok; it += npairs) {
         const int job = job_at(jmask, (int)(it / tiles));
-        const int nst = job_passes(job, k1) * kblocks;
-        uint32_t d = 0, acc = 0;
-        int sp = 0;   // stage within its K pass
-        int cp = 0;   // stage within its accumulation chunk
-        for (int si = 0; si < nst; ++si) {
-          if (cp == 0) {
-            if (!mbar_wait(bar_tempty + 8 * ab, abphase ^ 1, limit_ns, abort_flag,
-                           timeout_global)) {
-              ok = false;
-              break;
-            }
-            fence_after();
-            d = tmem_base + (uint32_t)(ab * BN);
-            acc = 0;
-          }
-          if (!mbar_wait(bar_full + 8 * stage, phase, limit_ns, abort_flag, timeout_global)) {
-            ok = false;
-            break;
-          }
-          fence_after();
-          const uint32_t sA = ring + stage * P_STAGE_BYTES;
-          const uint64_t ah = sw64_desc(sA), al = sw64_desc(sA + A_BYTES);
-          const uint64_t bh = sw64_desc(sA + 2 * A_BYTES);
-          const uint64_t bl = sw64_desc(sA + 3 * A_BYTES);
-#pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint64_t off = (uint64_t)((kk * 32) >> 4);
-            mma_f16_pair(d, ah + off, bh + off, idesc, acc);   // hi * hi
-            acc = 1;
-            mma_f16_pair(d, ah + off, bl + off, idesc, 1);     // hi * lo
-            mma_f16_pair(d, al + off, bh + off, idesc, 1);     // lo * hi
-          }
-          mma_commit_pair(bar_empty + 8 * stage);   // frees the stage in both CTAs
-          if (++stage == P_STAGES) {
-            stage = 0;
-            phase ^= 1;
-          }
-          const bool chunk_end = cp == chunk - 1 || sp == kblocks - 1;
-          if (++cp == chunk || sp == kblocks - 1) cp = 0;
-          if (++sp == kblocks) sp = 0;
-          if (chunk_end) {
-            mma_commit_pair(bar_tfull + 8 * ab);    // chunk ready in both CTAs
-            if (++ab == 2) {
-              ab = 0;
-              abphase ^= 1;
-            }
-          }
-        }
+        ok = mma_item<BF16>(rg, tb, job_passes(job, k1) * kblocks, kblocks, chunk, tmem_base, ring,
+                            bar_full, bar_empty, bar_tfull, bar_tempty, limit_ns, abort_flag,
+                            timeout_global);
       }
       asm volatile(
           "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -1473,8 +1498,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
   if (warp == 0) {
     // ================= TMA producer (both CTAs load their own halves) ======
     if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
+      RingPos rg;
       bool ok = true;
       int last_inst = -1;
       for (int64_t g = pair; g < items && ok; g += npairs) {
@@ -1485,112 +1509,25 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
           last_inst = itm.inst;
         }
         const State* sti = gi.st;
-        const int k = gi.k;
-        const int cur0 = sti->cur0, z0c = sti->z0_cur;
         int I2, J;
         pair_tile_banded(itm.t, (int)(gi.Np / BN), band, &I2, &J);
-        const int rowA = I2 * 2 * BM + (int)rank * BM;
-        const int rowB = J * BN + (int)rank * BM;
-        for (int pp = 0; pp < itm.passes && ok; ++pp) {
-          const int pass = itm.rev ? itm.passes - 1 - pp : pp;
-          int mA, mB;
-          job_operands(itm.job, pass, k, &mA, &mB);
-          const int bufA = mA == 0 ? cur0 : sti->cur1[mA - 1];
-          const int bufB = mB == 0 ? cur0 : sti->cur1[mB - 1];
-          const int zAh = zop(mA, bufA, 0, k, z0c), zAl = zop(mA, bufA, 1, k, z0c);
-          const int zBh = zop(mB, bufB, 0, k, z0c), zBl = zop(mB, bufB, 1, k, z0c);
-          for (int kq = 0; kq < itm.kblocks; ++kq) {
-            const int kb = itm.rev ? itm.kblocks - 1 - kq : kq;
-            if (!mbar_wait(bar_empty + 8 * stage, phase ^ 1, limit_ns, abort_flag,
-                           timeout_global)) {
-              ok = false;
-              break;
-            }
-            const uint32_t sA = ring + stage * P_STAGE_BYTES;
-            if (leader) mbar_expect_tx(bar_full + 8 * stage, 2 * P_STAGE_BYTES);
-            const uint32_t fb = lead_full + 8 * stage;
-            tma_load_3d_pair(sA, &gi.map, kb * BK, rowA, zAh, fb);
-            tma_load_3d_pair(sA + A_BYTES, &gi.map, kb * BK, rowA, zAl, fb);
-            tma_load_3d_pair(sA + 2 * A_BYTES, &gi.map, kb * BK, rowB, zBh, fb);
-            tma_load_3d_pair(sA + 3 * A_BYTES, &gi.map, kb * BK, rowB, zBl, fb);
-            if (++stage == P_STAGES) {
-              stage = 0;
-              phase ^= 1;
-            }
-          }
-        }
+        ok = produce_item(rg, &gi.map, sti, itm.job, itm.passes, gi.k, gi.k, sti->cur0,
+                          sti->z0_cur, I2 * 2 * BM + (int)rank * BM, J * BN + (int)rank * BM,
+                          itm.kblocks, itm.rev, leader, ring, bar_full, bar_empty, lead_full,
+                          limit_ns, abort_flag, timeout_global);
       }
-      // wait (bounded) for this CTA's copies to land before the CTA may exit
-      for (int i = 0; i < P_STAGES; ++i) {
-        const uint64_t t0 = gtimer();
-        while (!mbar_try_wait(bar_empty + 8 * stage, phase ^ 1) && gtimer() - t0 < limit_ns) {
-        }
-        if (++stage == P_STAGES) {
-          stage = 0;
-          phase ^= 1;
-        }
-      }
+      producer_drain(rg, bar_empty, limit_ns);
     }
   } else if (warp == 1) {
     // ================= MMA issuer (leader CTA only) =================
     if (leader && lane == 0) {
-      constexpr uint32_t idesc = make_idesc_m256(BF16 ? 1 : 0);
-      int stage = 0;
-      uint32_t phase = 0;
-      int ab = 0;
-      uint32_t abphase = 0;
+      RingPos rg, tb;
       bool ok = true;
       for (int64_t g = pair; g < items && ok; g += npairs) {
         const GroupItem itm = group_item(inst, first, jmask, count, g, k_snake);
-        const int kblocks = itm.kblocks;
-        const int nst = itm.passes * kblocks;
-        uint32_t d = 0, acc = 0;
-        int sp = 0;   // stage within its K pass
-        int cp = 0;   // stage within its accumulation chunk
-        for (int si = 0; si < nst; ++si) {
-          if (cp == 0) {
-            if (!mbar_wait(bar_tempty + 8 * ab, abphase ^ 1, limit_ns, abort_flag,
-                           timeout_global)) {
-              ok = false;
-              break;
-            }
-            fence_after();
-            d = tmem_base + (uint32_t)(ab * BN);
-            acc = 0;
-          }
-          if (!mbar_wait(bar_full + 8 * stage, phase, limit_ns, abort_flag, timeout_global)) {
-            ok = false;
-            break;
-          }
-          fence_after();
-          const uint32_t sA = ring + stage * P_STAGE_BYTES;
-          const uint64_t ah = sw64_desc(sA), al = sw64_desc(sA + A_BYTES);
-          const uint64_t bh = sw64_desc(sA + 2 * A_BYTES);
-          const uint64_t bl = sw64_desc(sA + 3 * A_BYTES);
-#pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint64_t off = (uint64_t)((kk * 32) >> 4);
-            mma_f16_pair(d, ah + off, bh + off, idesc, acc);   // hi * hi
-            acc = 1;
-            mma_f16_pair(d, ah + off, bl + off, idesc, 1);     // hi * lo
-            mma_f16_pair(d, al + off, bh + off, idesc, 1);     // lo * hi
-          }
-          mma_commit_pair(bar_empty + 8 * stage);   // frees the stage in both CTAs
-          if (++stage == P_STAGES) {
-            stage = 0;
-            phase ^= 1;
-          }
-          const bool chunk_end = cp == chunk - 1 || sp == kblocks - 1;
-          if (++cp == chunk || sp == kblocks - 1) cp = 0;
-          if (++sp == kblocks) sp = 0;
-          if (chunk_end) {
-            mma_commit_pair(bar_tfull + 8 * ab);    // chunk ready in both CTAs
-            if (++ab == 2) {
-              ab = 0;
-              abphase ^= 1;
-            }
-          }
-        }
+        ok = mma_item<BF16>(rg, tb, itm.passes * itm.kblocks, itm.kblocks, chunk, tmem_base,
+                            ring, bar_full, bar_empty, bar_tfull, bar_tempty, limit_ns,
+                            abort_flag, timeout_global);
       }
       asm volatile(
           "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
