@@ -40,10 +40,18 @@ Readings taken where the text is silent or inconsistent:
 Everything else (N_X = Tr X_n, the N_S bookkeeping of Alg. 2, FroErr^(0)
 from the X_n of the converging layer) follows the algorithms as printed.
 
+Higher orders (order = m >= 2): S^(o) for o = 2..m follow Eq. (S_n
+detailed) with S^(o)_0 = 0 (a linear perturbation), each stopped by the
+Alg. 3 test applied to its own idempotency error (the paper states the
+criteria for orders 0 and 1 only; this is the reading taken for o >= 2).
+
 Pinned by: agreement with ``sos.response_sos`` (a different route to the
 same limit), the 2x2 closed form, the invariants, and an independent plain
 SP2 run on the 2n x 2n block upper-triangular matrix [[H, H1], [0, H]]
-(Sec. III B) whose upper-right block must equal S1 layer by layer.
+(Sec. III B) whose upper-right block must equal S1 layer by layer.  Orders
+o >= 2 are pinned by the (m+1)n block matrix with H1 on the block
+superdiagonal, sympy derivatives of the 2x2 projector, finite differences
+of the second-order sum over states, and the identities of each order.
 """
 
 from dataclasses import dataclass, field
@@ -69,7 +77,9 @@ class SP2Result:
     bounds: tuple = (0.0, 0.0)
     checkpoints: dict = field(default_factory=dict)       # n -> S_n (if requested)
     d2_layer: List[int] = field(default_factory=list)    # order 2: layer whose test fired
-    P2: Optional[np.ndarray] = None     # (k, n, n) S2 at exit (D^(2)), order = 2
+    P2: Optional[np.ndarray] = None     # (k, n, n) S2 at exit (D^(2)), order >= 2
+    Pk: List[np.ndarray] = field(default_factory=list)   # [S^(o) at exit, (k, n, n)] for o = 1..order
+    dk_layer: List[List[int]] = field(default_factory=list)  # per order o = 1..order, per direction
 
 
 def _sign_tie_minus(x):
@@ -80,14 +90,18 @@ def sp2_pt(H, H1, n_occ, c_pt=9.0, c_d0=4.5, max_layers=100, bounds=None,
            keep_states=False, order=1):
     """Algorithms 1-3 in FP64.  H1: one (n, n) matrix or a (k, n, n) stack.
 
-    order = 2 also propagates the second-order term of Eq. (S_n detailed)
-    (H2 = 0, so S2_0 = 0):
-        S2_n = sigma_n (S0 S2 + S1 S1 + S2 S0) + (1 - sigma_n) S2.
-    The paper gives stopping criteria for orders 0 and 1 only; the reading
-    taken here applies the test of Alg. 3 to the second-order idempotency
-    error FroErr2_n = ||S2 - (S0 S2 + S1 S1 + S2 S0)||_F with the same C_pt
-    and FroErr^(0) (Eq. (ConvCrit) in the same form), each direction's S2
-    freezing when it fires; S2 keeps using the (possibly frozen) S1.
+    order = m >= 2 also propagates the higher-order terms of
+    Eq. (S_n detailed) (a linear perturbation: H^(o) = 0 for o >= 2, so
+    S^(o)_0 = 0):
+        S^(o)_n = sigma_n sum_{a=0..o} S^(a)_{n-1} S^(o-a)_{n-1}
+                  + (1 - sigma_n) S^(o)_{n-1},
+    every activation formed from the states at the start of the layer.  The
+    paper gives stopping criteria for orders 0 and 1 only; the reading taken
+    here applies the test of Alg. 3 to each order's idempotency error
+    FroErr^(o)_n = ||S^(o) - sum_a S^(a) S^(o-a)||_F with the same C_pt and
+    FroErr^(0) (Eq. (ConvCrit) in the same form), each direction's S^(o)
+    freezing when it fires; higher orders keep using the (possibly frozen)
+    lower ones.
     """
     H = np.asarray(H, dtype=np.float64)
     H1 = np.asarray(H1, dtype=np.float64)
@@ -95,13 +109,17 @@ def sp2_pt(H, H1, n_occ, c_pt=9.0, c_d0=4.5, max_layers=100, bounds=None,
         H1 = H1[None]
     n = H.shape[0]
     k = H1.shape[0]
+    if order < 1:
+        raise ValueError("order >= 1")
     if not (0 <= n_occ <= n):
         raise ValueError("n_occ out of range")
     if n_occ == 0 or n_occ == n:
         P = np.zeros((n, n)) if n_occ == 0 else np.eye(n)
-        return SP2Result(P=P, P1=np.zeros((k, n, n)), layers=0, d0_layer=0,
+        zeros = [np.zeros((k, n, n)) for _ in range(order)]
+        return SP2Result(P=P, P1=zeros[0], layers=0, d0_layer=0,
                          converged=True, froerr1=[[] for _ in range(k)],
-                         d1_layer=[0] * k)
+                         d1_layer=[0] * k, P2=zeros[1] if order >= 2 else None,
+                         d2_layer=[0] * k, Pk=zeros, dk_layer=[[0] * k for _ in range(order)])
 
     # Alg. 1 inputs: spectral bound estimates of H^(0)
     eps1, epsN = gershgorin_bounds(H) if bounds is None else bounds
@@ -109,37 +127,41 @@ def sp2_pt(H, H1, n_occ, c_pt=9.0, c_d0=4.5, max_layers=100, bounds=None,
     W0 = -1.0 / (epsN - eps1)
     S0 = W0 * H + (epsN / (epsN - eps1)) * np.eye(n)
     NS = np.trace(S0)
-    S1 = [W0 * H1[j] for j in range(k)]                 # B_0^(1) = 0
-    S2 = [np.zeros((n, n)) for _ in range(k)] if order == 2 else []
-    d2_conv = [order != 2] * k
-    froerr2 = [dict() for _ in range(k)]
-    d2_layer = [0] * k
+    # S[o][j]: order o = 1..order of direction j; B_0^(1) = 0, S^(o)_0 = 0 for o >= 2
+    S = {1: [W0 * H1[j] for j in range(k)]}
+    for o in range(2, order + 1):
+        S[o] = [np.zeros((n, n)) for _ in range(k)]
+    conv = {o: [False] * k for o in range(1, order + 1)}
+    froerr = {o: [dict() for _ in range(k)] for o in range(1, order + 1)}
+    dlayer = {o: [0] * k for o in range(1, order + 1)}
 
     n_layer = 1
     d0_conv = False
-    d1_conv = [False] * k
     sigma = {}
     iderr = {}
-    froerr1 = [dict() for _ in range(k)]
     froerr0 = None
     d0_layer = 0
-    d1_layer = [0] * k
     ckpt = {0: S0.copy()} if keep_states else {}
     converged = True
 
-    while not (d0_conv and all(d1_conv) and all(d2_conv)):
+    def all_conv():
+        return all(all(conv[o]) for o in conv)
+
+    while not (d0_conv and all_conv()):
         if n_layer > max_layers:
             converged = False
             n_layer -= 1
             break
-        # activation f^(1) for every direction still running
-        X1 = [None] * k
-        X2 = [None] * k
-        for j in range(k):
-            if not d1_conv[j]:
-                X1[j] = S0 @ S1[j] + S1[j] @ S0
-            if order == 2 and not d2_conv[j]:
-                X2[j] = S0 @ S2[j] + S1[j] @ S1[j] + S2[j] @ S0   # uses S1_{n-1}
+        # activations f^(o) of every direction still running, from the layer-start states
+        X = {o: [None] * k for o in range(1, order + 1)}
+        for o in range(1, order + 1):
+            for j in range(k):
+                if conv[o][j]:
+                    continue
+                acc = S0 @ S[o][j] + S[o][j] @ S0
+                for a in range(1, o):
+                    acc = acc + S[a][j] @ S[o - a][j]
+                X[o][j] = acc
         if not d0_conv:
             X0 = S0 @ S0                                  # activation f^(0)
             NX = np.trace(X0)
@@ -164,32 +186,21 @@ def sp2_pt(H, H1, n_occ, c_pt=9.0, c_d0=4.5, max_layers=100, bounds=None,
                     ckpt[n_layer] = S0.copy()
         else:
             sigma[n_layer] = -sigma[n_layer - 1]           # the sigma flip
-        # ---- Alg. 3, per direction
+        # ---- Alg. 3 (and its reading for o >= 2), per order and direction
         s = sigma[n_layer]
-        for j in range(k):
-            if d1_conv[j]:
-                continue
-            if d0_conv:
-                fe = np.linalg.norm(S1[j] - X1[j], "fro")
-                froerr1[j][n_layer] = fe
-                prev = froerr1[j].get(n_layer - 2)
-                if n_layer - 2 >= d0_layer and prev is not None and fe >= c_pt * froerr0 * prev:
-                    d1_conv[j] = True
-                    d1_layer[j] = n_layer
-            if not d1_conv[j]:
-                S1[j] = s * X1[j] + (1 - s) * S1[j]
-        for j in range(k):
-            if d2_conv[j]:
-                continue
-            if d0_conv:
-                fe = np.linalg.norm(S2[j] - X2[j], "fro")
-                froerr2[j][n_layer] = fe
-                prev = froerr2[j].get(n_layer - 2)
-                if n_layer - 2 >= d0_layer and prev is not None and fe >= c_pt * froerr0 * prev:
-                    d2_conv[j] = True
-                    d2_layer[j] = n_layer
-            if not d2_conv[j]:
-                S2[j] = s * X2[j] + (1 - s) * S2[j]
+        for o in range(1, order + 1):
+            for j in range(k):
+                if conv[o][j]:
+                    continue
+                if d0_conv:
+                    fe = np.linalg.norm(S[o][j] - X[o][j], "fro")
+                    froerr[o][j][n_layer] = fe
+                    prev = froerr[o][j].get(n_layer - 2)
+                    if n_layer - 2 >= d0_layer and prev is not None and fe >= c_pt * froerr0 * prev:
+                        conv[o][j] = True
+                        dlayer[o][j] = n_layer
+                if not conv[o][j]:
+                    S[o][j] = s * X[o][j] + (1 - s) * S[o][j]
         n_layer += 1
     else:
         n_layer -= 1
@@ -197,15 +208,16 @@ def sp2_pt(H, H1, n_occ, c_pt=9.0, c_d0=4.5, max_layers=100, bounds=None,
     layers = n_layer
     fe_lists = []
     for j in range(k):
-        fe_lists.append([froerr1[j].get(m, float("nan")) for m in range(1, layers + 1)])
-    return SP2Result(P=S0, P1=np.stack(S1), layers=layers, d0_layer=d0_layer,
-                     converged=converged, P2=np.stack(S2) if order == 2 else None,
-                     d2_layer=d2_layer,
+        fe_lists.append([froerr[1][j].get(m, float("nan")) for m in range(1, layers + 1)])
+    Pk = [np.stack(S[o]) for o in range(1, order + 1)]
+    return SP2Result(P=S0, P1=Pk[0], layers=layers, d0_layer=d0_layer,
+                     converged=converged, P2=Pk[1] if order >= 2 else None,
+                     d2_layer=dlayer[2] if order >= 2 else [0] * k,
                      sigma=[sigma[m] for m in range(1, layers + 1)],
                      iderr=[iderr[m] for m in sorted(iderr)],
                      froerr0=float(froerr0) if froerr0 is not None else float("nan"),
-                     froerr1=fe_lists, d1_layer=d1_layer, bounds=(eps1, epsN),
-                     checkpoints=ckpt)
+                     froerr1=fe_lists, d1_layer=dlayer[1], bounds=(eps1, epsN),
+                     checkpoints=ckpt, Pk=Pk, dk_layer=[dlayer[o] for o in range(1, order + 1)])
 
 
 def sp2_adjoint(H, G, n_occ, sigma_d0, bounds):
