@@ -713,6 +713,12 @@ constexpr int P_STAGES = 6;
 constexpr int64_t kRolledMaxN = 4096;   // padded sizes that use the rolled tile epilogue
 constexpr int P_STAGE_BYTES = 2 * A_BYTES + 2 * A_BYTES;   // A hi/lo + B-half hi/lo: 32 KB
 constexpr int P_SMEM_BYTES = P_STAGES * P_STAGE_BYTES + 1024 + 1024 + EPI_THREADS * 4 * 8;
+// The rolled form's epilogue warps also keep a 2560-byte transpose buffer
+// each (32 rows of 20 words); it shares its space with the reduction array,
+// which is used only after every epilogue warp has left its tile epilogue.
+constexpr int P_SCRATCH_ROLLED = EPI_WARPS * 32 * 20 * 4;
+static_assert(P_SCRATCH_ROLLED >= EPI_THREADS * 4 * 8, "reduction array fits the scratch");
+constexpr int P_SMEM_BYTES_ROLLED = P_STAGES * P_STAGE_BYTES + 1024 + 1024 + P_SCRATCH_ROLLED;
 
 __host__ __device__ inline int64_t num_pair_tiles(int64_t Np) {
   const int64_t tj = Np / BN;
@@ -923,102 +929,158 @@ __device__ __forceinline__ bool mma_item(RingPos& rg, RingPos& tb, int nst, int 
   return true;
 }
 
+// Bit pattern of a 16-bit float (FP16 or BF16).
+template <class H16>
+__device__ __forceinline__ uint32_t h16_bits(H16 x) {
+  return (uint32_t)(*reinterpret_cast<const uint16_t*>(&x));
+}
+
 // Rolled tile epilogue of one thread: its row r, columns c0 .. c0 + 127 of a
 // pair tile, whose sums the caller has written to tensor memory at ta_sum.
-// Reads the old master 32 columns at a time (eight float4 through the
-// read-only path: the old master is not written during the layer), so a tile
-// waits on four memory round trips instead of one per 4-column group; then
-// forms S_new = sigma X + (1 - sigma) S_old (Eq. (eq:Sn) / Eq. (dB)), its
+// Forms S_new = sigma X + (1 - sigma) S_old (Eq. (eq:Sn) / Eq. (dB)), its
 // FP16/BF16 hi/lo split (Sec. II C), the partial sums (||S_new||_F^2 with
 // TwoSum compensation, ||S_old - X||_F^2, trace, non-finite count) and stores
 // each owned element (column >= row) at (r, c) and (c, r).  OFF: the tile is
 // off the diagonal (every column > every row).
+//
+// Memory access pattern.  A warp holds 32 consecutive rows (one per lane)
+// and the same columns, so an access down a column (lane = row) is one
+// contiguous segment while an access along its rows touches 32 lines.
+//  * S_old is read down the columns: the masters are exactly symmetric
+//    (both halves are written with the same value), so S_old[r][c] is read
+//    at (c, r), 32 columns per batch of loads.
+//  * The mirror (c, r) is stored down the columns directly.
+//  * The row-direction stores (r, c) go through this warp's transpose
+//    buffer `xp` in shared memory (32 rows of XP_STRIDE words; 16 columns at
+//    a time): each lane writes its row, then the warp stores 4 rows x 64 B
+//    (FP32) or 4 rows x 32 B (hi, lo) per instruction.  The row stride of
+//    20 words keeps both the 16-byte row writes and the column-pair reads
+//    free of bank conflicts.
+// The arithmetic and the order of the per-thread sums are those of the
+// unrolled epilogue.
+constexpr int XP_STRIDE = 20;                       // words per buffer row
+constexpr int XP_WARP_BYTES = 32 * XP_STRIDE * 4;   // 2560 B per epilogue warp
+static_assert(EPI_WARPS * XP_WARP_BYTES == P_SCRATCH_ROLLED, "transpose buffers");
 template <class CV, bool OFF>
 __device__ __forceinline__ void rolled_tile_epilogue(
     const uint32_t ta_sum, const float* __restrict__ Sold, float* Snew, typename CV::T* hi_new,
-    typename CV::T* lo_new, const size_t row_off, const int64_t Np, const int r, const int c0,
-    const float sg, const float om, const float scale_new, const bool write, float& fn_s,
-    float& fn_c, float& fd, float& trf, int& bad) {
-  using H16 = typename CV::T;
+    typename CV::T* lo_new, uint32_t* xp, const int lane, const int64_t Np, const int r,
+    const int c0, const float sg, const float om, const float scale_new, const bool write,
+    float& fn_s, float& fn_c, float& fd, float& trf, int& bad) {
+  const int r0 = r - lane;   // row of lane 0
+  const int np = (int)Np;
+  // element (c, r) of the tile's columns at col_base + (c - c0) * np; element
+  // (r0 + i, c) at row_base + i * np + (c - c0)  (32-bit offsets)
+  const size_t col_base = (size_t)c0 * Np + r;
+  const size_t row_base = (size_t)r0 * Np + c0;
+  const float* Sc = Sold + col_base;
+  float* Snc = Snew + col_base;
+  uint16_t* hic = reinterpret_cast<uint16_t*>(hi_new) + col_base;
+  uint16_t* loc = reinterpret_cast<uint16_t*>(lo_new) + col_base;
+  float* Snr = Snew + row_base;
+  uint16_t* hir = reinterpret_cast<uint16_t*>(hi_new) + row_base;
+  uint16_t* lor = reinterpret_cast<uint16_t*>(lo_new) + row_base;
+  float olds[16];   // S_old of the current 16 columns; the next 16 are loaded
+                    // while the current ones are stored
+#pragma unroll
+  for (int q = 0; q < 16; ++q) olds[q] = __ldg(Sc + q * np);
 #pragma unroll 1
-  for (int g32 = 0; g32 < 4; ++g32) {
-    float4 o4s[8];
+  for (int g16 = 0; g16 < 8; ++g16) {
+    uint32_t xs[16];
+    tmem_ld16(ta_sum + 16 * g16, xs);
+    const int cb16 = c0 + 16 * g16;
+    // FP32 values go to the transpose buffer as each group of 4 is formed;
+    // the hi/lo bits stay in registers, packed in column pairs, until the
+    // FP32 rows have been stored
+    float4* xr = reinterpret_cast<float4*>(xp + lane * XP_STRIDE);
+    uint32_t hp[8], lp[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-      o4s[q] = __ldg(reinterpret_cast<const float4*>(Sold + c0 + 32 * g32 + 4 * q));
+    for (int i = 0; i < 8; ++i) hp[i] = lp[i] = 0u;
 #pragma unroll
-    for (int g2 = 0; g2 < 2; ++g2) {
-      uint32_t xs[16];
-      tmem_ld16(ta_sum + 32 * g32 + 16 * g2, xs);
+    for (int gg = 0; gg < 4; ++gg) {
+      const int cb = cb16 + 4 * gg;
+      if (!OFF && r > cb + 3) continue;
+      float nw[4];
 #pragma unroll
-      for (int gg = 0; gg < 4; ++gg) {
-        const int cb = c0 + 32 * g32 + 16 * g2 + 4 * gg;
-        if (!OFF && r > cb + 3) continue;
-        const float4 o4 = o4s[4 * g2 + gg];
-        const float old[4] = {o4.x, o4.y, o4.z, o4.w};
-        float nw[4];
-        H16 nh[4], nl[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const float xv = __uint_as_float(xs[4 * gg + i]);
-          const int c = cb + i;
-          const bool own = OFF || c >= r;
-          const float w = (!OFF && c == r) ? 1.0f : 2.0f;
-          bad += (own && !isfinite(xv)) ? 1 : 0;
-          const float dd = old[i] - xv;
-          fd = own ? fmaf(w * dd, dd, fd) : fd;
-          const float n1 = sg * xv + om * old[i];
-          nw[i] = n1;
-          if (own && write) {
-            const float p = w * n1 * n1;
-            const float e = w * fmaf(n1, n1, -n1 * n1);
-            const float tt = fn_s + p;
-            const float bp = tt - fn_s;
-            fn_c += (fn_s - (tt - bp)) + (p - bp) + e;
-            fn_s = tt;
-            if (!OFF && c == r) trf += n1;
-          }
-          const float y = n1 * scale_new;
-          nh[i] = CV::to(y);
-          nl[i] = CV::to(y - CV::from(nh[i]));
+      for (int i = 0; i < 4; ++i) {
+        const int e = 4 * gg + i;
+        const float xv = __uint_as_float(xs[e]);
+        const int c = cb + i;
+        const bool own = OFF || c >= r;
+        const float w = (!OFF && c == r) ? 1.0f : 2.0f;
+        bad += (own && !isfinite(xv)) ? 1 : 0;
+        const float old = olds[e];
+        const float dd = old - xv;
+        fd = own ? fmaf(w * dd, dd, fd) : fd;
+        const float n1 = sg * xv + om * old;
+        nw[i] = n1;
+        if (own && write) {
+          const float p = w * n1 * n1;
+          const float ee = w * fmaf(n1, n1, -n1 * n1);
+          const float tt = fn_s + p;
+          const float bp = tt - fn_s;
+          fn_c += (fn_s - (tt - bp)) + (p - bp) + ee;
+          fn_s = tt;
+          if (!OFF && c == r) trf += n1;
         }
-        if (!write) continue;
-        if (OFF || r <= cb) {
-          *reinterpret_cast<float4*>(Snew + row_off + cb) =
-              make_float4(nw[0], nw[1], nw[2], nw[3]);
-          uint2 ph, pl2;
-          ph.x = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[0])) |
-                 ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[1])) << 16);
-          ph.y = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[2])) |
-                 ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[3])) << 16);
-          pl2.x = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[0])) |
-                  ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[1])) << 16);
-          pl2.y = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[2])) |
-                  ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[3])) << 16);
-          *reinterpret_cast<uint2*>(hi_new + row_off + cb) = ph;
-          *reinterpret_cast<uint2*>(lo_new + row_off + cb) = pl2;
-        } else {
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            if (cb + i >= r) {
-              Snew[row_off + cb + i] = nw[i];
-              hi_new[row_off + cb + i] = nh[i];
-              lo_new[row_off + cb + i] = nl[i];
-            }
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int c = cb + i;
-          if (OFF || c > r) {
-            const size_t m = (size_t)c * Np + r;
-            Snew[m] = nw[i];
-            hi_new[m] = nh[i];
-            lo_new[m] = nl[i];
-          }
+        const float y = n1 * scale_new;
+        const typename CV::T h = CV::to(y);
+        const uint32_t hbits = h16_bits(h);
+        const uint32_t lbits = h16_bits(CV::to(y - CV::from(h)));
+        hp[e >> 1] |= hbits << (16 * (e & 1));
+        lp[e >> 1] |= lbits << (16 * (e & 1));
+        if (write && (OFF || c > r)) {   // mirror (c, r), down the column
+          const int m = (c - c0) * np;
+          Snc[m] = n1;
+          hic[m] = (uint16_t)hbits;
+          loc[m] = (uint16_t)lbits;
         }
       }
+      xr[gg] = make_float4(nw[0], nw[1], nw[2], nw[3]);
     }
+    if (g16 < 7) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) olds[q] = __ldg(Sc + (16 * (g16 + 1) + q) * np);
+    }
+    if (!write) continue;
+    // ---- row direction (r, c) through the transpose buffer
+    __syncwarp();
+#pragma unroll
+    for (int sidx = 0; sidx < 8; ++sidx) {
+      const int i = (sidx & 3) + 16 * (sidx >> 2) + 4 * (lane >> 3);   // rows i, +4, +8, +12
+      const int w2 = 2 * (lane & 7);
+      const float2 v = *reinterpret_cast<const float2*>(xp + i * XP_STRIDE + w2);
+      const int rr = r0 + i, c = cb16 + w2;
+      float* dst = Snr + i * np + (c - c0);
+      if (OFF || c >= rr)
+        *reinterpret_cast<float2*>(dst) = v;
+      else if (c + 1 >= rr)
+        dst[1] = v.y;
+    }
+    __syncwarp();
+    uint4* xr4 = reinterpret_cast<uint4*>(xp + lane * XP_STRIDE);
+    xr4[0] = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+    xr4[1] = make_uint4(hp[4], hp[5], hp[6], hp[7]);
+    xr4[2] = make_uint4(lp[0], lp[1], lp[2], lp[3]);
+    xr4[3] = make_uint4(lp[4], lp[5], lp[6], lp[7]);
+    __syncwarp();
+#pragma unroll
+    for (int sidx = 0; sidx < 8; ++sidx) {
+      const int i = 8 * (sidx >> 1) + (sidx & 1) + 2 * (lane >> 3);   // rows i, +2, +4, +6
+      const int m = lane & 7;                                           // column pair
+      const uint32_t vh = xp[i * XP_STRIDE + m];
+      const uint32_t vl = xp[i * XP_STRIDE + 8 + m];
+      const int rr = r0 + i, c = cb16 + 2 * m;
+      const int o = i * np + (c - c0);
+      if (OFF || c >= rr) {
+        *reinterpret_cast<uint32_t*>(hir + o) = vh;
+        *reinterpret_cast<uint32_t*>(lor + o) = vl;
+      } else if (c + 1 >= rr) {
+        hir[o + 1] = (uint16_t)(vh >> 16);
+        lor[o + 1] = (uint16_t)(vl >> 16);
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -1238,12 +1300,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
       // shared through a function: either form's register allocation depends
       // on it, and both were measured in exactly this shape.
       if constexpr (ROLLED) {
+        uint32_t* xp = reinterpret_cast<uint32_t*>(misc + 1024) +
+                       (warp - EPI_WARP0) * (XP_WARP_BYTES / 4);
         if (I2 < J)
-          rolled_tile_epilogue<CV, true>(ta_sum, Sold, Snew, hi_new, lo_new, row_off, Np, r, c0, sg,
-                                         om, scale_new, write, fn_s, fn_c, fd, trf, bad);
+          rolled_tile_epilogue<CV, true>(ta_sum, Sold - row_off, Snew, hi_new, lo_new, xp, lane, Np,
+                                         r, c0, sg, om, scale_new, write, fn_s, fn_c, fd, trf, bad);
         else
-          rolled_tile_epilogue<CV, false>(ta_sum, Sold, Snew, hi_new, lo_new, row_off, Np, r, c0,
-                                          sg, om, scale_new, write, fn_s, fn_c, fd, trf, bad);
+          rolled_tile_epilogue<CV, false>(ta_sum, Sold - row_off, Snew, hi_new, lo_new, xp, lane,
+                                          Np, r, c0, sg, om, scale_new, write, fn_s, fn_c, fd, trf,
+                                          bad);
         fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive_cluster(lead_tempty + 8 * ab);
@@ -1320,6 +1385,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
         }
       }
       }
+      if constexpr (ROLLED) epi_sync();   // the reduction array overlays the transpose buffers
       red[0 * EPI_THREADS + et] = (double)trf;
       red[1 * EPI_THREADS + et] = (double)fn_s + (double)fn_c;
       red[2 * EPI_THREADS + et] = (double)fd;
@@ -1425,7 +1491,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
   uint8_t* gbase = smem_raw + (base - raw);
   const uint32_t ring = base;
   uint8_t* misc = gbase + P_STAGES * P_STAGE_BYTES;
-  int64_t* first = reinterpret_cast<int64_t*>(misc + 1024 + EPI_THREADS * 4 * 8);
+  int64_t* first = reinterpret_cast<int64_t*>(misc + 1024 + P_SCRATCH_ROLLED);
   uint32_t* jmask = reinterpret_cast<uint32_t*>(first + count + 1);
 
   // ---- this layer's items of every instance (same values in every CTA:
@@ -1612,9 +1678,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
       const bool write = job != 0 || sti->plan_write0;
       const int r = I2 * 2 * BM + (int)rank * BM + rloc;
       const int c0 = J * BN + half * 128;
-      const size_t row_off = (size_t)r * Np;
       float* master = gi.master;
-      const float* Sold = master + (size_t)(curj * (1 + k) + job) * mat + row_off;
+      const float* Sold = master + (size_t)(curj * (1 + k) + job) * mat;
       float* Snew = master + (size_t)((curj ^ 1) * (1 + k) + job) * mat;
       const int zh_new = job == 0 ? sti->z0_next : zslice(curj ^ 1, job, 0, k);
       H16* hi_new = reinterpret_cast<H16*>(gi.ops) + (size_t)zh_new * mat;
@@ -1622,11 +1687,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 
       float fn_s = 0.0f, fn_c = 0.0f, fd = 0.0f, trf = 0.0f;
       int bad = 0;
+      uint32_t* xp = reinterpret_cast<uint32_t*>(misc + 1024) +
+                     (warp - EPI_WARP0) * (XP_WARP_BYTES / 4);
       if (I2 < J)
-        rolled_tile_epilogue<CV, true>(ta_sum, Sold, Snew, hi_new, lo_new, row_off, Np, r, c0, sg,
-                                       om, scale_new, write, fn_s, fn_c, fd, trf, bad);
+        rolled_tile_epilogue<CV, true>(ta_sum, Sold, Snew, hi_new, lo_new, xp, lane, Np, r, c0,
+                                       sg, om, scale_new, write, fn_s, fn_c, fd, trf, bad);
       else
-        rolled_tile_epilogue<CV, false>(ta_sum, Sold, Snew, hi_new, lo_new, row_off, Np, r, c0,
+        rolled_tile_epilogue<CV, false>(ta_sum, Sold, Snew, hi_new, lo_new, xp, lane, Np, r, c0,
                                         sg, om, scale_new, write, fn_s, fn_c, fd, trf, bad);
       fence_before();
       __syncwarp();
@@ -1635,6 +1702,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
         ab = 0;
         abphase ^= 1;
       }
+      epi_sync();   // the reduction array overlays the transpose buffers
       red[0 * EPI_THREADS + et] = (double)trf;
       red[1 * EPI_THREADS + et] = (double)fn_s + (double)fn_c;
       red[2 * EPI_THREADS + et] = (double)fd;
@@ -1696,11 +1764,12 @@ int device_setup() {
     cudaFuncSetAttribute(layer_tc2_kernel<true, false>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
     cudaFuncSetAttribute(layer_tc2_kernel<false, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES_ROLLED);
     cudaFuncSetAttribute(layer_tc2_kernel<true, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
-    const int group_smem = P_SMEM_BYTES + (kGroupMax + 1) * (int)sizeof(int64_t) +
-                           kGroupMax * (int)sizeof(uint32_t);
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES_ROLLED);
+    constexpr int group_smem = P_SMEM_BYTES_ROLLED + (kGroupMax + 1) * (int)sizeof(int64_t) +
+                               kGroupMax * (int)sizeof(uint32_t);
+    static_assert(group_smem <= 227 * 1024, "grouped kernel shared memory");
     cudaFuncSetAttribute(layer_tc2_group_kernel<false>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, group_smem);
     cudaFuncSetAttribute(layer_tc2_group_kernel<true>,
@@ -1772,7 +1841,8 @@ cudaError_t launch_layer_tc_group(const GroupInst* inst, int count, bool bf16, i
                                   int sm_count, cudaStream_t s) {
   using namespace tc;
   if (count < 1 || count > kGroupMax) return cudaErrorInvalidValue;
-  const int smem = P_SMEM_BYTES + (count + 1) * (int)sizeof(int64_t) + count * (int)sizeof(uint32_t);
+  const int smem =
+      P_SMEM_BYTES_ROLLED + (count + 1) * (int)sizeof(int64_t) + count * (int)sizeof(uint32_t);
   if (device_setup() == 0) return cudaErrorInvalidDevice;
   const uint64_t limit_ns = (uint64_t)(timeout_s * 1e9);
   const int ck = accum_chunk_k > 0 ? accum_chunk_k : DEFAULT_CHUNK_K;
@@ -1818,9 +1888,9 @@ cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double ti
     const bool rolled = L.Np <= kRolledMaxN;
     auto kern = bf16 ? (rolled ? layer_tc2_kernel<true, true> : layer_tc2_kernel<true, false>)
                      : (rolled ? layer_tc2_kernel<false, true> : layer_tc2_kernel<false, false>);
-    kern<<<grid, NUM_THREADS, P_SMEM_BYTES, s>>>(mA, st, master, ops, L.Np, L.k, partials,
-                                                 L.partial_tiles, limit_ns, chunk, k_snake, band,
-                                                 inject_stall);
+    kern<<<grid, NUM_THREADS, rolled ? P_SMEM_BYTES_ROLLED : P_SMEM_BYTES, s>>>(
+        mA, st, master, ops, L.Np, L.k, partials, L.partial_tiles, limit_ns, chunk, k_snake, band,
+        inject_stall);
     if (entries) *entries = 2 * tiles;
     if (pass_flops) *pass_flops = (double)tiles * 2 * BM * BN * (double)L.Np * 2.0;
     return cudaGetLastError();
