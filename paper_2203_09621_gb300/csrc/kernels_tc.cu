@@ -710,15 +710,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 //   tempty[b] leader only: 16 arrivals (8 epilogue warps per CTA)
 
 constexpr int P_STAGES = 6;
-constexpr int64_t kRolledMaxN = 4096;   // padded sizes that use the rolled tile epilogue
 constexpr int P_STAGE_BYTES = 2 * A_BYTES + 2 * A_BYTES;   // A hi/lo + B-half hi/lo: 32 KB
-constexpr int P_SMEM_BYTES = P_STAGES * P_STAGE_BYTES + 1024 + 1024 + EPI_THREADS * 4 * 8;
-// The rolled form's epilogue warps also keep a 2560-byte transpose buffer
-// each (32 rows of 20 words); it shares its space with the reduction array,
-// which is used only after every epilogue warp has left its tile epilogue.
-constexpr int P_SCRATCH_ROLLED = EPI_WARPS * 32 * 20 * 4;
-static_assert(P_SCRATCH_ROLLED >= EPI_THREADS * 4 * 8, "reduction array fits the scratch");
-constexpr int P_SMEM_BYTES_ROLLED = P_STAGES * P_STAGE_BYTES + 1024 + 1024 + P_SCRATCH_ROLLED;
+// Epilogue scratch: a 2560-byte transpose buffer per epilogue warp (32 rows
+// of 20 words); it shares its space with the reduction array of the tile's
+// partial sums, which is used only after every epilogue warp has left its
+// tile epilogue.
+constexpr int P_SCRATCH = EPI_WARPS * 32 * 20 * 4;
+static_assert(P_SCRATCH >= EPI_THREADS * 4 * 8, "reduction array fits the scratch");
+constexpr int P_SMEM_BYTES = P_STAGES * P_STAGE_BYTES + 1024 + 1024 + P_SCRATCH;
 
 __host__ __device__ inline int64_t num_pair_tiles(int64_t Np) {
   const int64_t tj = Np / BN;
@@ -948,7 +947,8 @@ __device__ __forceinline__ uint32_t h16_bits(H16 x) {
 // contiguous segment while an access along its rows touches 32 lines.
 //  * S_old is read down the columns: the masters are exactly symmetric
 //    (both halves are written with the same value), so S_old[r][c] is read
-//    at (c, r), 32 columns per batch of loads.
+//    at (c, r), 16 columns per batch of loads; the next batch is loaded
+//    while the current one is stored.
 //  * The mirror (c, r) is stored down the columns directly.
 //  * The row-direction stores (r, c) go through this warp's transpose
 //    buffer `xp` in shared memory (32 rows of XP_STRIDE words; 16 columns at
@@ -956,11 +956,11 @@ __device__ __forceinline__ uint32_t h16_bits(H16 x) {
 //    (FP32) or 4 rows x 32 B (hi, lo) per instruction.  The row stride of
 //    20 words keeps both the 16-byte row writes and the column-pair reads
 //    free of bank conflicts.
-// The arithmetic and the order of the per-thread sums are those of the
-// unrolled epilogue.
+// The sums run over the columns in ascending order, so every thread's
+// partial sums do not depend on the memory access pattern.
 constexpr int XP_STRIDE = 20;                       // words per buffer row
 constexpr int XP_WARP_BYTES = 32 * XP_STRIDE * 4;   // 2560 B per epilogue warp
-static_assert(EPI_WARPS * XP_WARP_BYTES == P_SCRATCH_ROLLED, "transpose buffers");
+static_assert(EPI_WARPS * XP_WARP_BYTES == P_SCRATCH, "transpose buffers");
 template <class CV, bool OFF>
 __device__ __forceinline__ void rolled_tile_epilogue(
     const uint32_t ta_sum, const float* __restrict__ Sold, float* Snew, typename CV::T* hi_new,
@@ -1084,16 +1084,12 @@ __device__ __forceinline__ void rolled_tile_epilogue(
   }
 }
 
-// ROLLED selects how the tile epilogue reads the tile's sums.  false: from
-// the registers that accumulated the chunks, in a loop unrolled over the
-// 128 columns.  true: the sums are written back into the tensor-memory
-// buffer of the tile's last chunk and read 16 columns at a time in a rolled
-// loop (no register spills, far less code per tile); the buffer returns to
-// the MMA only after that loop, so the MMA can run one chunk ahead instead
-// of two.  The rolled form is faster when a launch has few tiles per pair;
-// on long launches the unrolled form's slower, HBM-bound tile epilogue keeps
-// the pairs closer to lockstep, which the operand panels' L2 reuse needs.
-template <bool BF16, bool ROLLED>
+// Tile epilogue of the pair kernel: after a tile's last chunk the sums are
+// written back into that chunk's tensor-memory buffer and read 16 columns at
+// a time by rolled_tile_epilogue (no register spills, little code per tile);
+// the buffer returns to the MMA after that loop, so the MMA runs one chunk
+// ahead of the epilogue during it.
+template <bool BF16>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     layer_tc2_kernel(const __grid_constant__ CUtensorMap mapA, State* st, float* __restrict__ master,
                      uint16_t* __restrict__ ops, int64_t Np, int k, double* __restrict__ partials,
@@ -1258,7 +1254,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
           for (int i = 0; i < 16; ++i) sum[16 * cc + i] = fmaf(__uint_as_float(x[i]), u, sum[16 * cc + i]);
         }
-        if (ROLLED && ch + 1 == nchunks) break;   // keep the last chunk's buffer
+        if (ch + 1 == nchunks) break;   // keep the last chunk's buffer
         fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive_cluster(lead_tempty + 8 * ab);
@@ -1268,14 +1264,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
         }
       }
       if (!alive) break;
-      // rolled form: the tile's sums go back into its last chunk's buffer
-      [[maybe_unused]] uint32_t ta_sum = 0;
-      if constexpr (ROLLED) {
-        ta_sum = tmem_base + tlane + (uint32_t)(ab * BN + half * 128);
+      // the tile's sums go back into its last chunk's buffer
+      const uint32_t ta_sum = tmem_base + tlane + (uint32_t)(ab * BN + half * 128);
 #pragma unroll
-        for (int cc = 0; cc < 8; ++cc) tmem_st16(ta_sum + 16 * cc, sum + 16 * cc);
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-      }
+      for (int cc = 0; cc < 8; ++cc) tmem_st16(ta_sum + 16 * cc, sum + 16 * cc);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 
       const int64_t t = it % tiles;
       int I2, J;
@@ -1287,8 +1280,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
       const bool write = job != 0 || write0;
       const int r = I2 * 2 * BM + (int)rank * BM + rloc;
       const int c0 = J * BN + half * 128;
-      const size_t row_off = (size_t)r * Np;
-      const float* Sold = master + (size_t)(curj * (1 + k) + job) * mat + row_off;
+      const float* Sold = master + (size_t)(curj * (1 + k) + job) * mat;
       float* Snew = master + (size_t)((curj ^ 1) * (1 + k) + job) * mat;
       const int zh_new = job == 0 ? z0n : zslice(curj ^ 1, job, 0, k);
       H16* hi_new = reinterpret_cast<H16*>(ops) + (size_t)zh_new * mat;
@@ -1296,96 +1288,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 
       float fn_s = 0.0f, fn_c = 0.0f, fd = 0.0f, trf = 0.0f;
       int bad = 0;
-      // The column loop is written out twice (rolled / unrolled) rather than
-      // shared through a function: either form's register allocation depends
-      // on it, and both were measured in exactly this shape.
-      if constexpr (ROLLED) {
-        uint32_t* xp = reinterpret_cast<uint32_t*>(misc + 1024) +
-                       (warp - EPI_WARP0) * (XP_WARP_BYTES / 4);
-        if (I2 < J)
-          rolled_tile_epilogue<CV, true>(ta_sum, Sold - row_off, Snew, hi_new, lo_new, xp, lane, Np,
-                                         r, c0, sg, om, scale_new, write, fn_s, fn_c, fd, trf, bad);
-        else
-          rolled_tile_epilogue<CV, false>(ta_sum, Sold - row_off, Snew, hi_new, lo_new, xp, lane,
-                                          Np, r, c0, sg, om, scale_new, write, fn_s, fn_c, fd, trf,
-                                          bad);
-        fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive_cluster(lead_tempty + 8 * ab);
-        if (++ab == 2) {
-          ab = 0;
-          abphase ^= 1;
-        }
-      } else {
-#pragma unroll
-      for (int g = 0; g < 32; ++g) {
-        const int cb = c0 + 4 * g;
-        if (r > cb + 3) continue;
-        const float4 o4 = *reinterpret_cast<const float4*>(Sold + cb);
-        const float old[4] = {o4.x, o4.y, o4.z, o4.w};
-        float nw[4];
-        H16 nh[4], nl[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const float xv = sum[4 * g + i];
-          const int c = cb + i;
-          const bool own = c >= r;
-          const float w = (c == r) ? 1.0f : 2.0f;
-          bad += (own && !isfinite(xv)) ? 1 : 0;
-          const float dd = old[i] - xv;
-          fd = own ? fmaf(w * dd, dd, fd) : fd;
-          const float n1 = sg * xv + om * old[i];
-          nw[i] = n1;
-          if (own && write) {
-            const float p = w * n1 * n1;
-            const float e = w * fmaf(n1, n1, -n1 * n1);
-            const float tt = fn_s + p;
-            const float bp = tt - fn_s;
-            fn_c += (fn_s - (tt - bp)) + (p - bp) + e;
-            fn_s = tt;
-            if (c == r) trf += n1;
-          }
-          const float y = n1 * scale_new;
-          nh[i] = CV::to(y);
-          nl[i] = CV::to(y - CV::from(nh[i]));
-        }
-        if (!write) continue;
-        if (r <= cb) {
-          *reinterpret_cast<float4*>(Snew + row_off + cb) = make_float4(nw[0], nw[1], nw[2], nw[3]);
-          uint2 ph, pl2;
-          ph.x = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[0])) |
-                 ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[1])) << 16);
-          ph.y = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[2])) |
-                 ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[3])) << 16);
-          pl2.x = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[0])) |
-                  ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[1])) << 16);
-          pl2.y = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[2])) |
-                  ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[3])) << 16);
-          *reinterpret_cast<uint2*>(hi_new + row_off + cb) = ph;
-          *reinterpret_cast<uint2*>(lo_new + row_off + cb) = pl2;
-        } else {
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            if (cb + i >= r) {
-              Snew[row_off + cb + i] = nw[i];
-              hi_new[row_off + cb + i] = nh[i];
-              lo_new[row_off + cb + i] = nl[i];
-            }
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int c = cb + i;
-          if (c > r) {
-            const size_t m = (size_t)c * Np + r;
-            Snew[m] = nw[i];
-            hi_new[m] = nh[i];
-            lo_new[m] = nl[i];
-          }
-        }
+      uint32_t* xp = reinterpret_cast<uint32_t*>(misc + 1024) +
+                     (warp - EPI_WARP0) * (XP_WARP_BYTES / 4);
+      if (I2 < J)
+        rolled_tile_epilogue<CV, true>(ta_sum, Sold, Snew, hi_new, lo_new, xp, lane, Np, r, c0,
+                                       sg, om, scale_new, write, fn_s, fn_c, fd, trf, bad);
+      else
+        rolled_tile_epilogue<CV, false>(ta_sum, Sold, Snew, hi_new, lo_new, xp, lane, Np, r, c0,
+                                        sg, om, scale_new, write, fn_s, fn_c, fd, trf, bad);
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(lead_tempty + 8 * ab);
+      if (++ab == 2) {
+        ab = 0;
+        abphase ^= 1;
       }
-      }
-      if constexpr (ROLLED) epi_sync();   // the reduction array overlays the transpose buffers
+      epi_sync();   // the reduction array overlays the transpose buffers
       red[0 * EPI_THREADS + et] = (double)trf;
       red[1 * EPI_THREADS + et] = (double)fn_s + (double)fn_c;
       red[2 * EPI_THREADS + et] = (double)fd;
@@ -1432,7 +1350,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 // by binary search over the prefix sums.  Everything an item computes --
 // its tile, passes, accumulation chunks, K direction (the K-snake parity is
 // taken from the round the single-instance launch would run it in) and its
-// tile epilogue (the rolled form) -- is what the single-instance kernel
+// tile epilogue -- is what the single-instance kernel
 // computes for it, so the results are the same bit for bit.
 
 // largest i with first[i] <= g (first[0] = 0 <= g)
@@ -1491,7 +1409,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
   uint8_t* gbase = smem_raw + (base - raw);
   const uint32_t ring = base;
   uint8_t* misc = gbase + P_STAGES * P_STAGE_BYTES;
-  int64_t* first = reinterpret_cast<int64_t*>(misc + 1024 + P_SCRATCH_ROLLED);
+  int64_t* first = reinterpret_cast<int64_t*>(misc + 1024 + P_SCRATCH);
   uint32_t* jmask = reinterpret_cast<uint32_t*>(first + count + 1);
 
   // ---- this layer's items of every instance (same values in every CTA:
@@ -1759,15 +1677,11 @@ int device_setup() {
                          SMEM_BYTES);
     cudaFuncSetAttribute(layer_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          SMEM_BYTES);
-    cudaFuncSetAttribute(layer_tc2_kernel<false, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
-    cudaFuncSetAttribute(layer_tc2_kernel<true, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
-    cudaFuncSetAttribute(layer_tc2_kernel<false, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES_ROLLED);
-    cudaFuncSetAttribute(layer_tc2_kernel<true, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES_ROLLED);
-    constexpr int group_smem = P_SMEM_BYTES_ROLLED + (kGroupMax + 1) * (int)sizeof(int64_t) +
+    cudaFuncSetAttribute(layer_tc2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         P_SMEM_BYTES);
+    cudaFuncSetAttribute(layer_tc2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         P_SMEM_BYTES);
+    constexpr int group_smem = P_SMEM_BYTES + (kGroupMax + 1) * (int)sizeof(int64_t) +
                                kGroupMax * (int)sizeof(uint32_t);
     static_assert(group_smem <= 227 * 1024, "grouped kernel shared memory");
     cudaFuncSetAttribute(layer_tc2_group_kernel<false>,
@@ -1842,7 +1756,7 @@ cudaError_t launch_layer_tc_group(const GroupInst* inst, int count, bool bf16, i
   using namespace tc;
   if (count < 1 || count > kGroupMax) return cudaErrorInvalidValue;
   const int smem =
-      P_SMEM_BYTES_ROLLED + (count + 1) * (int)sizeof(int64_t) + count * (int)sizeof(uint32_t);
+      P_SMEM_BYTES + (count + 1) * (int)sizeof(int64_t) + count * (int)sizeof(uint32_t);
   if (device_setup() == 0) return cudaErrorInvalidDevice;
   const uint64_t limit_ns = (uint64_t)(timeout_s * 1e9);
   const int ck = accum_chunk_k > 0 ? accum_chunk_k : DEFAULT_CHUNK_K;
@@ -1884,11 +1798,8 @@ cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double ti
     int64_t pairs = sms / 2;
     if (pairs > max_items) pairs = max_items;
     const int grid = (int)(2 * pairs);
-    // rolled tile epilogue up to n = 4096 (at most ~7 tiles per pair and job)
-    const bool rolled = L.Np <= kRolledMaxN;
-    auto kern = bf16 ? (rolled ? layer_tc2_kernel<true, true> : layer_tc2_kernel<true, false>)
-                     : (rolled ? layer_tc2_kernel<false, true> : layer_tc2_kernel<false, false>);
-    kern<<<grid, NUM_THREADS, rolled ? P_SMEM_BYTES_ROLLED : P_SMEM_BYTES, s>>>(
+    auto kern = bf16 ? layer_tc2_kernel<true> : layer_tc2_kernel<false>;
+    kern<<<grid, NUM_THREADS, P_SMEM_BYTES, s>>>(
         mA, st, master, ops, L.Np, L.k, partials, L.partial_tiles, limit_ns, chunk, k_snake, band,
         inject_stall);
     if (entries) *entries = 2 * tiles;

@@ -250,8 +250,8 @@ def test_full_size_dipole3_n8192(ctx):
 
 @pytest.mark.parametrize("precision", ["dual_fp16", "dual_bf16"])
 def test_full_size_cfg2_n4096(ctx, precision):
-    """Config 2 at its full size (n = 4096, n_occ = 2048, gap 0.2, one H1): the
-    largest size on the rolled tile epilogue.  Whole P and P1 against the
+    """Config 2 at its full size (n = 4096, n_occ = 2048, gap 0.2, one H1).
+    Whole P and P1 against the
     oracle evaluated from the known eigendecomposition, plus the idempotency
     identities P P = P and P P1 + P1 P = P1 on the GPU result."""
     inst = make_workload(2, backend="torch", device="cuda")
