@@ -44,10 +44,10 @@ K_DEFAULT = 3
 # n8192_k3_dram.md).  Valid only for that kernel source and that workload.
 TRAFFIC_RECORD = {
     "source": "paper_2203_09621_gb300/csrc/kernels_tc.cu",
-    "sha256": "eb566e1bd6ebfe65d52c016e6b05abe9ee71dfb76211550af9d80d6429166d2a",
+    "sha256": "cf62c42fd4f2724f41ac4642586560af79a442c4c93c48ba7b6f6685cdf64f3b",
     "workload": {"n": 8192, "k": 3, "precision": "dual_fp16", "cta_pair": 1, "k_snake": 1,
                  "tile_band": 8, "accum_chunk": 0},
-    "bytes_per_launch": 20.0370e9 + 2.0870e9,
+    "bytes_per_launch": 10.1845e9 + 2.0716e9,
 }
 
 

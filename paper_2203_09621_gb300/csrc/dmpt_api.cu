@@ -109,6 +109,7 @@ __global__ void state_init_kernel(State* st, int k, int max_layers, int precisio
   st->k_fwd = k;
   st->n = n;
   st->n_layer = 0;
+  st->round_ctr = 0u;
   st->done = 0;
   st->status = DMPT_OK;
   st->timeout_flag = 0;
@@ -918,8 +919,10 @@ static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
   auto issue_step = [&](int i) -> cudaError_t {
     cudaStream_t si = h->streams[i];
     void* ws = base + offs[i];
+    // the instances' layer kernels run side by side: no round alignment
     cudaError_t r = dual ? launch_layer_tc(L[i], ws, si, o->timeout_s, o->accum_chunk,
-                                           o->cta_pair, o->k_snake, o->tile_band, &entries[i], &pass_flops[i])
+                                           o->cta_pair, o->k_snake, o->tile_band, &entries[i],
+                                           &pass_flops[i], 0, /*round_align=*/0)
                          : launch_layer_simt(L[i], ws, si, &entries[i], &pass_flops[i]);
     if (r != cudaSuccess) return r;
     return launch_decide(L[i], ws, kDecideLayer, entries[i], si);

@@ -60,6 +60,8 @@ struct State {
   int rp_layers;        // replay: layers run
   int order;            // 1: first-order response; 2: also the second-order term
   int k1;               // first-order directions (jobs k1 + 1 .. 2 k1 are order 2)
+  unsigned round_ctr;   // pair kernel: rounds started by its CTAs (soft alignment);
+                        // every decide step resets it before the next launch
   int64_t n;
   int cur1[kMaxK];
   int d1_conv[kMaxK];
@@ -137,9 +139,13 @@ cudaError_t launch_trivial(int64_t n, int k, int64_t ld, int full, double* P,
 int simt_tile(int precision);
 
 // ---- tensor-core path (kernels_tc.cu) ----
+// round_align: the pair kernel's producers keep their rounds in step (a
+// bounded wait, never an error); off where several instances' layer kernels
+// run at the same time, whose CTAs need not all be resident.
 cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double timeout_s,
                             int accum_chunk_k, int cta_pair, int k_snake, int band,
-                            int64_t* entries, double* pass_flops, int inject_stall = 0);
+                            int64_t* entries, double* pass_flops, int inject_stall = 0,
+                            int round_align = 1);
 int tc_tile();
 
 // ---- grouped layer products of a batch (kernels_tc.cu) ----

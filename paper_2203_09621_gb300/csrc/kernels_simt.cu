@@ -425,6 +425,7 @@ __device__ void plan_replay(State* st, int m) {
 // 256 doubles, sums: (kMaxK + 1) x kNQ doubles of shared memory).
 __device__ void decide_body(State* st, const double* __restrict__ partials, int64_t ptiles,
                             int64_t entries, int mode, double* red, double (*sums)[kNQ]) {
+  if (threadIdx.x == 0) st->round_ctr = 0u;   // for the next pair-kernel launch
   if (st->done) return;
   const bool adj = mode == kDecideAdjInit || mode == kDecideAdjLayer;
   const bool rp = mode == kDecideReplayInit || mode == kDecideReplayLayer;

@@ -1084,6 +1084,34 @@ __device__ __forceinline__ void rolled_tile_epilogue(
   }
 }
 
+// Soft round alignment of the pair kernel's producers.  Items go to the
+// pairs round-robin, so the 76 tiles of a round share their operand panels
+// in L2 only while the pairs stay in step; a pair that drifts a round ahead
+// fetches those panels from HBM again (with the tile epilogue below the
+// pairs do drift, and DRAM reads per layer double).  At the start of each
+// round r >= 1 a producer counts itself in and waits until every CTA that
+// has an item in round r has started it.  The wait is bounded
+// (kRoundAlignNs) and is never an error: after an expiry that producer stops
+// waiting for the rest of the launch (it still counts itself in), so a grid
+// whose CTAs are not all resident at once costs at most one bound.
+constexpr uint64_t kRoundAlignNs = 300000;
+__device__ __forceinline__ void round_start(unsigned* ctr, int64_t round, int64_t items,
+                                            int64_t npairs, bool& align) {
+  atomicAdd(ctr, 1u);
+  if (!align) return;
+  // CTAs with an item in rounds 1 .. round (only the last round is partial)
+  const int64_t upto = (round + 1) * npairs < items ? (round + 1) * npairs : items;
+  const unsigned target = (unsigned)(2 * (upto - npairs));
+  const uint64_t t0 = gtimer();
+  while (*reinterpret_cast<volatile unsigned*>(ctr) < target) {
+    if (gtimer() - t0 > kRoundAlignNs) {
+      align = false;
+      return;
+    }
+    __nanosleep(128);
+  }
+}
+
 // Tile epilogue of the pair kernel: after a tile's last chunk the sums are
 // written back into that chunk's tensor-memory buffer and read 16 columns at
 // a time by rolled_tile_epilogue (no register spills, little code per tile);
@@ -1094,7 +1122,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     layer_tc2_kernel(const __grid_constant__ CUtensorMap mapA, State* st, float* __restrict__ master,
                      uint16_t* __restrict__ ops, int64_t Np, int k, double* __restrict__ partials,
                      int64_t ptiles, uint64_t limit_ns, int chunk, int k_snake, int band,
-                     int inject_stall) {
+                     int inject_stall, int round_align) {
   using CV = Cvt<BF16>;
   using H16 = typename CV::T;
   extern __shared__ uint8_t smem_raw[];
@@ -1172,7 +1200,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
       RingPos rg;
       bool ok = true;
       int64_t round = 0;
+      bool align = round_align != 0;
       for (int64_t it = pair; it < items && ok; it += npairs, ++round) {
+        if (round > 0) round_start(&st->round_ctr, round, items, npairs, align);
         const int job = job_at(jmask, (int)(it / tiles));
         int I2, J;
         pair_tile_banded(it % tiles, (int)(Np / BN), band, &I2, &J);
@@ -1773,7 +1803,8 @@ cudaError_t launch_layer_tc_group(const GroupInst* inst, int count, bool bf16, i
 
 cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double timeout_s,
                             int accum_chunk_k, int cta_pair, int k_snake, int band,
-                            int64_t* entries, double* pass_flops, int inject_stall) {
+                            int64_t* entries, double* pass_flops, int inject_stall,
+                            int round_align) {
   using namespace tc;
   char* base = (char*)ws;
   const bool bf16 = L.precision == DMPT_DUAL_BF16;
@@ -1801,7 +1832,7 @@ cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double ti
     auto kern = bf16 ? layer_tc2_kernel<true> : layer_tc2_kernel<false>;
     kern<<<grid, NUM_THREADS, P_SMEM_BYTES, s>>>(
         mA, st, master, ops, L.Np, L.k, partials, L.partial_tiles, limit_ns, chunk, k_snake, band,
-        inject_stall);
+        inject_stall, round_align);
     if (entries) *entries = 2 * tiles;
     if (pass_flops) *pass_flops = (double)tiles * 2 * BM * BN * (double)L.Np * 2.0;
     return cudaGetLastError();
