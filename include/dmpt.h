@@ -42,7 +42,8 @@
 extern "C" {
 #endif
 
-#define DMPT_MAX_K 8        /* perturbation directions per call           */
+#define DMPT_MAX_K 8        /* response slots per call: directions x order */
+#define DMPT_MAX_ORDER 8    /* highest response order (k = 1)             */
 #define DMPT_MAX_LAYERS 256 /* upper bound of dmpt_options.max_layers      */
 
 typedef enum {
@@ -95,7 +96,8 @@ typedef struct {
   int k_snake;          /* CTA-pair form: 1 = alternate the K-sweep direction
                            between scheduling rounds for L2 reuse (default 1) */
   int order;            /* response order the workspace is sized for: 1
-                           (default), 2 for dmpt_sp2_response2                */
+                           (default); m for dmpt_sp2_response_m (2 for
+                           dmpt_sp2_response2)                                */
   int tile_band;        /* CTA-pair form: tile order in bands of this many
                            256-column blocks, row-major inside a band (L2 reuse
                            of operand panels); 0 = column-major (default 8)   */
@@ -198,6 +200,32 @@ dmpt_status dmpt_sp2_response2(dmpt_handle h, const double* H, const double* H1,
                                int64_t n, int64_t ld, int64_t n_occ, const dmpt_options* o,
                                double* P, double* P1, double* P2, dmpt_info* info,
                                void* workspace, size_t ws_bytes, void* stream);
+
+/* Responses of every order up to m (Sec. III A, Eq. (S_n detailed); Sec.
+ * III B: P_o = D^(o), the lambda^o Taylor coefficient of theta(mu - H -
+ * lambda H1), i.e. (1/o!) d^o P / dlambda^o).  With S_o,0 = 0 for o >= 2
+ * (a linear perturbation):
+ *   S_o,n = sigma_n (S0 S_o + S_o S0 + sum_{a=1}^{o-1} S_a S_{o-a})
+ *           + (1 - sigma_n) S_o,
+ * all terms from the states at the start of the layer, each term's
+ * products accumulated on the tensor cores in o + 1 K passes.  Each S_o
+ * stops by the test of Alg. 3 applied to its own idempotency error (the
+ * reading dmpt_sp2_response2 takes for order 2).
+ *   order  1 .. DMPT_MAX_ORDER, with order * k <= DMPT_MAX_K; order 1 is
+ *          dmpt_sp2_response (Pk unused), order 2 is dmpt_sp2_response2.
+ *   Pk     device, the terms of orders 2 .. order: (order - 1) k blocks of
+ *          n x n (ld), order o's direction j at Pk + ((o - 2) k + j) n ld.
+ *   Other arguments as dmpt_sp2_response; dual precisions and no tape for
+ *   order >= 2.  The workspace is dmpt_workspace_size(n, k, o) with
+ *   o->order = order.  In info, entries (o - 1) k .. o k - 1 of d1_layer /
+ *   froerr1 are those of order o.  Errors: DMPT_EINVAL for an order outside
+ *   [1, DMPT_MAX_ORDER], order * k > DMPT_MAX_K or a null Pk;
+ *   DMPT_EUNSUPPORTED for order >= 2 with a non-dual precision or a tape. */
+dmpt_status dmpt_sp2_response_m(dmpt_handle h, const double* H, const double* H1, int k,
+                                int64_t n, int64_t ld, int64_t n_occ, int order,
+                                const dmpt_options* o, double* P, double* P1, double* Pk,
+                                dmpt_info* info, void* workspace, size_t ws_bytes,
+                                void* stream);
 
 /* Adjoint of the S0 recursion: the gradient of L = Tr[G P] with respect to H
  * for the P of the preceding dmpt_sp2_response call that used `workspace`

@@ -81,7 +81,7 @@ bool valid_options(const dmpt_options* o) {
   if (o->accum_chunk < 0) return false;
   if (o->cta_pair < 0 || o->cta_pair > 1) return false;
   if (o->k_snake < 0 || o->k_snake > 1) return false;
-  if (o->order < 1 || o->order > 2) return false;
+  if (o->order < 1 || o->order > DMPT_MAX_ORDER) return false;
   if (o->tile_band < 0 || o->tile_band > 1024) return false;
   if (o->inject_stall < 0 || o->inject_stall > 1) return false;
   if (o->autotune < 0 || o->autotune > 1) return false;
@@ -92,7 +92,7 @@ bool valid_options(const dmpt_options* o) {
 // one when S0 states are kept, for the adjoint) and tape capacity.
 Layout layout_for(int64_t n, int k, const dmpt_options* o) {
   const bool tape = o->ckpt_every == 1;
-  const int slots = o->order == 2 ? 2 * k : ((tape && k == 0) ? 1 : k);
+  const int slots = o->order >= 2 ? o->order * k : ((tape && k == 0) ? 1 : k);
   return make_layout(n, slots, o->precision, tape ? o->max_layers + 2 : 0);
 }
 
@@ -101,7 +101,7 @@ __global__ void state_init_kernel(State* st, int k, int max_layers, int precisio
                                   int tape_states, int layout_k, int64_t n, int order = 1,
                                   int k1 = 0) {
   st->order = order;
-  st->k1 = order == 2 ? k1 : k;
+  st->k1 = order >= 2 ? k1 : k;
   st->tape = tape;
   st->tape_base = tape_base;
   st->tape_states = tape_states;
@@ -234,20 +234,31 @@ dmpt_status replay_run(dmpt_handle h, const Layout& L, const double* H1, const d
   return DMPT_OK;
 }
 
-double layer_alg_flops(double n, int prec, bool square, int active, int active2 = 0) {
-  // dual: square A + B + B^T (2 products), response A + B + C (3), second-order
-  // term S0 S2 (3, its transpose free) + S1 S1 (2, like the square)
-  const double n3x2 = 2.0 * n * n * n;
-  if (prec >= DMPT_DUAL_FP16)
-    return ((square ? 2.0 : 0.0) + 3.0 * active + 5.0 * active2) * n3x2;
-  return ((square ? 1.0 : 0.0) + 1.0 * active + 2.0 * active2) * n3x2;
+// Algorithmic products of an order-o term, S0 S_o + S_o S0 + sum_{a=1}^{o-1}
+// S_a S_{o-a}: S0 S_o (its transpose free), floor((o - 1) / 2) pairs
+// S_a S_{o-a} + (S_a S_{o-a})^T, and for even o the square S_{o/2}^2.  In
+// dual arithmetic a general product is 3 (A + B + C) and a square 2
+// (A + B + B^T); in a plain form 1 each.
+double term_products(int o, bool dual) {
+  const double gen = dual ? 3.0 : 1.0, sq = dual ? 2.0 : 1.0;
+  return gen * (1 + (o - 1) / 2) + (o % 2 == 0 ? sq : 0.0);
 }
 
+// active[o]: running terms of order o = 1 .. order
+double layer_alg_flops(double n, int prec, bool square, const int* active, int order) {
+  const bool dual = prec >= DMPT_DUAL_FP16;
+  double p = square ? (dual ? 2.0 : 1.0) : 0.0;
+  for (int od = 1; od <= order; ++od) p += term_products(od, dual) * active[od];
+  return p * 2.0 * n * n * n;
+}
+
+// executed: an order-o term runs o + 1 full-K passes (3 MMAs each in dual)
 double layer_mma_flops(const Layout& L, double per /* one full-K single-term pass */,
-                       bool square, int active, int active2 = 0) {
+                       bool square, const int* active, int order) {
   const bool dual = L.precision >= DMPT_DUAL_FP16;
-  return (square ? (dual ? 3.0 : 1.0) : 0.0) * per + active * (dual ? 6.0 : 2.0) * per +
-         active2 * 9.0 * per;
+  double passes = square ? (dual ? 3.0 : 1.0) : 0.0;
+  for (int od = 1; od <= order; ++od) passes += (od + 1) * (dual ? 3.0 : 1.0) * active[od];
+  return passes * per;
 }
 
 }  // namespace
@@ -333,7 +344,7 @@ size_t dmpt_workspace_size(int64_t n, int k, const dmpt_options* o) {
   dmpt_default_options(&d);
   if (!o) o = &d;
   if (n < 1 || k < 0 || k > DMPT_MAX_K || !valid_options(o)) return 0;
-  if (o->order == 2 && (2 * k > DMPT_MAX_K || k < 1)) return 0;
+  if (o->order >= 2 && (o->order * k > DMPT_MAX_K || k < 1)) return 0;
   return layout_for(n, k, o).total;
 }
 
@@ -349,9 +360,11 @@ dmpt_status dmpt_bounds(dmpt_handle h, const double* H, int64_t n, int64_t ld, d
   return DMPT_OK;
 }
 
+// Pk (order >= 2): the terms of orders 2 .. order, (order - 1) k blocks of n
+// x n (ld), order o's block j at Pk + ((o - 2) k + j) n ld.
 static dmpt_status forward_impl(dmpt_handle h, const double* H, const double* H1, int k,
                                 int64_t n, int64_t ld, int64_t n_occ, const dmpt_options* o,
-                                double* P, double* P1, double* P2, dmpt_info* info,
+                                double* P, double* P1, double* Pk, dmpt_info* info,
                                 void* workspace, size_t ws_bytes, void* stream) {
   const int order = o->order;
   if (info) memset(info, 0, sizeof(*info));
@@ -361,12 +374,13 @@ static dmpt_status forward_impl(dmpt_handle h, const double* H, const double* H1
   if (n < 1 || ld < n) return fail(h, DMPT_EINVAL, "dmpt_sp2_response: need n >= 1, ld >= n%s");
   if (n_occ < 0 || n_occ > n) return fail(h, DMPT_EINVAL, "dmpt_sp2_response: n_occ out of [0, n]%s");
   if (!valid_options(o)) return fail(h, DMPT_EINVAL, "dmpt_sp2_response: invalid options%s");
-  if (order == 2) {
-    if (k < 1 || 2 * k > DMPT_MAX_K || !P2)
-      return fail(h, DMPT_EINVAL, "dmpt_sp2_response2: need 1 <= k <= DMPT_MAX_K / 2 and P2%s");
+  if (order >= 2) {
+    if (k < 1 || order * k > DMPT_MAX_K || !Pk)
+      return fail(h, DMPT_EINVAL,
+                  "dmpt_sp2_response_m: need k >= 1, order * k <= DMPT_MAX_K and Pk%s");
     if (o->precision < DMPT_DUAL_FP16 || o->ckpt_every != 0)
       return fail(h, DMPT_EUNSUPPORTED,
-                  "dmpt_sp2_response2: the second order needs a dual precision and no tape%s");
+                  "dmpt_sp2_response_m: orders >= 2 need a dual precision and no tape%s");
   }
   if (o->ckpt_every != 0 && o->precision < DMPT_DUAL_FP16)
     return fail(h, DMPT_EUNSUPPORTED,
@@ -376,7 +390,8 @@ static dmpt_status forward_impl(dmpt_handle h, const double* H, const double* H1
 
   if (n_occ == 0 || n_occ == n) {
     cudaError_t e = launch_trivial(n, k, ld, n_occ == n, P, P1, s);
-    if (e == cudaSuccess && order == 2) e = launch_trivial(n, k, ld, 0, nullptr, P2, s);
+    if (e == cudaSuccess && order >= 2)
+      e = launch_trivial(n, (order - 1) * k, ld, 0, nullptr, Pk, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(h, e, "dmpt_sp2_response (trivial)");
     if (info) {
@@ -398,14 +413,14 @@ static dmpt_status forward_impl(dmpt_handle h, const double* H, const double* H1
   State* st = (State*)(base + L.off_state);
   cudaError_t e = cudaMemsetAsync(st, 0, sizeof(State), s);
   if (e != cudaSuccess) return cuda_fail(h, e, "state reset");
-  state_init_kernel<<<1, 1, 0, s>>>(st, order == 2 ? 2 * k : k, o->max_layers, o->precision,
+  state_init_kernel<<<1, 1, 0, s>>>(st, order >= 2 ? order * k : k, o->max_layers, o->precision,
                                     (double)n_occ, o->c_pt, o->c_d0, L.tape_states > 0 ? 1 : 0,
                                     4 * (1 + L.k), L.tape_states, L.k, n, order, k);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "state init");
   if ((e = launch_bounds(H, n, ld, &st->eps1, s)) != cudaSuccess) return cuda_fail(h, e, "bounds");
   const int init_blocks = 1024;
   if ((e = launch_init(L, workspace, H, H1, ld, k, init_blocks, s, 0, nullptr,
-                       order == 2 ? k : 0)) != cudaSuccess)
+                       (order - 1) * k)) != cudaSuccess)
     return cuda_fail(h, e, "init");
   if ((e = launch_decide(L, workspace, kDecideInit, init_blocks, s)) != cudaSuccess)
     return cuda_fail(h, e, "decide(init)");
@@ -445,8 +460,10 @@ static dmpt_status forward_impl(dmpt_handle h, const double* H, const double* H1
   }
   if ((e = launch_finalize(L, workspace, P, P1, ld, k, s)) != cudaSuccess)
     return cuda_fail(h, e, "finalize");
-  if (order == 2 && (e = launch_finalize(L, workspace, nullptr, P2, ld, k, s, k + 1)) != cudaSuccess)
-    return cuda_fail(h, e, "finalize (second order)");
+  for (int od = 2; od <= order; ++od)
+    if ((e = launch_finalize(L, workspace, nullptr, Pk + (size_t)(od - 2) * k * n * ld, ld, k, s,
+                             1 + (od - 1) * k)) != cudaSuccess)
+      return cuda_fail(h, e, "finalize (higher orders)");
 
   State* host_state = new State;
   e = cudaMemcpyAsync(host_state, st, sizeof(State), cudaMemcpyDeviceToHost, s);
@@ -463,7 +480,7 @@ static dmpt_status forward_impl(dmpt_handle h, const double* H, const double* H1
     info->layers = S.layers_run;
     info->d0_layer = S.d0_layer;
     bool all1 = S.d0_conv != 0;
-    const int kj = order == 2 ? 2 * k : k;   // order 2: entries k .. 2k-1 are the S2 terms
+    const int kj = order >= 2 ? order * k : k;   // entries (o - 1) k .. o k - 1: order o
     for (int j = 0; j < kj; ++j) {
       info->d1_layer[j] = S.d1_layer[j];
       all1 = all1 && S.d1_conv[j];
@@ -480,13 +497,11 @@ static dmpt_status forward_impl(dmpt_handle h, const double* H, const double* H1
     double mma = 0.0, alg = 0.0;
     for (int m = 1; m <= S.layers_run; ++m) {
       const bool sq = S.d0_layer == 0 || m <= S.d0_layer;
-      int active = 0, active2 = 0;
-      for (int j = 0; j < kj; ++j) {
-        const int a = (S.d1_conv[j] ? m <= S.d1_layer[j] : true) ? 1 : 0;
-        if (j < k) active += a; else active2 += a;
-      }
-      mma += layer_mma_flops(L, pass_flops, sq, active, active2);
-      alg += layer_alg_flops((double)n, o->precision, sq, active, active2);
+      int active[DMPT_MAX_ORDER + 1] = {0};   // running terms per order
+      for (int j = 0; j < kj; ++j)
+        active[1 + j / (k > 0 ? k : 1)] += (S.d1_conv[j] ? m <= S.d1_layer[j] : true) ? 1 : 0;
+      mma += layer_mma_flops(L, pass_flops, sq, active, order);
+      alg += layer_alg_flops((double)n, o->precision, sq, active, order);
     }
     info->mma_flops = mma;
     info->alg_flops = alg;
@@ -731,19 +746,30 @@ dmpt_status dmpt_sp2_response_host(dmpt_handle h, int count, const double* const
   return status;
 }
 
+dmpt_status dmpt_sp2_response_m(dmpt_handle h, const double* H, const double* H1, int k,
+                                int64_t n, int64_t ld, int64_t n_occ, int order,
+                                const dmpt_options* o, double* P, double* P1, double* Pk,
+                                dmpt_info* info, void* workspace, size_t ws_bytes,
+                                void* stream) {
+  if (!h) return DMPT_EINVAL;
+  h->err[0] = 0;
+  if (info) memset(info, 0, sizeof(*info));
+  if (order < 1 || order > DMPT_MAX_ORDER)
+    return fail(h, DMPT_EINVAL, "dmpt_sp2_response_m: order out of [1, DMPT_MAX_ORDER]%s");
+  dmpt_options opts;
+  dmpt_default_options(&opts);
+  if (o) opts = *o;
+  opts.order = order;
+  return forward_impl(h, H, H1, k, n, ld, n_occ, &opts, P, P1, Pk, info, workspace, ws_bytes,
+                      stream);
+}
+
 dmpt_status dmpt_sp2_response2(dmpt_handle h, const double* H, const double* H1, int k,
                                int64_t n, int64_t ld, int64_t n_occ, const dmpt_options* o,
                                double* P, double* P1, double* P2, dmpt_info* info,
                                void* workspace, size_t ws_bytes, void* stream) {
-  if (!h) return DMPT_EINVAL;
-  h->err[0] = 0;
-  dmpt_options opts;
-  dmpt_default_options(&opts);
-  if (o) opts = *o;
-  opts.order = 2;
-  if (info) memset(info, 0, sizeof(*info));
-  return forward_impl(h, H, H1, k, n, ld, n_occ, &opts, P, P1, P2, info, workspace, ws_bytes,
-                      stream);
+  return dmpt_sp2_response_m(h, H, H1, k, n, ld, n_occ, 2, o, P, P1, P2, info, workspace,
+                             ws_bytes, stream);
 }
 
 dmpt_status dmpt_sp2_backward(dmpt_handle h, const double* G, int64_t n, int64_t ld,
@@ -1067,10 +1093,10 @@ static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
       double alg = 0.0;
       for (int m = 1; m <= S.layers_run; ++m) {
         const bool sq = S.d0_layer == 0 || m <= S.d0_layer;
-        int act = 0;
-        for (int j = 0; j < k; ++j) act += (S.d1_conv[j] ? m <= S.d1_layer[j] : true) ? 1 : 0;
-        alg += layer_alg_flops((double)n[i], o->precision, sq, act);
-        I.mma_flops += layer_mma_flops(L[i], pass_flops[i], sq, act);
+        int act[2] = {0, 0};   // first-order terms only
+        for (int j = 0; j < k; ++j) act[1] += (S.d1_conv[j] ? m <= S.d1_layer[j] : true) ? 1 : 0;
+        alg += layer_alg_flops((double)n[i], o->precision, sq, act, 1);
+        I.mma_flops += layer_mma_flops(L[i], pass_flops[i], sq, act, 1);
       }
       I.alg_flops = alg;
       for (int m = 1; m <= S.layers_run && m <= DMPT_MAX_LAYERS; ++m) I.sigma[m - 1] = S.sigma[m];

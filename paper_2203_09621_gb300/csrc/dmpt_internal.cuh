@@ -58,8 +58,8 @@ struct State {
   int adj_m;            // adjoint: layer whose adjoint runs next
   int rp_lmax;          // replay: last layer whose sigma the forward recorded
   int rp_layers;        // replay: layers run
-  int order;            // 1: first-order response; 2: also the second-order term
-  int k1;               // first-order directions (jobs k1 + 1 .. 2 k1 are order 2)
+  int order;            // highest response order (1: first order only)
+  int k1;               // first-order directions (job 1 + (o - 1) k1 + d: order o)
   unsigned round_ctr;   // pair kernel: rounds started by its CTAs (soft alignment);
                         // every decide step resets it before the next launch
   int64_t n;

@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const d
 #pragma unroll
     for (int j = 0; j < kMaxK; ++j) f1[j] = (double)f1s[j] + (double)f1c[j];
   }
-  // second-order slots start at zero (a linear perturbation has H2 = 0)
+  // higher-order slots start at zero (a linear perturbation: H^(o) = 0, o >= 2)
   for (int m = k + 1; m <= k + k_zero; ++m) {
     T* dst = master + (size_t)m * mat;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)mat;
@@ -394,9 +394,16 @@ __device__ void plan_layer(State* st, int n) {
     st->plan_resp[j] = !st->d1_conv[j];
     // |S1_n|_max <= ||S1_n||_2 <= (2 ||S0||_2 + |1 - sigma|) ||S1_{n-1}||_2
     //            <= 4.5 ||S1_{n-1}||_F   (spectrum of S0 within [-0.25, 1.25]);
-    // second-order slots add ||S1 S1||_2 <= ||S1||_F^2 (twice, for 2 S - S^2)
+    // an order-o slot (o >= 2) adds sum_{a=1}^{o-1} ||S_a S_{o-a}||_2
+    // <= sum ||S_a||_F ||S_{o-a}||_F (twice, for 2 S - S^2)
     double bound = 4.5 * sqrt(st->s1_fro2[j]);
-    if (st->order == 2 && j >= st->k1) bound += 2.0 * st->s1_fro2[j - st->k1];
+    if (st->order >= 2 && j >= st->k1) {
+      const int o = 1 + j / st->k1, d = j % st->k1;
+      double cross = 0.0;
+      for (int a = 1; a < o; ++a)
+        cross += sqrt(st->s1_fro2[(a - 1) * st->k1 + d] * st->s1_fro2[(o - a - 1) * st->k1 + d]);
+      bound += 2.0 * cross;
+    }
     st->s1_exp_next[j] = st->precision == DMPT_DUAL_FP16 ? fp16_exponent_for(bound) : 0;
   }
   st->n_layer = n;

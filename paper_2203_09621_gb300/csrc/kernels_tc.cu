@@ -271,12 +271,20 @@ __device__ __forceinline__ int job_at(uint32_t mask, int idx) {
   return __ffs(m) - 1;
 }
 
-// Jobs of a layer: 0 = square of S0; 1..k1 = first-order response of
-// direction job - 1 (passes S0 S1, S1 S0); k1 + 1 .. 2 k1 (order 2) =
-// second-order term of direction job - 1 - k1 (passes S0 S2, S2 S0, S1 S1).
+// Jobs of a layer: 0 = square of S0; 1 + (o - 1) k1 + d = the order-o term
+// of direction d (o = 1 .. order, d = 0 .. k1 - 1; k1 = first-order
+// directions), whose activation is (Sec. III A, Eq. (S_n detailed))
+//   S0 S_o + S_o S0 + sum_{a=1}^{o-1} S_a S_{o-a}
+// in o + 1 K passes: pass 0 = S0 S_o, pass 1 = S_o S0, pass p >= 2 =
+// S_{p-1} S_{o-p+1} (order 1: S0 S1, S1 S0; order 2 adds S1 S1).
 // The job id is also the matrix slot of the result.
+__device__ __forceinline__ int job_order(int job, int k1) { return 1 + (job - 1) / k1; }
 __device__ __forceinline__ int job_passes(int job, int k1) {
-  return job == 0 ? 1 : (job <= k1 ? 2 : 3);
+  return job == 0 ? 1 : (job <= k1 ? 2 : 1 + job_order(job, k1));
+}
+// slot of the order-a term (a >= 1) of the direction of job `job`
+__device__ __forceinline__ int job_slot(int job, int a, int k1) {
+  return 1 + (a - 1) * k1 + (job - 1) % k1;
 }
 // operand slots (A, B) of pass `pass` of job `job`
 __device__ __forceinline__ void job_operands(int job, int pass, int k1, int* mA, int* mB) {
@@ -290,9 +298,16 @@ __device__ __forceinline__ void job_operands(int job, int pass, int k1, int* mA,
     *mA = job;
     *mB = 0;
   } else {
-    *mA = job - k1;   // S1 of the same direction, times itself
-    *mB = job - k1;
+    *mA = job_slot(job, pass - 1, k1);
+    *mB = job_slot(job, job_order(job, k1) - pass + 1, k1);
   }
+}
+// exact power-of-two unscale of a pass p >= 2 product (operands scaled by
+// 2^e of their slots)
+__device__ __forceinline__ float cross_unscale(const State* st, int job, int pass, int k1) {
+  int mA, mB;
+  job_operands(job, pass, k1, &mA, &mB);
+  return ldexpf(1.0f, -(st->s1_exp_cur[mA - 1] + st->s1_exp_cur[mB - 1]));
 }
 // K-pass of accumulation chunk c (chunks never straddle passes); the
 // producer of the pair kernel runs the passes backwards in odd rounds
@@ -330,7 +345,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   const int write0 = st->plan_write0;
   const int s0e = st->s0_exp;
   const int z0c = st->z0_cur, z0n = st->z0_next;
-  const int k1 = st->order == 2 ? st->k1 : k;   // first-order directions
+  const int k1 = st->order >= 2 ? st->k1 : k;   // first-order directions
 
   const int64_t tiles = num_tiles(Np);
   const int64_t items = tiles * njobs;
@@ -527,13 +542,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const int passes = job_passes(job, k1);
       const int cpp = (kblocks + chunk - 1) / chunk;   // chunks per pass
       const int nchunks = passes * cpp;
-      // exact power-of-two unscale of each pass's products
-      float upass[3];
-      {
-        const int ej = job == 0 ? s0e : st->s1_exp_cur[job - 1];
-        upass[0] = upass[1] = ldexpf(1.0f, -(s0e + ej));
-        upass[2] = job > k1 ? ldexpf(1.0f, -2 * st->s1_exp_cur[job - k1 - 1]) : 0.0f;
-      }
+      // exact power-of-two unscale of the products of passes 0 and 1
+      // (passes >= 2 of higher-order terms: cross_unscale)
+      const float u01 = ldexpf(1.0f, -(s0e + (job == 0 ? s0e : st->s1_exp_cur[job - 1])));
 
       // ---- sum the chunk accumulators in FP32 (round to nearest)
       float sum[128];
@@ -550,7 +561,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         fence_after();
         const uint32_t ta = tmem_base + tlane + (uint32_t)(ab * BN + half * 128);
-        const float u = upass[chunk_pass(ch, cpp, passes, crev)];
+        const int pc = chunk_pass(ch, cpp, passes, crev);
+        const float u = pc < 2 ? u01 : cross_unscale(st, job, pc, k1);
 #pragma unroll
         for (int cc = 0; cc < 8; ++cc) {
           uint32_t x[16];
@@ -1139,7 +1151,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
   const int write0 = st->plan_write0;
   const int s0e = st->s0_exp;
   const int z0c = st->z0_cur, z0n = st->z0_next;
-  const int k1 = st->order == 2 ? st->k1 : k;   // first-order directions
+  const int k1 = st->order >= 2 ? st->k1 : k;   // first-order directions
 
   const uint32_t rank = cluster_rank();
   const bool leader = rank == 0;
@@ -1257,13 +1269,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
       const int passes = job_passes(job, k1);
       const int cpp = (kblocks + chunk - 1) / chunk;   // chunks per pass
       const int nchunks = passes * cpp;
-      // exact power-of-two unscale of each pass's products
-      float upass[3];
-      {
-        const int ej = job == 0 ? s0e : st->s1_exp_cur[job - 1];
-        upass[0] = upass[1] = ldexpf(1.0f, -(s0e + ej));
-        upass[2] = job > k1 ? ldexpf(1.0f, -2 * st->s1_exp_cur[job - k1 - 1]) : 0.0f;
-      }
+      // exact power-of-two unscale of the products of passes 0 and 1
+      // (passes >= 2 of higher-order terms: cross_unscale)
+      const float u01 = ldexpf(1.0f, -(s0e + (job == 0 ? s0e : st->s1_exp_cur[job - 1])));
       float sum[128];
 #pragma unroll
       for (int i = 0; i < 128; ++i) sum[i] = 0.0f;
@@ -1276,7 +1284,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
         }
         fence_after();
         const uint32_t ta = tmem_base + tlane + (uint32_t)(ab * BN + half * 128);
-        const float u = upass[chunk_pass(ch, cpp, passes, crev)];
+        const int pc = chunk_pass(ch, cpp, passes, crev);
+        const float u = pc < 2 ? u01 : cross_unscale(st, job, pc, k1);
 #pragma unroll
         for (int cc = 0; cc < 8; ++cc) {
           uint32_t x[16];

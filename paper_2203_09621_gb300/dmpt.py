@@ -102,6 +102,10 @@ def load_library(path: str = LIB_PATH):
                                        ctypes.POINTER(DmptOptions), vp, vp, vp,
                                        ctypes.POINTER(DmptInfo), vp, ctypes.c_size_t, vp]
     lib.dmpt_sp2_response2.restype = c_int
+    lib.dmpt_sp2_response_m.argtypes = [vp, vp, vp, c_int, i64, i64, i64, c_int,
+                                        ctypes.POINTER(DmptOptions), vp, vp, vp,
+                                        ctypes.POINTER(DmptInfo), vp, ctypes.c_size_t, vp]
+    lib.dmpt_sp2_response_m.restype = c_int
     lib.dmpt_sp2_backward.argtypes = [vp, vp, i64, i64, ctypes.POINTER(DmptOptions), vp, vp,
                                       ctypes.c_size_t, vp]
     lib.dmpt_sp2_backward.restype = c_int
@@ -372,6 +376,38 @@ class Context:
         if st != 0 and raise_on_error:
             self._check(st)
         return P, P1, P2, Info.from_c(info, 2 * k)
+
+    def sp2_response_m(self, H, H1, n_occ, order, precision="dual_fp16", stream=None,
+                       raise_on_error=True, **kw):
+        """Responses of orders 1 .. order: P_o = (1/o!) d^o P / dlambda^o.
+        Returns (P, [P_1, ..., P_order] each (k, n, n), Info); Info.d1_layer
+        entries (o - 1) k .. o k - 1 are order o's stop layers."""
+        import torch
+        H = H.contiguous()
+        if H1.dim() == 2:
+            H1 = H1.unsqueeze(0)
+        H1 = H1.contiguous()
+        k, n = H1.shape[0], H.shape[0]
+        opts = options(precision=precision, order=order, **kw)
+        P = torch.empty_like(H)
+        P1 = torch.empty_like(H1)
+        Pk = torch.empty((max(order - 1, 0) * k, n, n), dtype=H.dtype, device=H.device)
+        nbytes = self.workspace_size(n, k, opts)
+        if nbytes == 0:
+            raise DmptError(1, "invalid sizes or options")
+        ws_ptr, ws_len = self.workspace(nbytes)
+        info = DmptInfo()
+        s = stream if stream is not None else torch.cuda.current_stream(H.device)
+        st = self.lib.dmpt_sp2_response_m(self.h, H.data_ptr(), H1.data_ptr(), k, n, n,
+                                          int(n_occ), int(order), ctypes.byref(opts),
+                                          P.data_ptr(), P1.data_ptr(),
+                                          Pk.data_ptr() if order >= 2 else None,
+                                          ctypes.byref(info), ctypes.c_void_p(ws_ptr), ws_len,
+                                          ctypes.c_void_p(s.cuda_stream))
+        if st != 0 and raise_on_error:
+            self._check(st)
+        terms = [P1] + [Pk[(o - 2) * k:(o - 1) * k] for o in range(2, order + 1)]
+        return P, terms, Info.from_c(info, order * k)
 
     def sp2_backward(self, G, workspace, out=None, stream=None, **kw):
         """dL/dH of L = Tr[G P] for the forward run that filled `workspace`
