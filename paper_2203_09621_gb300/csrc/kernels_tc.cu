@@ -64,8 +64,14 @@ constexpr int EPI_WARPS = 8;     // two per TMEM lane quadrant (column halves)
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int EPI_WARP0 = 2;     // epilogue = warps 2 .. 9
 constexpr int NUM_THREADS = 64 + EPI_THREADS;
+// Epilogue scratch: a 2560-byte transpose buffer per epilogue warp (32 rows
+// of 20 words); it shares its space with the reduction array of the tile's
+// partial sums (EPI_THREADS x 4 doubles), which is used only after every
+// epilogue warp has left its tile epilogue.
+constexpr int EPI_SCRATCH = EPI_WARPS * 32 * 20 * 4;
+static_assert(EPI_SCRATCH >= EPI_THREADS * 4 * 8, "reduction array fits the scratch");
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* align */ + 1024 /* barriers etc */ +
-                           EPI_THREADS * 4 * 8;
+                           EPI_SCRATCH;
 constexpr int DEFAULT_CHUNK_K = 256;  // K elements per tensor-memory accumulation chunk
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
@@ -323,6 +329,162 @@ __device__ __forceinline__ int zop(int m, int buf, int part, int k, int z0) {
   return m == 0 ? z0 + part : zslice(buf, m, part, k);
 }
 
+// Bit pattern of a 16-bit float (FP16 or BF16).
+template <class H16>
+__device__ __forceinline__ uint32_t h16_bits(H16 x) {
+  return (uint32_t)(*reinterpret_cast<const uint16_t*>(&x));
+}
+
+// Rolled tile epilogue of one thread: its row r, columns c0 .. c0 + 127 of a
+// pair tile, whose sums the caller has written to tensor memory at ta_sum.
+// Forms S_new = sigma X + (1 - sigma) S_old (Eq. (eq:Sn) / Eq. (dB)), its
+// FP16/BF16 hi/lo split (Sec. II C), the partial sums (||S_new||_F^2 with
+// TwoSum compensation, ||S_old - X||_F^2, trace, non-finite count) and stores
+// each owned element (column >= row) at (r, c) and (c, r).  OFF: the tile is
+// off the diagonal (every column > every row).
+//
+// Memory access pattern.  A warp holds 32 consecutive rows (one per lane)
+// and the same columns, so an access down a column (lane = row) is one
+// contiguous segment while an access along its rows touches 32 lines.
+//  * S_old is read down the columns: the masters are exactly symmetric
+//    (both halves are written with the same value), so S_old[r][c] is read
+//    at (c, r), 16 columns per batch of loads; the next batch is loaded
+//    while the current one is stored.
+//  * The mirror (c, r) is stored down the columns directly.
+//  * The row-direction stores (r, c) go through this warp's transpose
+//    buffer `xp` in shared memory (32 rows of XP_STRIDE words; 16 columns at
+//    a time): each lane writes its row, then the warp stores 4 rows x 64 B
+//    (FP32) or 4 rows x 32 B (hi, lo) per instruction.  The row stride of
+//    20 words keeps both the 16-byte row writes and the column-pair reads
+//    free of bank conflicts.
+// The sums run over the columns in ascending order, so every thread's
+// partial sums do not depend on the memory access pattern.
+constexpr int XP_STRIDE = 20;                       // words per buffer row
+constexpr int XP_WARP_BYTES = 32 * XP_STRIDE * 4;   // 2560 B per epilogue warp
+static_assert(EPI_WARPS * XP_WARP_BYTES == EPI_SCRATCH, "transpose buffers");
+template <class CV, bool OFF>
+__device__ __forceinline__ void rolled_tile_epilogue(
+    const uint32_t ta_sum, const float* __restrict__ Sold, float* Snew, typename CV::T* hi_new,
+    typename CV::T* lo_new, uint32_t* xp, const int lane, const int64_t Np, const int r,
+    const int c0, const float sg, const float om, const float scale_new, const bool write,
+    float& fn_s, float& fn_c, float& fd, float& trf, int& bad) {
+  const int r0 = r - lane;   // row of lane 0
+  const int np = (int)Np;
+  // element (c, r) of the tile's columns at col_base + (c - c0) * np; element
+  // (r0 + i, c) at row_base + i * np + (c - c0)  (32-bit offsets)
+  const size_t col_base = (size_t)c0 * Np + r;
+  const size_t row_base = (size_t)r0 * Np + c0;
+  const float* Sc = Sold + col_base;
+  float* Snc = Snew + col_base;
+  uint16_t* hic = reinterpret_cast<uint16_t*>(hi_new) + col_base;
+  uint16_t* loc = reinterpret_cast<uint16_t*>(lo_new) + col_base;
+  float* Snr = Snew + row_base;
+  uint16_t* hir = reinterpret_cast<uint16_t*>(hi_new) + row_base;
+  uint16_t* lor = reinterpret_cast<uint16_t*>(lo_new) + row_base;
+  float olds[16];   // S_old of the current 16 columns; the next 16 are loaded
+                    // while the current ones are stored
+#pragma unroll
+  for (int q = 0; q < 16; ++q) olds[q] = __ldg(Sc + q * np);
+#pragma unroll 1
+  for (int g16 = 0; g16 < 8; ++g16) {
+    uint32_t xs[16];
+    tmem_ld16(ta_sum + 16 * g16, xs);
+    const int cb16 = c0 + 16 * g16;
+    // FP32 values go to the transpose buffer as each group of 4 is formed;
+    // the hi/lo bits stay in registers, packed in column pairs, until the
+    // FP32 rows have been stored
+    float4* xr = reinterpret_cast<float4*>(xp + lane * XP_STRIDE);
+    uint32_t hp[8], lp[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) hp[i] = lp[i] = 0u;
+#pragma unroll
+    for (int gg = 0; gg < 4; ++gg) {
+      const int cb = cb16 + 4 * gg;
+      if (!OFF && r > cb + 3) continue;
+      float nw[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int e = 4 * gg + i;
+        const float xv = __uint_as_float(xs[e]);
+        const int c = cb + i;
+        const bool own = OFF || c >= r;
+        const float w = (!OFF && c == r) ? 1.0f : 2.0f;
+        bad += (own && !isfinite(xv)) ? 1 : 0;
+        const float old = olds[e];
+        const float dd = old - xv;
+        fd = own ? fmaf(w * dd, dd, fd) : fd;
+        const float n1 = sg * xv + om * old;
+        nw[i] = n1;
+        if (own && write) {
+          const float p = w * n1 * n1;
+          const float ee = w * fmaf(n1, n1, -n1 * n1);
+          const float tt = fn_s + p;
+          const float bp = tt - fn_s;
+          fn_c += (fn_s - (tt - bp)) + (p - bp) + ee;
+          fn_s = tt;
+          if (!OFF && c == r) trf += n1;
+        }
+        const float y = n1 * scale_new;
+        const typename CV::T h = CV::to(y);
+        const uint32_t hbits = h16_bits(h);
+        const uint32_t lbits = h16_bits(CV::to(y - CV::from(h)));
+        hp[e >> 1] |= hbits << (16 * (e & 1));
+        lp[e >> 1] |= lbits << (16 * (e & 1));
+        if (write && (OFF || c > r)) {   // mirror (c, r), down the column
+          const int m = (c - c0) * np;
+          Snc[m] = n1;
+          hic[m] = (uint16_t)hbits;
+          loc[m] = (uint16_t)lbits;
+        }
+      }
+      xr[gg] = make_float4(nw[0], nw[1], nw[2], nw[3]);
+    }
+    if (g16 < 7) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) olds[q] = __ldg(Sc + (16 * (g16 + 1) + q) * np);
+    }
+    if (!write) continue;
+    // ---- row direction (r, c) through the transpose buffer
+    __syncwarp();
+#pragma unroll
+    for (int sidx = 0; sidx < 8; ++sidx) {
+      const int i = (sidx & 3) + 16 * (sidx >> 2) + 4 * (lane >> 3);   // rows i, +4, +8, +12
+      const int w2 = 2 * (lane & 7);
+      const float2 v = *reinterpret_cast<const float2*>(xp + i * XP_STRIDE + w2);
+      const int rr = r0 + i, c = cb16 + w2;
+      float* dst = Snr + i * np + (c - c0);
+      if (OFF || c >= rr)
+        *reinterpret_cast<float2*>(dst) = v;
+      else if (c + 1 >= rr)
+        dst[1] = v.y;
+    }
+    __syncwarp();
+    uint4* xr4 = reinterpret_cast<uint4*>(xp + lane * XP_STRIDE);
+    xr4[0] = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+    xr4[1] = make_uint4(hp[4], hp[5], hp[6], hp[7]);
+    xr4[2] = make_uint4(lp[0], lp[1], lp[2], lp[3]);
+    xr4[3] = make_uint4(lp[4], lp[5], lp[6], lp[7]);
+    __syncwarp();
+#pragma unroll
+    for (int sidx = 0; sidx < 8; ++sidx) {
+      const int i = 8 * (sidx >> 1) + (sidx & 1) + 2 * (lane >> 3);   // rows i, +2, +4, +6
+      const int m = lane & 7;                                           // column pair
+      const uint32_t vh = xp[i * XP_STRIDE + m];
+      const uint32_t vl = xp[i * XP_STRIDE + 8 + m];
+      const int rr = r0 + i, c = cb16 + 2 * m;
+      const int o = i * np + (c - c0);
+      if (OFF || c >= rr) {
+        *reinterpret_cast<uint32_t*>(hir + o) = vh;
+        *reinterpret_cast<uint32_t*>(lor + o) = vl;
+      } else if (c + 1 >= rr) {
+        hir[o + 1] = (uint16_t)(vh >> 16);
+        lor[o + 1] = (uint16_t)(vl >> 16);
+      }
+    }
+    __syncwarp();
+  }
+}
+
 template <bool BF16>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     layer_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
@@ -570,6 +732,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
           for (int i = 0; i < 16; ++i) sum[16 * cc + i] = fmaf(__uint_as_float(x[i]), u, sum[16 * cc + i]);
         }
+        if (ch + 1 == nchunks) break;   // keep the last chunk's buffer
         fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(bar_tempty + 8 * ab);
@@ -579,6 +742,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
       }
       if (!alive) break;
+      // the tile's sums go back into its last chunk's buffer
+      const uint32_t ta_sum = tmem_base + tlane + (uint32_t)(ab * BN + half * 128);
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc) tmem_st16(ta_sum + 16 * cc, sum + 16 * cc);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 
       // ---- fused layer update, split and stores
       const int64_t t = it % tiles;
@@ -591,8 +759,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const bool write = job != 0 || write0;
       const int r = I * BM + rloc;
       const int c0 = J * BN + half * 128;
-      const size_t row_off = (size_t)r * Np;
-      const float* Sold = master + (size_t)(curj * (1 + k) + job) * mat + row_off;
+      const float* Sold = master + (size_t)(curj * (1 + k) + job) * mat;
       float* Snew = master + (size_t)((curj ^ 1) * (1 + k) + job) * mat;
       const int zh_new = job == 0 ? z0n : zslice(curj ^ 1, job, 0, k);
       H16* hi_new = reinterpret_cast<H16*>(ops) + (size_t)zh_new * mat;
@@ -604,75 +771,22 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       // FroErr sums only enter ratio tests and use plain FP32.
       float fn_s = 0.0f, fn_c = 0.0f, fd = 0.0f, trf = 0.0f;
       int bad = 0;
-#pragma unroll
-      for (int g = 0; g < 32; ++g) {   // groups of 4 columns
-        const int cb = c0 + 4 * g;
-        if (r > cb + 3) continue;      // no element with r <= c in this group
-        const float4 o4 = *reinterpret_cast<const float4*>(Sold + cb);
-        const float old[4] = {o4.x, o4.y, o4.z, o4.w};
-        float nw[4];
-        H16 nh[4], nl[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const float xv = sum[4 * g + i];
-          const int c = cb + i;
-          const bool own = c >= r;
-          const float w = (c == r) ? 1.0f : 2.0f;
-          bad += (own && !isfinite(xv)) ? 1 : 0;
-          const float dd = old[i] - xv;
-          fd = own ? fmaf(w * dd, dd, fd) : fd;
-          const float n1 = sg * xv + om * old[i];
-          nw[i] = n1;
-          if (own && write) {
-            const float p = w * n1 * n1;                // w in {1, 2}: exact scaling
-            const float e = w * fmaf(n1, n1, -n1 * n1);  // exact product error
-            const float t = fn_s + p;                    // TwoSum(fn_s, p)
-            const float bp = t - fn_s;
-            fn_c += (fn_s - (t - bp)) + (p - bp) + e;
-            fn_s = t;
-            if (c == r) trf += n1;                       // at most one per thread
-          }
-          const float y = n1 * scale_new;
-          nh[i] = CV::to(y);
-          nl[i] = CV::to(y - CV::from(nh[i]));
-        }
-        if (!write) continue;
-        if (r <= cb) {
-          // whole group owned: vector stores at (r, cb .. cb+3)
-          *reinterpret_cast<float4*>(Snew + row_off + cb) = make_float4(nw[0], nw[1], nw[2], nw[3]);
-          uint2 ph, pl2;
-          ph.x = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[0])) |
-                 ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[1])) << 16);
-          ph.y = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[2])) |
-                 ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nh[3])) << 16);
-          pl2.x = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[0])) |
-                  ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[1])) << 16);
-          pl2.y = (uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[2])) |
-                  ((uint32_t)__half_as_ushort(*reinterpret_cast<__half*>(&nl[3])) << 16);
-          *reinterpret_cast<uint2*>(hi_new + row_off + cb) = ph;
-          *reinterpret_cast<uint2*>(lo_new + row_off + cb) = pl2;
-        } else {
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            if (cb + i >= r) {
-              Snew[row_off + cb + i] = nw[i];
-              hi_new[row_off + cb + i] = nh[i];
-              lo_new[row_off + cb + i] = nl[i];
-            }
-          }
-        }
-        // mirrored stores at (c, r): for fixed c the warp's 32 rows are contiguous
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int c = cb + i;
-          if (c > r) {
-            const size_t m = (size_t)c * Np + r;
-            Snew[m] = nw[i];
-            hi_new[m] = nh[i];
-            lo_new[m] = nl[i];
-          }
-        }
+      uint32_t* xp = reinterpret_cast<uint32_t*>(misc + 1024) +
+                     (warp - EPI_WARP0) * (XP_WARP_BYTES / 4);
+      if (I * BM + BM - 1 < J * BN)   // every column of the tile above every row
+        rolled_tile_epilogue<CV, true>(ta_sum, Sold, Snew, hi_new, lo_new, xp, lane, Np, r, c0,
+                                       sg, om, scale_new, write, fn_s, fn_c, fd, trf, bad);
+      else
+        rolled_tile_epilogue<CV, false>(ta_sum, Sold, Snew, hi_new, lo_new, xp, lane, Np, r, c0,
+                                        sg, om, scale_new, write, fn_s, fn_c, fd, trf, bad);
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar_tempty + 8 * ab);
+      if (++ab == 2) {
+        ab = 0;
+        abphase ^= 1;
       }
+      epi_sync();   // the reduction array overlays the transpose buffers
       // deterministic tile reduction over the 256 epilogue threads (FP64)
       red[0 * EPI_THREADS + et] = (double)trf;
       red[1 * EPI_THREADS + et] = (double)fn_s + (double)fn_c;
@@ -723,13 +837,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
 constexpr int P_STAGES = 6;
 constexpr int P_STAGE_BYTES = 2 * A_BYTES + 2 * A_BYTES;   // A hi/lo + B-half hi/lo: 32 KB
-// Epilogue scratch: a 2560-byte transpose buffer per epilogue warp (32 rows
-// of 20 words); it shares its space with the reduction array of the tile's
-// partial sums, which is used only after every epilogue warp has left its
-// tile epilogue.
-constexpr int P_SCRATCH = EPI_WARPS * 32 * 20 * 4;
-static_assert(P_SCRATCH >= EPI_THREADS * 4 * 8, "reduction array fits the scratch");
-constexpr int P_SMEM_BYTES = P_STAGES * P_STAGE_BYTES + 1024 + 1024 + P_SCRATCH;
+constexpr int P_SMEM_BYTES = P_STAGES * P_STAGE_BYTES + 1024 + 1024 + EPI_SCRATCH;
 
 __host__ __device__ inline int64_t num_pair_tiles(int64_t Np) {
   const int64_t tj = Np / BN;
@@ -938,162 +1046,6 @@ __device__ __forceinline__ bool mma_item(RingPos& rg, RingPos& tb, int nst, int 
     }
   }
   return true;
-}
-
-// Bit pattern of a 16-bit float (FP16 or BF16).
-template <class H16>
-__device__ __forceinline__ uint32_t h16_bits(H16 x) {
-  return (uint32_t)(*reinterpret_cast<const uint16_t*>(&x));
-}
-
-// Rolled tile epilogue of one thread: its row r, columns c0 .. c0 + 127 of a
-// pair tile, whose sums the caller has written to tensor memory at ta_sum.
-// Forms S_new = sigma X + (1 - sigma) S_old (Eq. (eq:Sn) / Eq. (dB)), its
-// FP16/BF16 hi/lo split (Sec. II C), the partial sums (||S_new||_F^2 with
-// TwoSum compensation, ||S_old - X||_F^2, trace, non-finite count) and stores
-// each owned element (column >= row) at (r, c) and (c, r).  OFF: the tile is
-// off the diagonal (every column > every row).
-//
-// Memory access pattern.  A warp holds 32 consecutive rows (one per lane)
-// and the same columns, so an access down a column (lane = row) is one
-// contiguous segment while an access along its rows touches 32 lines.
-//  * S_old is read down the columns: the masters are exactly symmetric
-//    (both halves are written with the same value), so S_old[r][c] is read
-//    at (c, r), 16 columns per batch of loads; the next batch is loaded
-//    while the current one is stored.
-//  * The mirror (c, r) is stored down the columns directly.
-//  * The row-direction stores (r, c) go through this warp's transpose
-//    buffer `xp` in shared memory (32 rows of XP_STRIDE words; 16 columns at
-//    a time): each lane writes its row, then the warp stores 4 rows x 64 B
-//    (FP32) or 4 rows x 32 B (hi, lo) per instruction.  The row stride of
-//    20 words keeps both the 16-byte row writes and the column-pair reads
-//    free of bank conflicts.
-// The sums run over the columns in ascending order, so every thread's
-// partial sums do not depend on the memory access pattern.
-constexpr int XP_STRIDE = 20;                       // words per buffer row
-constexpr int XP_WARP_BYTES = 32 * XP_STRIDE * 4;   // 2560 B per epilogue warp
-static_assert(EPI_WARPS * XP_WARP_BYTES == P_SCRATCH, "transpose buffers");
-template <class CV, bool OFF>
-__device__ __forceinline__ void rolled_tile_epilogue(
-    const uint32_t ta_sum, const float* __restrict__ Sold, float* Snew, typename CV::T* hi_new,
-    typename CV::T* lo_new, uint32_t* xp, const int lane, const int64_t Np, const int r,
-    const int c0, const float sg, const float om, const float scale_new, const bool write,
-    float& fn_s, float& fn_c, float& fd, float& trf, int& bad) {
-  const int r0 = r - lane;   // row of lane 0
-  const int np = (int)Np;
-  // element (c, r) of the tile's columns at col_base + (c - c0) * np; element
-  // (r0 + i, c) at row_base + i * np + (c - c0)  (32-bit offsets)
-  const size_t col_base = (size_t)c0 * Np + r;
-  const size_t row_base = (size_t)r0 * Np + c0;
-  const float* Sc = Sold + col_base;
-  float* Snc = Snew + col_base;
-  uint16_t* hic = reinterpret_cast<uint16_t*>(hi_new) + col_base;
-  uint16_t* loc = reinterpret_cast<uint16_t*>(lo_new) + col_base;
-  float* Snr = Snew + row_base;
-  uint16_t* hir = reinterpret_cast<uint16_t*>(hi_new) + row_base;
-  uint16_t* lor = reinterpret_cast<uint16_t*>(lo_new) + row_base;
-  float olds[16];   // S_old of the current 16 columns; the next 16 are loaded
-                    // while the current ones are stored
-#pragma unroll
-  for (int q = 0; q < 16; ++q) olds[q] = __ldg(Sc + q * np);
-#pragma unroll 1
-  for (int g16 = 0; g16 < 8; ++g16) {
-    uint32_t xs[16];
-    tmem_ld16(ta_sum + 16 * g16, xs);
-    const int cb16 = c0 + 16 * g16;
-    // FP32 values go to the transpose buffer as each group of 4 is formed;
-    // the hi/lo bits stay in registers, packed in column pairs, until the
-    // FP32 rows have been stored
-    float4* xr = reinterpret_cast<float4*>(xp + lane * XP_STRIDE);
-    uint32_t hp[8], lp[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) hp[i] = lp[i] = 0u;
-#pragma unroll
-    for (int gg = 0; gg < 4; ++gg) {
-      const int cb = cb16 + 4 * gg;
-      if (!OFF && r > cb + 3) continue;
-      float nw[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int e = 4 * gg + i;
-        const float xv = __uint_as_float(xs[e]);
-        const int c = cb + i;
-        const bool own = OFF || c >= r;
-        const float w = (!OFF && c == r) ? 1.0f : 2.0f;
-        bad += (own && !isfinite(xv)) ? 1 : 0;
-        const float old = olds[e];
-        const float dd = old - xv;
-        fd = own ? fmaf(w * dd, dd, fd) : fd;
-        const float n1 = sg * xv + om * old;
-        nw[i] = n1;
-        if (own && write) {
-          const float p = w * n1 * n1;
-          const float ee = w * fmaf(n1, n1, -n1 * n1);
-          const float tt = fn_s + p;
-          const float bp = tt - fn_s;
-          fn_c += (fn_s - (tt - bp)) + (p - bp) + ee;
-          fn_s = tt;
-          if (!OFF && c == r) trf += n1;
-        }
-        const float y = n1 * scale_new;
-        const typename CV::T h = CV::to(y);
-        const uint32_t hbits = h16_bits(h);
-        const uint32_t lbits = h16_bits(CV::to(y - CV::from(h)));
-        hp[e >> 1] |= hbits << (16 * (e & 1));
-        lp[e >> 1] |= lbits << (16 * (e & 1));
-        if (write && (OFF || c > r)) {   // mirror (c, r), down the column
-          const int m = (c - c0) * np;
-          Snc[m] = n1;
-          hic[m] = (uint16_t)hbits;
-          loc[m] = (uint16_t)lbits;
-        }
-      }
-      xr[gg] = make_float4(nw[0], nw[1], nw[2], nw[3]);
-    }
-    if (g16 < 7) {
-#pragma unroll
-      for (int q = 0; q < 16; ++q) olds[q] = __ldg(Sc + (16 * (g16 + 1) + q) * np);
-    }
-    if (!write) continue;
-    // ---- row direction (r, c) through the transpose buffer
-    __syncwarp();
-#pragma unroll
-    for (int sidx = 0; sidx < 8; ++sidx) {
-      const int i = (sidx & 3) + 16 * (sidx >> 2) + 4 * (lane >> 3);   // rows i, +4, +8, +12
-      const int w2 = 2 * (lane & 7);
-      const float2 v = *reinterpret_cast<const float2*>(xp + i * XP_STRIDE + w2);
-      const int rr = r0 + i, c = cb16 + w2;
-      float* dst = Snr + i * np + (c - c0);
-      if (OFF || c >= rr)
-        *reinterpret_cast<float2*>(dst) = v;
-      else if (c + 1 >= rr)
-        dst[1] = v.y;
-    }
-    __syncwarp();
-    uint4* xr4 = reinterpret_cast<uint4*>(xp + lane * XP_STRIDE);
-    xr4[0] = make_uint4(hp[0], hp[1], hp[2], hp[3]);
-    xr4[1] = make_uint4(hp[4], hp[5], hp[6], hp[7]);
-    xr4[2] = make_uint4(lp[0], lp[1], lp[2], lp[3]);
-    xr4[3] = make_uint4(lp[4], lp[5], lp[6], lp[7]);
-    __syncwarp();
-#pragma unroll
-    for (int sidx = 0; sidx < 8; ++sidx) {
-      const int i = 8 * (sidx >> 1) + (sidx & 1) + 2 * (lane >> 3);   // rows i, +2, +4, +6
-      const int m = lane & 7;                                           // column pair
-      const uint32_t vh = xp[i * XP_STRIDE + m];
-      const uint32_t vl = xp[i * XP_STRIDE + 8 + m];
-      const int rr = r0 + i, c = cb16 + 2 * m;
-      const int o = i * np + (c - c0);
-      if (OFF || c >= rr) {
-        *reinterpret_cast<uint32_t*>(hir + o) = vh;
-        *reinterpret_cast<uint32_t*>(lor + o) = vl;
-      } else if (c + 1 >= rr) {
-        hir[o + 1] = (uint16_t)(vh >> 16);
-        lor[o + 1] = (uint16_t)(vl >> 16);
-      }
-    }
-    __syncwarp();
-  }
 }
 
 // Soft round alignment of the pair kernel's producers.  Items go to the
@@ -1448,7 +1400,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
   uint8_t* gbase = smem_raw + (base - raw);
   const uint32_t ring = base;
   uint8_t* misc = gbase + P_STAGES * P_STAGE_BYTES;
-  int64_t* first = reinterpret_cast<int64_t*>(misc + 1024 + P_SCRATCH);
+  int64_t* first = reinterpret_cast<int64_t*>(misc + 1024 + EPI_SCRATCH);
   uint32_t* jmask = reinterpret_cast<uint32_t*>(first + count + 1);
 
   // ---- this layer's items of every instance (same values in every CTA:
@@ -1580,12 +1532,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
       const int cpp = (itm.kblocks + chunk - 1) / chunk;   // chunks per pass
       const int nchunks = passes * cpp;
       const int s0e = sti->s0_exp;
-      float upass[3];
-      {
-        const int ej = job == 0 ? s0e : sti->s1_exp_cur[job - 1];
-        upass[0] = upass[1] = ldexpf(1.0f, -(s0e + ej));
-        upass[2] = 0.0f;   // first-order jobs only
-      }
+      // exact power-of-two unscale of the products (first-order jobs and the
+      // square: passes 0 and 1 only)
+      const float u = ldexpf(1.0f, -(s0e + (job == 0 ? s0e : sti->s1_exp_cur[job - 1])));
       float sum[128];
 #pragma unroll
       for (int i = 0; i < 128; ++i) sum[i] = 0.0f;
@@ -1598,7 +1547,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
         }
         fence_after();
         const uint32_t ta = tmem_base + tlane + (uint32_t)(ab * BN + half * 128);
-        const float u = upass[chunk_pass(ch, cpp, passes, itm.rev)];
 #pragma unroll
         for (int cc = 0; cc < 8; ++cc) {
           uint32_t x[16];
