@@ -58,6 +58,20 @@ def test_order_m_matches_oracle(ctx, precision, cfg, n, k, order):
 
 
 @pytest.mark.parametrize("precision", ["dual_fp16", "dual_bf16"])
+def test_order_m_one_cta_tiles(ctx, precision):
+    """The 1-CTA kernel (128 x 256 tiles) runs the same order-o jobs."""
+    inst = make_workload(2, n=300, k=2)
+    H = torch.from_numpy(inst.H).to(DEV)
+    H1 = torch.from_numpy(inst.H1).to(DEV)
+    P, terms, info = ctx.sp2_response_m(H, H1, inst.n_occ, 3, precision=precision, cta_pair=0)
+    torch.cuda.synchronize()
+    assert info.converged
+    ref = oracle.sp2_pt(inst.H, inst.H1, inst.n_occ, order=3)
+    errs = [[rel(terms[o][j].cpu().numpy(), ref.Pk[o][j]) for j in range(2)] for o in range(3)]
+    assert max(max(e) for e in errs) < TOL[precision], errs
+
+
+@pytest.mark.parametrize("precision", ["dual_fp16", "dual_bf16"])
 def test_lower_orders_bitwise(ctx, precision):
     inst = make_workload(3, n=384, k=2)
     H = torch.from_numpy(inst.H).to(DEV)

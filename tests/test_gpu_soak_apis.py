@@ -6,7 +6,13 @@
 * the host-buffer pipeline (dmpt_sp2_response_host): random instance
   counts and sizes; bit-exact against the device calls;
 * the second-order response (dmpt_sp2_response2): random sizes and
-  occupations against the oracle's second-order formula.
+  occupations against the oracle's second-order formula;
+* responses of orders 3-5 (dmpt_sp2_response_m): random sizes, occupations,
+  k, precision and tile shape (CTA pair or 1 CTA) against the oracle's SP2
+  recursion of the same order.  An order-o term is formed from the products
+  S_a S_{o-a}, so its rounding scales with sum_a ||P_a|| ||P_{o-a}||, which
+  can exceed ||P_o|| (cancellation); the tolerance is relative to the larger
+  of the two.
 """
 
 import numpy as np
@@ -105,3 +111,27 @@ def test_soak_second_order(ctx, trial):
     for j in range(k):
         want = response2_sos(x.H, x.H1[j], x.n_occ)
         assert rel(P2[j].cpu().numpy(), want) < tol2, (j, rel(P2[j].cpu().numpy(), want))
+
+
+@pytest.mark.parametrize("trial", range(4))
+def test_soak_any_order(ctx, trial):
+    rng = np.random.default_rng(34000 + trial)
+    order = int(rng.integers(3, 6))
+    k = int(rng.integers(1, 8 // order + 1))
+    precision = str(rng.choice(["dual_fp16", "dual_bf16"]))
+    cta_pair = int(rng.integers(0, 2))
+    x = random_instance(rng, f"om_{trial}", 40, 400, k, trivial_ok=False)
+    H = torch.from_numpy(x.H).to(DEV)
+    H1 = torch.from_numpy(x.H1[:k]).to(DEV)
+    P, terms, info = ctx.sp2_response_m(H, H1, x.n_occ, order, precision=precision,
+                                        cta_pair=cta_pair)
+    torch.cuda.synchronize()
+    assert info.converged
+    ref = oracle.sp2_pt(x.H, x.H1[:k], x.n_occ, order=order)
+    for j in range(k):
+        Pj = [ref.P] + [ref.Pk[o][j] for o in range(order)]
+        for o in range(1, order + 1):
+            scale = max(np.linalg.norm(Pj[o]),
+                        sum(np.linalg.norm(Pj[a]) * np.linalg.norm(Pj[o - a]) for a in range(1, o)))
+            err = np.linalg.norm(terms[o - 1][j].cpu().numpy() - Pj[o]) / scale
+            assert err < TOL[precision], (order, k, cta_pair, j, o, err)
