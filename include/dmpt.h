@@ -111,6 +111,12 @@ typedef struct {
                            with the call's own inputs; in a batch, choose the
                            grouped or per-instance path the same way.  0
                            (default) = use the fields as given              */
+  int round_align;      /* CTA-pair form: 1 (default) = the CTAs' operand
+                           loads keep their scheduling rounds in step (a
+                           bounded wait of at most 300 us, never an error), so
+                           the tiles of a round share their operand panels in
+                           L2; 0 = off, for several solves running at once on
+                           one GPU (their CTAs need not all be resident)      */
 } dmpt_options;
 
 /* Filled on the host by dmpt_sp2_response (when info != NULL). */

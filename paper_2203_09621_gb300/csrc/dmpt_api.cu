@@ -85,6 +85,7 @@ bool valid_options(const dmpt_options* o) {
   if (o->tile_band < 0 || o->tile_band > 1024) return false;
   if (o->inject_stall < 0 || o->inject_stall > 1) return false;
   if (o->autotune < 0 || o->autotune > 1) return false;
+  if (o->round_align < 0 || o->round_align > 1) return false;
   return true;
 }
 
@@ -181,7 +182,8 @@ dmpt_status replay_run(dmpt_handle h, const Layout& L, const double* H1, const d
   while (launched < o->max_layers && !done) {
     for (int j = 0; j < o->sync_every && launched < o->max_layers; ++j) {
       if ((e = launch_layer_tc(L, workspace, s, o->timeout_s, o->accum_chunk, o->cta_pair,
-                               o->k_snake, o->tile_band, &entries, &pass_flops)) != cudaSuccess)
+                               o->k_snake, o->tile_band, &entries, &pass_flops, 0,
+                               o->round_align)) != cudaSuccess)
         return cuda_fail(h, e, "replay layer");
       if ((e = launch_decide(L, workspace, kDecideReplayLayer, entries, s)) != cudaSuccess)
         return cuda_fail(h, e, "replay decide");
@@ -286,6 +288,7 @@ void dmpt_default_options(dmpt_options* o) {
   o->k_snake = 1;
   o->order = 1;
   o->tile_band = 8;
+  o->round_align = 1;
 }
 
 const char* dmpt_status_string(dmpt_status s) {
@@ -445,7 +448,7 @@ static dmpt_status forward_impl(dmpt_handle h, const double* H, const double* H1
       if (o->timing) cudaEventRecord(h->events[2 * launched], s);
       e = dual ? launch_layer_tc(L, workspace, s, o->timeout_s, o->accum_chunk, o->cta_pair,
                                  o->k_snake, o->tile_band, &entries, &pass_flops,
-                                 o->inject_stall)
+                                 o->inject_stall, o->round_align)
                : launch_layer_simt(L, workspace, s, &entries, &pass_flops);
       if (e != cudaSuccess) return cuda_fail(h, e, "layer product");
       if (o->timing) cudaEventRecord(h->events[2 * launched + 1], s);
@@ -821,7 +824,8 @@ dmpt_status dmpt_sp2_backward(dmpt_handle h, const double* G, int64_t n, int64_t
   double pass_flops = 0.0;
   for (int m = fs.d0_updates; m >= 1; --m) {
     if ((e = launch_layer_tc(L, workspace, s, o->timeout_s, o->accum_chunk, o->cta_pair,
-                             o->k_snake, o->tile_band, &entries, &pass_flops)) != cudaSuccess)
+                             o->k_snake, o->tile_band, &entries, &pass_flops, 0,
+                             o->round_align)) != cudaSuccess)
       return cuda_fail(h, e, "adjoint layer");
     if ((e = launch_decide(L, workspace, kDecideAdjLayer, entries, s)) != cudaSuccess)
       return cuda_fail(h, e, "adjoint decide");

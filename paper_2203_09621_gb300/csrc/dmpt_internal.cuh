@@ -141,7 +141,8 @@ int simt_tile(int precision);
 // ---- tensor-core path (kernels_tc.cu) ----
 // round_align: the pair kernel's producers keep their rounds in step (a
 // bounded wait, never an error); off where several instances' layer kernels
-// run at the same time, whose CTAs need not all be resident.
+// run at the same time, whose CTAs need not all be resident (dmpt_options::
+// round_align; always off on the per-instance batch path).
 cudaError_t launch_layer_tc(const Layout& L, void* ws, cudaStream_t s, double timeout_s,
                             int accum_chunk_k, int cta_pair, int k_snake, int band,
                             int64_t* entries, double* pass_flops, int inject_stall = 0,

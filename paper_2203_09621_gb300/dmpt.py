@@ -44,6 +44,7 @@ class DmptOptions(ctypes.Structure):
         ("tile_band", ctypes.c_int),
         ("inject_stall", ctypes.c_int),
         ("autotune", ctypes.c_int),
+        ("round_align", ctypes.c_int),
     ]
 
 
@@ -183,7 +184,7 @@ class Info:
 def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_scaling=1,
             sync_every=4, timing=False, timeout_s=2.0, accum_chunk=0,
             cta_pair=1, k_snake=1, ckpt_every=0, order=1, tile_band=8,
-            inject_stall=0, autotune=0) -> DmptOptions:
+            inject_stall=0, autotune=0, round_align=1) -> DmptOptions:
     lib = load_library()
     o = DmptOptions()
     lib.dmpt_default_options(ctypes.byref(o))
@@ -203,6 +204,7 @@ def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_s
     o.tile_band = int(tile_band)
     o.inject_stall = int(inject_stall)
     o.autotune = int(autotune)
+    o.round_align = int(round_align)
     return o
 
 

@@ -308,12 +308,13 @@ def test_leading_dimension(ctx, precision):
 @pytest.mark.parametrize("opts", [dict(k_snake=0), dict(tile_band=0), dict(tile_band=3),
                                   dict(tile_band=16), dict(accum_chunk=64),
                                   dict(accum_chunk=1024), dict(sync_every=1),
-                                  dict(cta_pair=0, accum_chunk=512)])
+                                  dict(cta_pair=0, accum_chunk=512), dict(round_align=0)])
 def test_options_keep_parity(ctx, opts):
     """Scheduling and accumulation options change the order of the work
-    (tile order, K direction, chunk length, host polling), not the method:
-    every setting stays within the dual-FP16 tolerance of the oracle.  Tile
-    order and host polling leave the result bit-identical to the defaults."""
+    (tile order, K direction, chunk length, host polling, round alignment),
+    not the method: every setting stays within the dual-FP16 tolerance of the
+    oracle.  Tile order, host polling and round alignment leave the result
+    bit-identical to the defaults."""
     inst = make_workload(2, n=1300, k=2)
     H = torch.from_numpy(inst.H).to(DEV)
     H1 = torch.from_numpy(inst.H1).to(DEV)
@@ -324,7 +325,7 @@ def test_options_keep_parity(ctx, opts):
     for j in range(2):
         _, P1r = oracle.response_from_eigs(eps, V, inst.H1[j], inst.n_occ)
         assert rel(P1[j].cpu().numpy(), P1r) < TOL["dual_fp16"], (opts, j)
-    if set(opts) <= {"tile_band", "sync_every"}:
+    if set(opts) <= {"tile_band", "sync_every", "round_align"}:
         Pd, P1d, _ = ctx.sp2_response(H, H1, inst.n_occ)
         torch.cuda.synchronize()
         assert torch.equal(P, Pd) and torch.equal(P1, P1d), opts
