@@ -9,6 +9,8 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include <mutex>
+
 #include "dmpt_internal.cuh"
 
 namespace dmpt {
@@ -749,21 +751,46 @@ struct SimtBlocks<double> {
   static constexpr int value = 1;
 };
 
+// 16-byte asynchronous copy global -> shared (L2 only), and its group waits
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Shared memory of the SIMT layer kernel: SIMT_STAGES stages of the two
+// operand slabs (BK x BT, rows padded by one 16-byte chunk), then the
+// block's reduction array.
+constexpr int SIMT_STAGES = 3;
+template <typename T, int TM, int BK>
+constexpr int simt_smem_bytes() {
+  return SIMT_STAGES * 2 * BK * (16 * TM + 16 / (int)sizeof(T)) * (int)sizeof(T) + 4 * 256 * 8;
+}
+
 template <typename T, int TM, int BK>
 __global__ void __launch_bounds__(256, SimtBlocks<T>::value)
     layer_simt_kernel(State* st, T* __restrict__ master, int64_t Np, int k,
                       double* __restrict__ partials, int64_t ptiles) {
   constexpr int BT = 16 * TM;
-  constexpr int VW = Vec<T>::width;
-  using V = typename Vec<T>::type;
-  constexpr int CPR = BK / VW;                 // vectors per tile row
-  constexpr int NV = BT * BK / (256 * VW);     // vectors per thread per operand
-  constexpr int PAD = VW;
+  constexpr int VW = 16 / (int)sizeof(T);      // elements per 16-byte copy
+  constexpr int LD = BT + VW;                  // padded row of a slab
+  constexpr int CPR = BT / VW;                 // copies per slab row
+  constexpr int NCP = BK * CPR / 256;          // copies per thread per slab
+  static_assert(NCP >= 1 && (BK * CPR) % 256 == 0, "slab copies divide over the block");
 
-  // two stages: the next K block is stored while the current one is used
-  __shared__ __align__(16) T As[2][BK][BT + PAD];
-  __shared__ __align__(16) T Bs[2][BK][BT + PAD];
-  __shared__ double red[4 * 256];
+  // stage s: As = slab of the A operand, Bs = slab of the B operand, each
+  // BK rows (K index) x BT columns (output rows / columns of the tile)
+  extern __shared__ __align__(16) uint8_t simt_smem[];
+  T* slabs = reinterpret_cast<T*>(simt_smem);
+  double* red = reinterpret_cast<double*>(simt_smem + SIMT_STAGES * 2 * BK * LD * sizeof(T));
 
   if (st->done) return;
   const int job = blockIdx.y;
@@ -796,58 +823,58 @@ __global__ void __launch_bounds__(256, SimtBlocks<T>::value)
     for (int j = 0; j < TM; ++j) acc[i][j] = T(0);
 
   const int passes = job == 0 ? 1 : 2;
+  const int nkb = (int)(Np / BK);
   for (int pass = 0; pass < passes; ++pass) {
-    // pass 0: A = S0 rows I, B = Sj rows J;  pass 1: A = Sj rows I, B = S0 rows J
-    const T* A = (pass == 0 ? S0 : Sj) + (size_t)I * BT * Np;
-    const T* B = (pass == 0 ? Sj : S0) + (size_t)J * BT * Np;
-    V ra[NV], rb[NV];
-    auto gload = [&](int kb) {
+    // pass 0: A = S0 rows I, B = Sj rows J;  pass 1: A = Sj rows I, B = S0 rows J.
+    // The masters are exactly symmetric (both halves are always written with
+    // the same value), so the K x BT slab A[I rows][kb ..] is read as rows
+    // kb .. kb + BK - 1, columns I BT .. I BT + BT - 1: contiguous 16-byte
+    // copies that land in shared memory already K-major.
+    const T* A = (pass == 0 ? S0 : Sj) + (size_t)I * BT;
+    const T* B = (pass == 0 ? Sj : S0) + (size_t)J * BT;
+    auto load = [&](int stage, int kb) {
+      T* as = slabs + (size_t)stage * 2 * BK * LD;
+      T* bs = as + BK * LD;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
+      for (int v = 0; v < NCP; ++v) {
         const int idx = tid + 256 * v;
         const int row = idx / CPR, cq = idx % CPR;
-        ra[v] = *reinterpret_cast<const V*>(A + (size_t)row * Np + kb + cq * VW);
-        rb[v] = *reinterpret_cast<const V*>(B + (size_t)row * Np + kb + cq * VW);
+        const size_t g = (size_t)(kb + row) * Np + cq * VW;
+        cp_async16(as + row * LD + cq * VW, A + g);
+        cp_async16(bs + row * LD + cq * VW, B + g);
       }
     };
-    auto sstore = [&](int buf) {
+    __syncthreads();   // every stage of the previous pass has been read
+    // prologue: stages 0 .. SIMT_STAGES - 2 in flight (one group each)
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const int idx = tid + 256 * v;
-        const int row = idx / CPR, cq = idx % CPR;
-        const T* pa = reinterpret_cast<const T*>(&ra[v]);
-        const T* pb = reinterpret_cast<const T*>(&rb[v]);
-#pragma unroll
-        for (int e = 0; e < VW; ++e) {
-          As[buf][cq * VW + e][row] = pa[e];
-          Bs[buf][cq * VW + e][row] = pb[e];
-        }
+    for (int sidx = 0; sidx < SIMT_STAGES - 1; ++sidx) {
+      if (sidx < nkb) load(sidx, sidx * BK);
+      cp_async_commit();
+    }
+    for (int it = 0; it < nkb; ++it) {
+      cp_async_wait<SIMT_STAGES - 2>();   // stage it has landed (this thread's copies)
+      __syncthreads();                    // ... and every thread's; stage it - 1 is free
+      {
+        const int nx = it + SIMT_STAGES - 1;
+        if (nx < nkb) load(nx % SIMT_STAGES, nx * BK);
+        cp_async_commit();
       }
-    };
-    __syncthreads();   // the previous pass's last stage has been read
-    gload(0);
-    sstore(0);
-    __syncthreads();
-    int buf = 0;
-    for (int kb = 0; kb < Np; kb += BK) {
-      const bool more = kb + BK < Np;
-      if (more) gload(kb + BK);
+      const T* as = slabs + (size_t)(it % SIMT_STAGES) * 2 * BK * LD;
+      const T* bs = as + BK * LD;
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
         T a[TM], b[TM];
 #pragma unroll
-        for (int m = 0; m < TM; ++m) a[m] = As[buf][kk][frag_index<T, TM>(ty, m)];
+        for (int m = 0; m < TM; ++m) a[m] = as[kk * LD + frag_index<T, TM>(ty, m)];
 #pragma unroll
-        for (int m = 0; m < TM; ++m) b[m] = Bs[buf][kk][frag_index<T, TM>(tx, m)];
+        for (int m = 0; m < TM; ++m) b[m] = bs[kk * LD + frag_index<T, TM>(tx, m)];
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
           for (int j = 0; j < TM; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
       }
-      if (more) sstore(buf ^ 1);   // the other stage was last read one step ago
-      __syncthreads();
-      buf ^= 1;
     }
+    cp_async_wait<0>();   // no copy of this pass left in flight
   }
 
   // ---- fused epilogue
@@ -922,6 +949,23 @@ __global__ void __launch_bounds__(256, SimtBlocks<T>::value)
 
 int simt_tile(int precision) { return precision == DMPT_FP64 ? 64 : 128; }
 
+// Per-device one-time setup: the SIMT layer kernels' dynamic shared memory
+// exceeds the default 48 KB limit; thread-safe.
+static void simt_setup() {
+  constexpr int kDevices = 64;
+  static std::once_flag once[kDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevices) return;
+  std::call_once(once[dev], [] {
+    cudaFuncSetAttribute(layer_simt_kernel<double, 4, 8>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         simt_smem_bytes<double, 4, 8>());
+    cudaFuncSetAttribute(layer_simt_kernel<float, 8, 16>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         simt_smem_bytes<float, 8, 16>());
+  });
+}
+
 cudaError_t launch_layer_simt(const Layout& L, void* ws, cudaStream_t s, int64_t* entries,
                               double* pass_flops) {
   char* base = (char*)ws;
@@ -929,12 +973,16 @@ cudaError_t launch_layer_simt(const Layout& L, void* ws, cudaStream_t s, int64_t
   double* partials = (double*)(base + L.off_partials);
   const int bt = simt_tile(L.precision);
   dim3 grid((unsigned)upper_tiles(L.Np, bt), 1 + L.k);
+  constexpr int smem64 = simt_smem_bytes<double, 4, 8>();
+  constexpr int smem32 = simt_smem_bytes<float, 8, 16>();
+  static_assert(2 * smem32 <= 227 * 1024, "two FP32 blocks per SM");
+  simt_setup();
   if (L.precision == DMPT_FP64)
-    layer_simt_kernel<double, 4, 8><<<grid, 256, 0, s>>>(st, (double*)(base + L.off_master),
-                                                         L.Np, L.k, partials, L.partial_tiles);
+    layer_simt_kernel<double, 4, 8><<<grid, 256, smem64, s>>>(
+        st, (double*)(base + L.off_master), L.Np, L.k, partials, L.partial_tiles);
   else
-    layer_simt_kernel<float, 8, 16><<<grid, 256, 0, s>>>(st, (float*)(base + L.off_master),
-                                                         L.Np, L.k, partials, L.partial_tiles);
+    layer_simt_kernel<float, 8, 16><<<grid, 256, smem32, s>>>(
+        st, (float*)(base + L.off_master), L.Np, L.k, partials, L.partial_tiles);
   if (entries) *entries = upper_tiles(L.Np, bt);
   if (pass_flops) *pass_flops = (double)upper_tiles(L.Np, bt) * bt * bt * (double)L.Np * 2.0;
   return cudaGetLastError();
