@@ -44,7 +44,7 @@ K_DEFAULT = 3
 # n8192_k3_dram.md).  Valid only for that kernel source and that workload.
 TRAFFIC_RECORD = {
     "source": "paper_2203_09621_gb300/csrc/kernels_tc.cu",
-    "sha256": "b82155a3f6ab79ca8477a69eded369a6a1a906fbc02967fb6f7a4ec17809f725",
+    "sha256": "9fafaca2d1fa4e30d3d89402dffa206595546eebd72f4013afcb17c38285deb2",
     "workload": {"n": 8192, "k": 3, "precision": "dual_fp16", "cta_pair": 1, "k_snake": 1,
                  "tile_band": 8, "accum_chunk": 0},
     "bytes_per_launch": 9.8315e9 + 2.0589e9,

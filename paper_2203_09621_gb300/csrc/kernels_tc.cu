@@ -1051,8 +1051,9 @@ __device__ __forceinline__ bool mma_item(RingPos& rg, RingPos& tb, int nst, int 
 // Soft round alignment of the pair kernel's producers.  Items go to the
 // pairs round-robin, so the 76 tiles of a round share their operand panels
 // in L2 only while the pairs stay in step; a pair that drifts a round ahead
-// fetches those panels from HBM again (with the tile epilogue below the
-// pairs do drift, and DRAM reads per layer double).  At the start of each
+// fetches those panels from HBM again (with the fast, coalesced tile
+// epilogue the pairs do drift, and DRAM reads per layer double).  The count
+// is a scheduling hint only: no data depends on it.  At the start of each
 // round r >= 1 a producer counts itself in and waits until every CTA that
 // has an item in round r has started it.  The wait is bounded
 // (kRoundAlignNs) and is never an error: after an expiry that producer stops
