@@ -199,7 +199,7 @@ dmpt_status dmpt_sp2_response(dmpt_handle h, const double* H, const double* H1,
  * each S2_j stops by the test of Alg. 3 applied to its own idempotency error
  * ||S2 - (S0 S2 + S1 S1 + S2 S0)||_F (same C_pt and FroErr^(0)).
  *   Same arguments as dmpt_sp2_response plus P2 (device, k blocks n x n,
- *   ld); 1 <= k <= DMPT_MAX_K / 2; dual precisions, no tape.  The workspace
+ *   ld); 1 <= k <= DMPT_MAX_K / 2; any precision, no tape.  The workspace
  *   is dmpt_workspace_size(n, k, o) with o->order = 2.  In info, entries
  *   k .. 2k-1 of d1_layer / froerr1 are those of the second-order terms. */
 dmpt_status dmpt_sp2_response2(dmpt_handle h, const double* H, const double* H1, int k,
@@ -221,12 +221,12 @@ dmpt_status dmpt_sp2_response2(dmpt_handle h, const double* H, const double* H1,
  *          dmpt_sp2_response (Pk unused), order 2 is dmpt_sp2_response2.
  *   Pk     device, the terms of orders 2 .. order: (order - 1) k blocks of
  *          n x n (ld), order o's direction j at Pk + ((o - 2) k + j) n ld.
- *   Other arguments as dmpt_sp2_response; dual precisions and no tape for
- *   order >= 2.  The workspace is dmpt_workspace_size(n, k, o) with
+ *   Other arguments as dmpt_sp2_response; every precision, no tape for
+ *   order >= 2 (the FP32 / FP64 forms run the same passes on the CUDA cores).  The workspace is dmpt_workspace_size(n, k, o) with
  *   o->order = order.  In info, entries (o - 1) k .. o k - 1 of d1_layer /
  *   froerr1 are those of order o.  Errors: DMPT_EINVAL for an order outside
  *   [1, DMPT_MAX_ORDER], order * k > DMPT_MAX_K or a null Pk;
- *   DMPT_EUNSUPPORTED for order >= 2 with a non-dual precision or a tape. */
+ *   DMPT_EUNSUPPORTED for order >= 2 with a tape (o->ckpt_every). */
 dmpt_status dmpt_sp2_response_m(dmpt_handle h, const double* H, const double* H1, int k,
                                 int64_t n, int64_t ld, int64_t n_occ, int order,
                                 const dmpt_options* o, double* P, double* P1, double* Pk,

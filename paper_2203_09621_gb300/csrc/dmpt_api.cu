@@ -381,9 +381,8 @@ static dmpt_status forward_impl(dmpt_handle h, const double* H, const double* H1
     if (k < 1 || order * k > DMPT_MAX_K || !Pk)
       return fail(h, DMPT_EINVAL,
                   "dmpt_sp2_response_m: need k >= 1, order * k <= DMPT_MAX_K and Pk%s");
-    if (o->precision < DMPT_DUAL_FP16 || o->ckpt_every != 0)
-      return fail(h, DMPT_EUNSUPPORTED,
-                  "dmpt_sp2_response_m: orders >= 2 need a dual precision and no tape%s");
+    if (o->ckpt_every != 0)
+      return fail(h, DMPT_EUNSUPPORTED, "dmpt_sp2_response_m: orders >= 2 keep no tape%s");
   }
   if (o->ckpt_every != 0 && o->precision < DMPT_DUAL_FP16)
     return fail(h, DMPT_EUNSUPPORTED,

@@ -710,10 +710,11 @@ cudaError_t launch_decide(const Layout& L, void* ws, int mode, int64_t entries, 
 // ---------------------------------------------------------------------------
 // SIMT layer product with fused epilogue (FP64 and FP32 forms).
 //
-// Grid: (upper tiles, 1 + K).  Job 0 computes X = S0 S0 (Sec. II B,
+// Grid: (upper tiles, 1 + slots).  Job 0 computes X = S0 S0 (Sec. II B,
 // Eq. (DNN-SP2_act)) for tile (I, J), I <= J; job 1+k computes
 // X1 = S0 S1_k + S1_k S0 (activation f^(1), Eq. (eq:activation-function))
-// as one accumulation over two K-passes.  Both operands are read as row
+// as one accumulation over two K-passes; a higher-order term (Sec. III A,
+// Eq. (S_n detailed)) adds its cross products S_a S_{o-a} as further passes.  Both operands are read as row
 // panels: for symmetric B, B[k][j] = B[j][k].  The epilogue applies
 // S_n = sigma X + (1 - sigma) S_{n-1} (Eq. (eq:Sn); Alg. 2 / Alg. 3 updates)
 // to the elements with row <= col, stores them at (r, c) and (c, r) in the
@@ -750,6 +751,32 @@ template <>
 struct SimtBlocks<double> {
   static constexpr int value = 1;
 };
+
+// Jobs of a layer (as in the tensor-core kernels): 0 = square of S0; job
+// 1 + (o - 1) k1 + d = the order-o term of direction d, in o + 1 K passes
+// (pass 0 = S0 S_o, pass 1 = S_o S0, pass p >= 2 = S_{p-1} S_{o-p+1}).
+__device__ __forceinline__ int simt_job_order(int job, int k1) { return 1 + (job - 1) / k1; }
+__device__ __forceinline__ int simt_job_passes(int job, int k1) {
+  return job == 0 ? 1 : (job <= k1 ? 2 : 1 + simt_job_order(job, k1));
+}
+__device__ __forceinline__ int simt_job_slot(int job, int a, int k1) {
+  return 1 + (a - 1) * k1 + (job - 1) % k1;
+}
+__device__ __forceinline__ void simt_job_operands(int job, int pass, int k1, int* mA, int* mB) {
+  if (job == 0) {
+    *mA = 0;
+    *mB = 0;
+  } else if (pass == 0) {
+    *mA = 0;
+    *mB = job;
+  } else if (pass == 1) {
+    *mA = job;
+    *mB = 0;
+  } else {
+    *mA = simt_job_slot(job, pass - 1, k1);
+    *mB = simt_job_slot(job, simt_job_order(job, k1) - pass + 1, k1);
+  }
+}
 
 // 16-byte asynchronous copy global -> shared (L2 only), and its group waits
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -810,8 +837,7 @@ __global__ void __launch_bounds__(256, SimtBlocks<T>::value)
   const size_t mat = (size_t)Np * Np;
   const int cur0 = st->cur0;
   const int cur = job == 0 ? cur0 : st->cur1[job - 1];
-  const T* S0 = master + (size_t)(cur0 * (1 + k)) * mat;
-  const T* Sj = master + (size_t)(cur * (1 + k) + job) * mat;   // S0 (job 0) or S1_k
+  const T* Sj = master + (size_t)(cur * (1 + k) + job) * mat;   // the job's own slot
   T* out = master + (size_t)((cur ^ 1) * (1 + k) + job) * mat;
 
   const int tid = threadIdx.x;
@@ -822,16 +848,22 @@ __global__ void __launch_bounds__(256, SimtBlocks<T>::value)
 #pragma unroll
     for (int j = 0; j < TM; ++j) acc[i][j] = T(0);
 
-  const int passes = job == 0 ? 1 : 2;
+  const int k1 = st->order >= 2 ? st->k1 : k;   // first-order directions
+  const int passes = simt_job_passes(job, k1);
   const int nkb = (int)(Np / BK);
   for (int pass = 0; pass < passes; ++pass) {
-    // pass 0: A = S0 rows I, B = Sj rows J;  pass 1: A = Sj rows I, B = S0 rows J.
-    // The masters are exactly symmetric (both halves are always written with
-    // the same value), so the K x BT slab A[I rows][kb ..] is read as rows
+    // pass p of the job: A = slot mA rows I, B = slot mB rows J (square:
+    // S0 S0; order-o term: S0 S_o, S_o S0, then S_{p-1} S_{o-p+1}).  The
+    // masters are exactly symmetric (both halves are always written with the
+    // same value), so the K x BT slab A[I rows][kb ..] is read as rows
     // kb .. kb + BK - 1, columns I BT .. I BT + BT - 1: contiguous 16-byte
     // copies that land in shared memory already K-major.
-    const T* A = (pass == 0 ? S0 : Sj) + (size_t)I * BT;
-    const T* B = (pass == 0 ? Sj : S0) + (size_t)J * BT;
+    int mA, mB;
+    simt_job_operands(job, pass, k1, &mA, &mB);
+    const T* A = master + (size_t)((mA == 0 ? cur0 : st->cur1[mA - 1]) * (1 + k) + mA) * mat +
+                 (size_t)I * BT;
+    const T* B = master + (size_t)((mB == 0 ? cur0 : st->cur1[mB - 1]) * (1 + k) + mB) * mat +
+                 (size_t)J * BT;
     auto load = [&](int stage, int kb) {
       T* as = slabs + (size_t)stage * 2 * BK * LD;
       T* bs = as + BK * LD;

@@ -1,5 +1,8 @@
 """GPU parity of the responses of any order (dmpt_sp2_response_m).
 
+Dual forms on the tensor cores; the FP64 and FP32 forms run the same passes
+on the CUDA cores.
+
 P_o = (1/o!) d^o P / dlambda^o from S_o,n = sigma (S0 S_o + S_o S0 +
 sum_{a=1}^{o-1} S_a S_{o-a}) + (1 - sigma) S_o on the tensor cores (o + 1 K
 passes per term), against the FP64 oracle's SP2 recursion of the same order
@@ -57,6 +60,44 @@ def test_order_m_matches_oracle(ctx, precision, cfg, n, k, order):
         assert torch.equal(t, t.transpose(1, 2))
 
 
+@pytest.mark.parametrize("cfg,n,k,order", [(2, 300, 1, 3), (3, 256, 2, 4)])
+def test_order_m_fp64_form(ctx, cfg, n, k, order):
+    """The FP64 form runs the same recursion as the FP64 oracle: the same
+    first-order stop layers, every term to 1e-9.  A higher order's stop test
+    compares rounding-level residuals, so its layer may differ by a sigma-flip
+    pair without changing the converged term."""
+    inst = make_workload(cfg, n=n, k=k)
+    H = torch.from_numpy(inst.H).to(DEV)
+    H1 = torch.from_numpy(inst.H1).to(DEV)
+    P, terms, info = ctx.sp2_response_m(H, H1, inst.n_occ, order, precision="fp64")
+    torch.cuda.synchronize()
+    ref = oracle.sp2_pt(inst.H, inst.H1, inst.n_occ, order=order)
+    assert info.converged and ref.converged
+    assert abs(info.layers - ref.layers) <= 2
+    assert info.d1_layer[:k] == ref.dk_layer[0]
+    for o in range(order):
+        for j in range(k):
+            assert rel(terms[o][j].cpu().numpy(), ref.Pk[o][j]) < 1e-9, (o, j)
+
+
+def test_order_m_fp32_form(ctx):
+    """The FP32 form carries about the precision of the dual forms, and is
+    held to the dual-FP16 tolerance per term."""
+    inst = make_workload(2, n=300, k=1)
+    H = torch.from_numpy(inst.H).to(DEV)
+    H1 = torch.from_numpy(inst.H1).to(DEV)
+    P, terms, info = ctx.sp2_response_m(H, H1, inst.n_occ, 3, precision="fp32")
+    torch.cuda.synchronize()
+    assert info.converged
+    ref = oracle.sp2_pt(inst.H, inst.H1, inst.n_occ, order=3)
+    errs = [rel(terms[o][0].cpu().numpy(), ref.Pk[o][0]) for o in range(3)]
+    assert max(errs) < TOL["dual_fp16"], errs
+    # first-order terms bit-identical to the first-order call of the same form
+    P1c, P1r, _ = ctx.sp2_response(H, H1, inst.n_occ, precision="fp32")
+    torch.cuda.synchronize()
+    assert torch.equal(P, P1c) and torch.equal(terms[0], P1r)
+
+
 @pytest.mark.parametrize("precision", ["dual_fp16", "dual_bf16"])
 def test_order_m_one_cta_tiles(ctx, precision):
     """The 1-CTA kernel (128 x 256 tiles) runs the same order-o jobs."""
@@ -104,8 +145,8 @@ def test_rejections(ctx):
     inst = make_workload(1, n=64)
     H = torch.from_numpy(inst.H).to(DEV)
     H1 = torch.from_numpy(inst.H1).to(DEV)
-    with pytest.raises(dmpt.DmptError) as e:          # non-dual precision
-        ctx.sp2_response_m(H, H1, inst.n_occ, 3, precision="fp32")
+    with pytest.raises(dmpt.DmptError) as e:          # no tape for orders >= 2
+        ctx.sp2_response_m(H, H1, inst.n_occ, 3, ckpt_every=1)
     assert e.value.status == 7
     H1x3 = torch.zeros(3, 64, 64, dtype=torch.float64, device=DEV)
     with pytest.raises(dmpt.DmptError):               # order * k = 9 > DMPT_MAX_K
