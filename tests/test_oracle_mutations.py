@@ -1,0 +1,118 @@
+"""The oracle's pins catch plausible mistakes (mutation check, CPU only).
+
+Each case plants one mistake in a copy of the oracle's SP2 module (a
+dropped term, a wrong sign, a wrong index, a transposed or one-sided
+product, a wrong branch rule), loads the copy as a separate module, and
+checks that at least one pin that does not use the SP2 recursion itself
+fails on it:
+  * agreement with the sum-over-states response (a different route to the
+    same limit), first and second order;
+  * the order-by-order identities of the converged terms (idempotency,
+    commutation, trace);
+  * plain SP2 on the block upper-triangular matrix of Sec. III B.
+The unmutated module passes all of them.  Nothing here touches the CUDA
+path: the mistakes are planted in the oracle, on the CPU.
+"""
+
+import importlib.util
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.sos import response2_sos
+from paper_2203_09621_gb300.workloads import make_workload
+
+SP2_PATH = os.path.join(os.path.dirname(oracle.__file__), "sp2.py")
+
+MUTATIONS = [
+    ("dropped cross term of order o", "for a in range(1, o):", "for a in range(1, max(1, o - 1)):"),
+    ("one-sided response product", "acc = S0 @ S[o][j] + S[o][j] @ S0", "acc = 2 * S0 @ S[o][j]"),
+    ("wrong cross index", "acc = acc + S[a][j] @ S[o - a][j]", "acc = acc + S[a][j] @ S[a][j]"),
+    ("sign of the initial response", "S = {1: [W0 * H1[j] for j in range(k)]}",
+     "S = {1: [-W0 * H1[j] for j in range(k)]}"),
+    ("bias with S_n instead of S_{n-1}", "S0 = s * X0 + (1 - s) * S0", "S0 = s * X0 + (1 - s) * X0"),
+    ("response update without the bias", "S[o][j] = s * X[o][j] + (1 - s) * S[o][j]",
+     "S[o][j] = s * X[o][j]"),
+    ("branch rule inverted",
+     "sigma[n_layer] = _sign_tie_minus(abs(2.0 * NS - NX - n_occ) - abs(NX - n_occ))",
+     "sigma[n_layer] = -_sign_tie_minus(abs(2.0 * NS - NX - n_occ) - abs(NX - n_occ))"),
+]
+
+
+def load_variant(src, name):
+    spec = importlib.util.spec_from_loader(f"oracle.{name}", loader=None)
+    mod = importlib.util.module_from_spec(spec)
+    mod.__package__ = "oracle"
+    sys.modules[spec.name] = mod
+    try:
+        exec(compile(src, SP2_PATH, "exec"), mod.__dict__)
+    finally:
+        del sys.modules[spec.name]
+    return mod
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def case():
+    inst = make_workload(1, n=64)
+    D1 = oracle.response_sos(inst.H, inst.H1[0], inst.n_occ)[1]
+    D2 = response2_sos(inst.H, inst.H1[0], inst.n_occ)
+    return inst, D1, D2
+
+
+def pins_fail(mod, case):
+    """Names of the pins the module fails (empty: passes them all)."""
+    inst, D1, D2 = case
+    failed = []
+    try:
+        r = mod.sp2_pt(inst.H, inst.H1, inst.n_occ, order=3, max_layers=100)
+    except Exception as e:   # a mistake may also break the run
+        return [f"raised {type(e).__name__}"]
+    if not r.converged:
+        failed.append("converged")
+    if rel(r.Pk[0][0], D1) > 1e-9:
+        failed.append("first order vs sum over states")
+    if rel(r.Pk[1][0], D2) > 1e-9:
+        failed.append("second order vs sum over states")
+    Pk = [r.P] + [p[0] for p in r.Pk]
+    H, H1 = inst.H, inst.H1[0]
+    for o in range(1, 4):
+        sc = max(np.linalg.norm(Pk[o]), 1e-300)
+        if np.linalg.norm(sum(Pk[a] @ Pk[o - a] for a in range(o + 1)) - Pk[o]) > 1e-8 * sc:
+            failed.append(f"idempotency, order {o}")
+        comm = H @ Pk[o] - Pk[o] @ H + H1 @ Pk[o - 1] - Pk[o - 1] @ H1
+        if np.linalg.norm(comm) > 1e-7 * sc * np.linalg.norm(H):
+            failed.append(f"commutation, order {o}")
+    # plain SP2 of the 4n x 4n block matrix with the run's own decisions
+    n, m = inst.n, 3
+    Hb = np.zeros(((m + 1) * n, (m + 1) * n))
+    for b in range(m + 1):
+        Hb[b * n:(b + 1) * n, b * n:(b + 1) * n] = H
+        if b < m:
+            Hb[b * n:(b + 1) * n, (b + 1) * n:(b + 2) * n] = H1
+    e1, eN = r.bounds
+    S = (eN * np.eye((m + 1) * n) - Hb) / (eN - e1)
+    for s in r.sigma[: r.dk_layer[2][0] - 1]:
+        S = S @ S if s == 1 else 2 * S - S @ S
+    if rel(S[:n, 3 * n:], Pk[3]) > 1e-8:
+        failed.append("block matrix, order 3")
+    return failed
+
+
+def test_unmutated_oracle_passes(case):
+    src = open(SP2_PATH).read()
+    assert pins_fail(load_variant(src, "sp2_copy"), case) == []
+
+
+@pytest.mark.parametrize("what,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(case, what, old, new):
+    src = open(SP2_PATH).read()
+    assert src.count(old) == 1, what
+    failed = pins_fail(load_variant(src.replace(old, new), "sp2_mutant"), case)
+    assert failed, what
