@@ -1,16 +1,22 @@
 """The oracle's pins catch plausible mistakes (mutation check, CPU only).
 
-Each case plants one mistake in a copy of the oracle's SP2 module (a
-dropped term, a wrong sign, a wrong index, a transposed or one-sided
-product, a wrong branch rule), loads the copy as a separate module, and
-checks that at least one pin that does not use the SP2 recursion itself
-fails on it:
+Each case plants one mistake in a copy of an oracle module (a dropped
+term, a wrong sign, a wrong index, a transposed or one-sided product, a
+wrong branch rule), loads the copy as a separate module, and checks that at
+least one pin that does not use the mutated formula itself fails on it.
+
+SP2 recursion (oracle/sp2.py):
   * agreement with the sum-over-states response (a different route to the
     same limit), first and second order;
   * the order-by-order identities of the converged terms (idempotency,
     commutation, trace);
   * plain SP2 on the block upper-triangular matrix of Sec. III B.
-The unmutated module passes all of them.  Nothing here touches the CUDA
+Sum over states (oracle/sos.py), first and second order:
+  * the 2x2 closed form (tests/golden/two_level.json);
+  * central finite differences of the eigendecomposition projector;
+  * the identities of the first- and second-order blocks of D^2 = D and
+    [H + lambda H1, D] = 0.
+The unmutated modules pass all of them.  Nothing here touches the CUDA
 path: the mistakes are planted in the oracle, on the CPU.
 """
 
@@ -26,6 +32,7 @@ from oracle.sos import response2_sos
 from paper_2203_09621_gb300.workloads import make_workload
 
 SP2_PATH = os.path.join(os.path.dirname(oracle.__file__), "sp2.py")
+SOS_PATH = os.path.join(os.path.dirname(oracle.__file__), "sos.py")
 
 MUTATIONS = [
     ("dropped cross term of order o", "for a in range(1, o):", "for a in range(1, max(1, o - 1)):"),
@@ -42,13 +49,13 @@ MUTATIONS = [
 ]
 
 
-def load_variant(src, name):
+def load_variant(src, name, path=SP2_PATH):
     spec = importlib.util.spec_from_loader(f"oracle.{name}", loader=None)
     mod = importlib.util.module_from_spec(spec)
     mod.__package__ = "oracle"
     sys.modules[spec.name] = mod
     try:
-        exec(compile(src, SP2_PATH, "exec"), mod.__dict__)
+        exec(compile(src, path, "exec"), mod.__dict__)
     finally:
         del sys.modules[spec.name]
     return mod
@@ -115,4 +122,57 @@ def test_planted_mistake_is_caught(case, what, old, new):
     src = open(SP2_PATH).read()
     assert src.count(old) == 1, what
     failed = pins_fail(load_variant(src.replace(old, new), "sp2_mutant"), case)
+    assert failed, what
+
+
+SOS_MUTATIONS = [
+    ("sign of the divided difference", "F[mask] = df[mask] / de[mask]",
+     "F[mask] = -df[mask] / de[mask]"),
+    ("transposed eigenbasis", "P1 = V @ (F * Y) @ V.T", "P1 = V.T @ (F * Y) @ V"),
+    ("sign of the first divided difference in the second order",
+     "d1[mask] = (f[mask] - f[m]) / (eps[mask] - eps[m])",
+     "d1[mask] = (f[m] - f[mask]) / (eps[mask] - eps[m])"),
+    ("sign of the confluent second divided difference",
+     "diag[mask] = -(f[mask] - f[m]) / (eps[mask] - eps[m]) ** 2",
+     "diag[mask] = (f[mask] - f[m]) / (eps[mask] - eps[m]) ** 2"),
+    ("halved second-order sum", "M += _second_divided_differences(eps, f, m) * np.outer(Y[:, m], Y[m, :])",
+     "M += 0.5 * _second_divided_differences(eps, f, m) * np.outer(Y[:, m], Y[m, :])"),
+]
+
+
+def sos_pins_fail(mod, golden):
+    failed = []
+    g = golden("two_level.json")
+    P, P1 = mod.response_sos(np.array(g["H"]), np.array(g["H1"]), g["n_occ"])
+    if np.abs(P1 - np.array(g["P1"])).max() > 1e-12:
+        failed.append("2x2 closed form")
+    inst = make_workload(1, n=48)
+    H, H1, n_occ = inst.H, inst.H1[0], inst.n_occ
+    P, P1 = mod.response_sos(H, H1, n_occ)
+    D2 = mod.response2_sos(H, H1, n_occ)
+    D = lambda t: oracle.density_matrix(H + t * H1, n_occ)   # eigh projector, unmutated
+    h = 1e-3
+    if rel((D(h) - D(-h)) / (2 * h), P1) > 1e-4:
+        failed.append("first-order finite differences")
+    if rel((D(h) - 2 * D(0.0) + D(-h)) / (2 * h * h), D2) > 1e-3:
+        failed.append("second-order finite differences")
+    if np.linalg.norm(P @ P1 + P1 @ P - P1) > 1e-10 * np.linalg.norm(P1):
+        failed.append("first-order idempotency")
+    if np.linalg.norm(P @ D2 + P1 @ P1 + D2 @ P - D2) > 1e-10 * np.linalg.norm(D2):
+        failed.append("second-order idempotency")
+    if np.linalg.norm(H @ D2 - D2 @ H + H1 @ P1 - P1 @ H1) > 1e-9 * np.linalg.norm(D2):
+        failed.append("second-order commutation")
+    return failed
+
+
+def test_unmutated_sos_passes(golden):
+    src = open(SOS_PATH).read()
+    assert sos_pins_fail(load_variant(src, "sos_copy", SOS_PATH), golden) == []
+
+
+@pytest.mark.parametrize("what,old,new", SOS_MUTATIONS, ids=[m[0] for m in SOS_MUTATIONS])
+def test_planted_sos_mistake_is_caught(golden, what, old, new):
+    src = open(SOS_PATH).read()
+    assert src.count(old) == 1, what
+    failed = sos_pins_fail(load_variant(src.replace(old, new), "sos_mutant", SOS_PATH), golden)
     assert failed, what
