@@ -16,6 +16,11 @@ Sum over states (oracle/sos.py), first and second order:
   * central finite differences of the eigendecomposition projector;
   * the identities of the first- and second-order blocks of D^2 = D and
     [H + lambda H1, D] = 0.
+Adjoint (oracle/sp2.py, sp2_adjoint): the self-adjoint Daleckii-Krein
+derivative (the forward response with H1 := G, by sum over states) and
+central differences of Tr[G P(H + t E)].
+Self-consistent response (oracle/scc.py): the closed-form fixed point
+q = (I - chi gamma)^-1 q0 from the charge susceptibility chi.
 The unmutated modules pass all of them.  Nothing here touches the CUDA
 path: the mistakes are planted in the oracle, on the CPU.
 """
@@ -33,6 +38,7 @@ from paper_2203_09621_gb300.workloads import make_workload
 
 SP2_PATH = os.path.join(os.path.dirname(oracle.__file__), "sp2.py")
 SOS_PATH = os.path.join(os.path.dirname(oracle.__file__), "sos.py")
+SCC_PATH = os.path.join(os.path.dirname(oracle.__file__), "scc.py")
 
 MUTATIONS = [
     ("dropped cross term of order o", "for a in range(1, o):", "for a in range(1, max(1, o - 1)):"),
@@ -83,18 +89,18 @@ def pins_fail(mod, case):
         return [f"raised {type(e).__name__}"]
     if not r.converged:
         failed.append("converged")
-    if rel(r.Pk[0][0], D1) > 1e-9:
+    if not rel(r.Pk[0][0], D1) <= 1e-9:
         failed.append("first order vs sum over states")
-    if rel(r.Pk[1][0], D2) > 1e-9:
+    if not rel(r.Pk[1][0], D2) <= 1e-9:
         failed.append("second order vs sum over states")
     Pk = [r.P] + [p[0] for p in r.Pk]
     H, H1 = inst.H, inst.H1[0]
     for o in range(1, 4):
         sc = max(np.linalg.norm(Pk[o]), 1e-300)
-        if np.linalg.norm(sum(Pk[a] @ Pk[o - a] for a in range(o + 1)) - Pk[o]) > 1e-8 * sc:
+        if not np.linalg.norm(sum(Pk[a] @ Pk[o - a] for a in range(o + 1)) - Pk[o]) <= 1e-8 * sc:
             failed.append(f"idempotency, order {o}")
         comm = H @ Pk[o] - Pk[o] @ H + H1 @ Pk[o - 1] - Pk[o - 1] @ H1
-        if np.linalg.norm(comm) > 1e-7 * sc * np.linalg.norm(H):
+        if not np.linalg.norm(comm) <= 1e-7 * sc * np.linalg.norm(H):
             failed.append(f"commutation, order {o}")
     # plain SP2 of the 4n x 4n block matrix with the run's own decisions
     n, m = inst.n, 3
@@ -107,7 +113,7 @@ def pins_fail(mod, case):
     S = (eN * np.eye((m + 1) * n) - Hb) / (eN - e1)
     for s in r.sigma[: r.dk_layer[2][0] - 1]:
         S = S @ S if s == 1 else 2 * S - S @ S
-    if rel(S[:n, 3 * n:], Pk[3]) > 1e-8:
+    if not rel(S[:n, 3 * n:], Pk[3]) <= 1e-8:
         failed.append("block matrix, order 3")
     return failed
 
@@ -144,7 +150,7 @@ def sos_pins_fail(mod, golden):
     failed = []
     g = golden("two_level.json")
     P, P1 = mod.response_sos(np.array(g["H"]), np.array(g["H1"]), g["n_occ"])
-    if np.abs(P1 - np.array(g["P1"])).max() > 1e-12:
+    if not np.abs(P1 - np.array(g["P1"])).max() <= 1e-12:
         failed.append("2x2 closed form")
     inst = make_workload(1, n=48)
     H, H1, n_occ = inst.H, inst.H1[0], inst.n_occ
@@ -152,15 +158,15 @@ def sos_pins_fail(mod, golden):
     D2 = mod.response2_sos(H, H1, n_occ)
     D = lambda t: oracle.density_matrix(H + t * H1, n_occ)   # eigh projector, unmutated
     h = 1e-3
-    if rel((D(h) - D(-h)) / (2 * h), P1) > 1e-4:
+    if not rel((D(h) - D(-h)) / (2 * h), P1) <= 1e-4:
         failed.append("first-order finite differences")
-    if rel((D(h) - 2 * D(0.0) + D(-h)) / (2 * h * h), D2) > 1e-3:
+    if not rel((D(h) - 2 * D(0.0) + D(-h)) / (2 * h * h), D2) <= 1e-3:
         failed.append("second-order finite differences")
-    if np.linalg.norm(P @ P1 + P1 @ P - P1) > 1e-10 * np.linalg.norm(P1):
+    if not np.linalg.norm(P @ P1 + P1 @ P - P1) <= 1e-10 * np.linalg.norm(P1):
         failed.append("first-order idempotency")
-    if np.linalg.norm(P @ D2 + P1 @ P1 + D2 @ P - D2) > 1e-10 * np.linalg.norm(D2):
+    if not np.linalg.norm(P @ D2 + P1 @ P1 + D2 @ P - D2) <= 1e-10 * np.linalg.norm(D2):
         failed.append("second-order idempotency")
-    if np.linalg.norm(H @ D2 - D2 @ H + H1 @ P1 - P1 @ H1) > 1e-9 * np.linalg.norm(D2):
+    if not np.linalg.norm(H @ D2 - D2 @ H + H1 @ P1 - P1 @ H1) <= 1e-9 * np.linalg.norm(D2):
         failed.append("second-order commutation")
     return failed
 
@@ -176,3 +182,84 @@ def test_planted_sos_mistake_is_caught(golden, what, old, new):
     assert src.count(old) == 1, what
     failed = sos_pins_fail(load_variant(src.replace(old, new), "sos_mutant", SOS_PATH), golden)
     assert failed, what
+
+
+ADJ_MUTATIONS = [
+    ("one-sided adjoint product", "Gbar = s * (Sp @ Gbar + Gbar @ Sp) + (1 - s) * Gbar",
+     "Gbar = s * (2 * Sp @ Gbar) + (1 - s) * Gbar"),
+    ("sign of the input transform", "return -Gbar / (epsN - eps1)", "return Gbar / (epsN - eps1)"),
+    ("state of the wrong layer", "Sp = states[idx]", "Sp = states[idx + 1]"),
+]
+
+
+def adj_pins_fail(mod):
+    from paper_2203_09621_gb300.workloads import sym_gauss
+    failed = []
+    inst = make_workload(1, n=48)
+    G = sym_gauss(48, 12)
+    r = oracle.sp2_pt(inst.H, inst.H1, inst.n_occ)
+    dLdH = mod.sp2_adjoint(inst.H, G, inst.n_occ, r.sigma[: r.d0_layer - 1], r.bounds)
+    _, P1G = oracle.response_sos(inst.H, G, inst.n_occ)
+    if not rel(dLdH, P1G) <= 1e-9:
+        failed.append("self-adjoint derivative")
+    E = sym_gauss(48, 13)
+    L = lambda t: np.sum(G * oracle.density_matrix(inst.H + t * E, inst.n_occ))
+    h = 1e-4
+    fd = (L(h) - L(-h)) / (2 * h)
+    if not abs(fd - np.sum(dLdH * E)) <= 1e-6 * max(1.0, abs(fd)):
+        failed.append("finite differences of Tr[G P]")
+    return failed
+
+
+def test_unmutated_adjoint_passes():
+    assert adj_pins_fail(load_variant(open(SP2_PATH).read(), "adj_copy")) == []
+
+
+@pytest.mark.parametrize("what,old,new", ADJ_MUTATIONS, ids=[m[0] for m in ADJ_MUTATIONS])
+def test_planted_adjoint_mistake_is_caught(what, old, new):
+    src = open(SP2_PATH).read()
+    assert src.count(old) == 1, what
+    assert adj_pins_fail(load_variant(src.replace(old, new), "adj_mutant")), what
+
+
+SCC_MUTATIONS = [
+    ("charges from the wrong diagonal", "q_out = np.diag(P1).copy()", "q_out = -np.diag(P1).copy()"),
+    ("coupling transposed into a row sum",
+     "_, P1 = response_from_eigs(eps, V, H1_ext + np.diag(gamma @ q), n_occ)\n        q_out",
+     "_, P1 = response_from_eigs(eps, V, H1_ext + np.diag(gamma.sum(1) * q), n_occ)\n        q_out"),
+    ("coupling dropped in the final response",
+     "    _, P1 = response_from_eigs(eps, V, H1_ext + np.diag(gamma @ q), n_occ)\n    return",
+     "    _, P1 = response_from_eigs(eps, V, H1_ext, n_occ)\n    return"),
+]
+
+
+def scc_pins_fail(mod):
+    from paper_2203_09621_gb300.workloads import scc_gamma
+    failed = []
+    n = 32
+    inst = make_workload(3, n=n, k=1)
+    g = scc_gamma(n)
+    eps, V = np.linalg.eigh(inst.H)
+    chi = np.stack([np.diag(oracle.response_from_eigs(eps, V, np.diag(np.eye(n)[c]),
+                                                      inst.n_occ)[1]) for c in range(n)], axis=1)
+    q0 = np.diag(oracle.response_from_eigs(eps, V, inst.H1[0], inst.n_occ)[1])
+    q_closed = np.linalg.solve(np.eye(n) - chi @ g, q0)
+    with np.errstate(all="ignore"):
+        P1, q, _ = mod.scc_response(inst.H, inst.H1[0], g, inst.n_occ)
+    # "not <=" so that a non-finite result fails too
+    if not np.linalg.norm(q - q_closed) <= 1e-10 * np.linalg.norm(q_closed):
+        failed.append("closed-form fixed point")
+    if not np.linalg.norm(np.diag(P1) - q_closed) <= 1e-9 * np.linalg.norm(q_closed):
+        failed.append("response at the fixed point")
+    return failed
+
+
+def test_unmutated_scc_passes():
+    assert scc_pins_fail(load_variant(open(SCC_PATH).read(), "scc_copy", SCC_PATH)) == []
+
+
+@pytest.mark.parametrize("what,old,new", SCC_MUTATIONS, ids=[m[0] for m in SCC_MUTATIONS])
+def test_planted_scc_mistake_is_caught(what, old, new):
+    src = open(SCC_PATH).read()
+    assert src.count(old) == 1, what
+    assert scc_pins_fail(load_variant(src.replace(old, new), "scc_mutant", SCC_PATH)), what
