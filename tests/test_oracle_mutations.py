@@ -19,6 +19,8 @@ Sum over states (oracle/sos.py), first and second order:
 Adjoint (oracle/sp2.py, sp2_adjoint): the self-adjoint Daleckii-Krein
 derivative (the forward response with H1 := G, by sum over states) and
 central differences of Tr[G P(H + t E)].
+Gershgorin bounds (oracle/gershgorin.py): the hand-computed 3x3 fixture
+and containment of the spectrum.
 Self-consistent response (oracle/scc.py): the closed-form fixed point
 q = (I - chi gamma)^-1 q0 from the charge susceptibility chi.
 The unmutated modules pass all of them.  Nothing here touches the CUDA
@@ -39,6 +41,7 @@ from paper_2203_09621_gb300.workloads import make_workload
 SP2_PATH = os.path.join(os.path.dirname(oracle.__file__), "sp2.py")
 SOS_PATH = os.path.join(os.path.dirname(oracle.__file__), "sos.py")
 SCC_PATH = os.path.join(os.path.dirname(oracle.__file__), "scc.py")
+GER_PATH = os.path.join(os.path.dirname(oracle.__file__), "gershgorin.py")
 
 MUTATIONS = [
     ("dropped cross term of order o", "for a in range(1, o):", "for a in range(1, max(1, o - 1)):"),
@@ -263,3 +266,38 @@ def test_planted_scc_mistake_is_caught(what, old, new):
     src = open(SCC_PATH).read()
     assert src.count(old) == 1, what
     assert scc_pins_fail(load_variant(src.replace(old, new), "scc_mutant", SCC_PATH)), what
+
+
+GER_MUTATIONS = [
+    ("diagonal kept in the radius", "radius = np.sum(np.abs(H[i, :])) - abs(H[i, i])",
+     "radius = np.sum(np.abs(H[i, :]))"),
+    ("signed radius", "radius = np.sum(np.abs(H[i, :])) - abs(H[i, i])",
+     "radius = np.sum(H[i, :]) - H[i, i]"),
+    ("column of the wrong index", "radius = np.sum(np.abs(H[i, :])) - abs(H[i, i])",
+     "radius = np.sum(np.abs(H[:, 0])) - abs(H[0, 0])"),
+]
+
+
+def ger_pins_fail(mod, golden):
+    from paper_2203_09621_gb300.workloads import sym_gauss
+    failed = []
+    g = golden("gershgorin_3x3.json")
+    if list(mod.gershgorin_bounds(np.array(g["H"]))) != g["bounds"]:
+        failed.append("3x3 fixture")
+    H = sym_gauss(40, 7) + np.diag(np.linspace(-3, 3, 40))
+    lo, hi = mod.gershgorin_bounds(H)
+    ev = np.linalg.eigvalsh(H)
+    if not (lo <= ev[0] and ev[-1] <= hi):
+        failed.append("containment")
+    return failed
+
+
+def test_unmutated_gershgorin_passes(golden):
+    assert ger_pins_fail(load_variant(open(GER_PATH).read(), "ger_copy", GER_PATH), golden) == []
+
+
+@pytest.mark.parametrize("what,old,new", GER_MUTATIONS, ids=[m[0] for m in GER_MUTATIONS])
+def test_planted_gershgorin_mistake_is_caught(golden, what, old, new):
+    src = open(GER_PATH).read()
+    assert src.count(old) == 1, what
+    assert ger_pins_fail(load_variant(src.replace(old, new), "ger_mutant", GER_PATH), golden), what
