@@ -101,6 +101,33 @@ def test_host_only_calls(lib):
     assert lib.dmpt_destroy(None) == 1
 
 
+def test_higher_order_workspace_and_options(lib):
+    """Responses of order m keep m k response slots (m k <= DMPT_MAX_K = 8,
+    m <= DMPT_MAX_ORDER = 8); round_align defaults to 1 and takes 0 or 1."""
+    from paper_2203_09621_gb300 import dmpt
+
+    o = dmpt.DmptOptions()
+    lib.dmpt_default_options(ctypes.byref(o))
+    assert o.round_align == 1 and o.order == 1
+    w = {}
+    for m, k in ((1, 1), (2, 1), (4, 1), (8, 1), (2, 4), (4, 2)):
+        o.order = m
+        w[(m, k)] = lib.dmpt_workspace_size(1000, k, ctypes.byref(o))
+        assert w[(m, k)] > 0, (m, k)
+    assert w[(1, 1)] < w[(2, 1)] < w[(4, 1)] < w[(8, 1)]
+    assert w[(2, 4)] == w[(8, 1)] == w[(4, 2)]      # the same 8 slots
+    for m, k in ((3, 3), (9, 1), (2, 5), (0, 1), (2, 0)):
+        o.order = m
+        assert lib.dmpt_workspace_size(1000, k, ctypes.byref(o)) == 0, (m, k)
+    o.order = 1
+    for v, ok in ((0, True), (1, True), (2, False), (-1, False)):
+        o.round_align = v
+        assert (lib.dmpt_workspace_size(100, 1, ctypes.byref(o)) > 0) == ok, v
+    # null handle
+    assert lib.dmpt_sp2_response_m(None, None, None, 1, 4, 4, 2, 3, None, None, None, None,
+                                   None, None, 0, None) == 1
+
+
 def test_host_pipeline_sizes_and_argument_errors(lib):
     """dmpt_sp2_response_host: the workspace is the solver's plus two input
     and two output buffer sets of (1 + k) n x n float64; argument errors are
