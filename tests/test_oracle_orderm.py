@@ -111,3 +111,18 @@ def test_trivial_occupations_all_orders():
         r = oracle.sp2_pt(inst.H, inst.H1, n_occ, order=3)
         assert r.layers == 0 and len(r.Pk) == 3
         assert all(not p.any() for p in r.Pk)
+
+
+def test_directions_are_independent():
+    """Each direction's terms depend on its own H1 only: a run with the
+    stack [H1_a, H1_b] gives direction a's terms of a run with H1_a alone
+    (the shared S0 recursion is the same, and a converged term stays
+    frozen while the other direction runs on), so a mix-up of directions'
+    slots would show."""
+    inst = make_workload(3, n=96, k=2)
+    both = oracle.sp2_pt(inst.H, inst.H1, inst.n_occ, order=3)
+    for j in range(2):
+        alone = oracle.sp2_pt(inst.H, inst.H1[j:j + 1], inst.n_occ, order=3)
+        for o in range(3):
+            assert both.dk_layer[o][j] == alone.dk_layer[o][0]
+            np.testing.assert_array_equal(both.Pk[o][j], alone.Pk[o][0])
