@@ -52,6 +52,12 @@ SP2 run on the 2n x 2n block upper-triangular matrix [[H, H1], [0, H]]
 o >= 2 are pinned by the (m+1)n block matrix with H1 on the block
 superdiagonal, sympy derivatives of the 2x2 projector, finite differences
 of the second-order sum over states, and the identities of each order.
+The stopping rules (Alg. 2 with both clauses, Alg. 3 with C_pt, FroErr^(0)
+and the n - 2 index) are pinned by a hand-worked diagonal case whose values
+are exact dyadic rationals (tests/golden/stopping_rules_dyadic.json): the
+branch sequence, every IdErr_n, the layer where the second clause of Alg. 2
+fires, FroErr^(0), the FroErr^(1) history and the layer where Alg. 3 fires,
+for three settings of the two constants.
 """
 
 from dataclasses import dataclass, field

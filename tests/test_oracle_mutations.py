@@ -21,6 +21,9 @@ derivative (the forward response with H1 := G, by sum over states) and
 central differences of Tr[G P(H + t E)].
 Gershgorin bounds (oracle/gershgorin.py): the hand-computed 3x3 fixture
 and containment of the spectrum.
+Stopping rules (oracle/sp2.py, Alg. 2 and Alg. 3): the hand-worked dyadic
+fixture (both clauses of Alg. 2, C_pt, FroErr^(0) and the n - 2 index of
+Alg. 3) and the 2x2 closed form.
 Self-consistent response (oracle/scc.py): the closed-form fixed point
 q = (I - chi gamma)^-1 q0 from the charge susceptibility chi.
 The unmutated modules pass all of them.  Nothing here touches the CUDA
@@ -301,3 +304,72 @@ def test_planted_gershgorin_mistake_is_caught(golden, what, old, new):
     src = open(GER_PATH).read()
     assert src.count(old) == 1, what
     assert ger_pins_fail(load_variant(src.replace(old, new), "ger_mutant", GER_PATH), golden), what
+
+
+# Stopping rules (Alg. 2 and Alg. 3): planted in the SP2 oracle, caught by the
+# hand-worked dyadic fixture (tests/golden/stopping_rules_dyadic.json) and the
+# 2x2 closed form (tests/golden/two_level.json), neither of which runs the
+# mutated rule to obtain its expected values.
+STOP_MUTATIONS = [
+    ("second clause of Alg. 2 removed",
+     "and iderr[n_layer] > c_d0 * iderr[n_layer - 2] ** 2):", "and False):"),
+    ("IdErr_{n-1} in place of IdErr_{n-2}",
+     "c_d0 * iderr[n_layer - 2] ** 2", "c_d0 * iderr[n_layer - 1] ** 2"),
+    ("IdErr_{n-2} not squared", "c_d0 * iderr[n_layer - 2] ** 2", "c_d0 * iderr[n_layer - 2]"),
+    ("first clause of Alg. 2 strict", "if iderr[n_layer] <= 0.0:", "if iderr[n_layer] < 0.0:"),
+    ("C_pt dropped from Alg. 3", "fe >= c_pt * froerr0 * prev", "fe >= froerr0 * prev"),
+    ("FroErr^(0) dropped from Alg. 3", "fe >= c_pt * froerr0 * prev", "fe >= c_pt * prev"),
+    ("FroErr^(1)_{n-1} in place of FroErr^(1)_{n-2}",
+     "prev = froerr[o][j].get(n_layer - 2)", "prev = froerr[o][j].get(n_layer - 1)"),
+    ("strict comparison in Alg. 3 (never fires at exact zero)",
+     "fe >= c_pt * froerr0 * prev", "fe > c_pt * froerr0 * prev"),
+    ("FroErr^(0) of the updated state", 'froerr0 = np.linalg.norm(S0 - X0, "fro")',
+     'froerr0 = np.linalg.norm(X0 - X0 @ X0, "fro")'),
+    ("no sigma flip after D^(0) converged", "sigma[n_layer] = -sigma[n_layer - 1]",
+     "sigma[n_layer] = sigma[n_layer - 1]"),
+]
+
+
+def stop_pins_fail(mod, golden):
+    from fractions import Fraction
+    failed = []
+    g = golden("stopping_rules_dyadic.json")
+    H = np.diag(np.array(g["H_diag"]))
+    H1 = np.zeros_like(H)
+    for i, j in g["H1_offdiag"]["pairs"]:
+        H1[i, j] = H1[j, i] = g["H1_offdiag"]["value"]
+    try:
+        r = mod.sp2_pt(H, H1, g["n_occ"], c_pt=g["c_pt"], c_d0=g["c_d0"], max_layers=30)
+        if r.d0_layer != g["d0_layer"]:
+            failed.append("dyadic: D0 layer")
+        if r.iderr != [float(Fraction(s)) for s in g["iderr"]]:
+            failed.append("dyadic: IdErr history")
+        if not abs(r.froerr0 - float(Fraction(g["froerr0_sq"])) ** 0.5) <= 1e-14 * r.froerr0:
+            failed.append("dyadic: FroErr0")
+        if r.d1_layer != [g["d1_layer"]] or not r.converged:
+            failed.append("dyadic: D1 layer")
+        if r.sigma != g["sigma"][: len(r.sigma)]:
+            failed.append("dyadic: sigma")
+        for v in g["variants"]:
+            rv = mod.sp2_pt(H, H1, g["n_occ"], c_pt=v["c_pt"], c_d0=v["c_d0"], max_layers=30)
+            if rv.d0_layer != v["d0_layer"] or ("d1_layer" in v and rv.d1_layer != [v["d1_layer"]]):
+                failed.append(f"dyadic variant c_pt={v['c_pt']} c_d0={v['c_d0']}")
+        t = golden("two_level.json")
+        rt = mod.sp2_pt(np.array(t["H"]), np.array(t["H1"]), t["n_occ"], max_layers=30)
+        if not rt.converged or rt.d0_layer != t["d0_layer"] or \
+                not np.abs(rt.P1[0] - np.array(t["P1"])).max() <= 1e-15:
+            failed.append("2x2 closed form")
+    except Exception as e:
+        failed.append(f"raised {type(e).__name__}")
+    return failed
+
+
+def test_unmutated_stopping_rules_pass(golden):
+    assert stop_pins_fail(load_variant(open(SP2_PATH).read(), "stop_copy"), golden) == []
+
+
+@pytest.mark.parametrize("what,old,new", STOP_MUTATIONS, ids=[m[0] for m in STOP_MUTATIONS])
+def test_planted_stopping_mistake_is_caught(golden, what, old, new):
+    src = open(SP2_PATH).read()
+    assert src.count(old) == 1, what
+    assert stop_pins_fail(load_variant(src.replace(old, new), "stop_mutant"), golden), what

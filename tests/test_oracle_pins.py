@@ -246,3 +246,59 @@ def test_adjoint_matches_response_and_fd():
     h = 1e-4
     fd = (L(h) - L(-h)) / (2 * h)
     assert abs(fd - np.sum(dLdH * E)) < 1e-6 * max(1.0, abs(fd))
+
+
+# --------------------------------------------------------------------------
+# Stopping rules (Alg. 2 second clause, Alg. 3 / Eq. (ConvCrit)): a
+# hand-worked diagonal case whose values are exact dyadic rationals
+
+def stopping_fixture(g):
+    from fractions import Fraction
+    H = np.diag(np.array(g["H_diag"]))
+    n = H.shape[0]
+    H1 = np.zeros((n, n))
+    for i, j in g["H1_offdiag"]["pairs"]:
+        H1[i, j] = H1[j, i] = g["H1_offdiag"]["value"]
+    return H, H1, Fraction
+
+
+def test_stopping_rules_golden(golden):
+    g = golden("stopping_rules_dyadic.json")
+    H, H1, Fraction = stopping_fixture(g)
+    r = oracle.sp2_pt(H, H1, g["n_occ"], c_pt=g["c_pt"], c_d0=g["c_d0"], max_layers=30)
+    assert r.bounds == tuple(g["bounds"])
+    assert r.converged
+    # Alg. 2: branch sequence, exact idempotency errors, the second clause at layer 4
+    assert r.d0_layer == g["d0_layer"]
+    assert r.sigma == g["sigma"]
+    want_iderr = [float(Fraction(s)) for s in g["iderr"]]
+    assert r.iderr == want_iderr          # exact: every value is a short dyadic rational
+    assert r.iderr[-1] > 0.0              # fired by the second clause, not by IdErr <= 0
+    assert r.froerr0 == pytest.approx(float(Fraction(g["froerr0_sq"])) ** 0.5, rel=1e-14)
+    # Alg. 3: FroErr^(1) history from the D^(0) layer on and the layer where it fires
+    for layer, want in g["froerr1"].items():
+        assert r.froerr1[0][int(layer) - 1] == pytest.approx(want, rel=1e-10)
+    assert all(np.isnan(r.froerr1[0][m - 1]) for m in range(1, g["d0_layer"]))
+    assert r.d1_layer == [g["d1_layer"]]
+    assert r.layers == g["d1_layer"]
+
+
+@pytest.mark.parametrize("variant", range(3))
+def test_stopping_rules_golden_variants(golden, variant):
+    g = golden("stopping_rules_dyadic.json")
+    v = g["variants"][variant]
+    H, H1, _ = stopping_fixture(g)
+    r = oracle.sp2_pt(H, H1, g["n_occ"], c_pt=v["c_pt"], c_d0=v["c_d0"], max_layers=30)
+    assert r.d0_layer == v["d0_layer"]
+    if "d1_layer" in v:
+        assert r.converged == v["converged"]
+        assert r.d1_layer == [v["d1_layer"]]
+        if not v["converged"]:
+            assert r.layers == 30
+
+
+def test_stopping_rule_constants_default_to_the_paper():
+    import inspect
+    sig = inspect.signature(oracle.sp2_pt)
+    assert sig.parameters["c_pt"].default == 9.0    # Eq. (ConvCrit), Alg. 3
+    assert sig.parameters["c_d0"].default == 4.5    # Alg. 2
