@@ -45,6 +45,7 @@ extern "C" {
 #define DMPT_MAX_K 8        /* response slots per call: directions x order */
 #define DMPT_MAX_ORDER 8    /* highest response order (k = 1)             */
 #define DMPT_MAX_LAYERS 256 /* upper bound of dmpt_options.max_layers      */
+#define DMPT_MAX_TIMEOUT_S 600.0 /* upper bound of dmpt_options.timeout_s  */
 
 typedef enum {
   DMPT_OK = 0,
@@ -83,7 +84,8 @@ typedef struct {
                            state (default 4)                                  */
   int timing;           /* 1: time every layer-product launch with CUDA events
                            on `stream` and report it in dmpt_info             */
-  double timeout_s;     /* limit of any device-side spin wait (default 2.0)   */
+  double timeout_s;     /* limit of any device-side spin wait, in seconds,
+                           0 < timeout_s <= DMPT_MAX_TIMEOUT_S (default 2.0)  */
   int ckpt_every;       /* 1: keep the 16-bit copies of every S0 layer state in
                            the workspace (dual forms) for dmpt_sp2_backward;
                            0: none (default)                                  */
@@ -138,6 +140,20 @@ typedef struct {
                                         D0 layer, 3K 2n^3 per D1-only layer
                                         (Eq. (flop rate formula), 2/FMA)     */
   signed char sigma[DMPT_MAX_LAYERS];/* sigma_1..sigma_layers                */
+  /* Per-layer histories of the quantities the stopping rules test (entry
+   * n - 1 holds layer n; 0 where a quantity was not formed at that layer),
+   * so that a caller can re-check every decision against Alg. 1-3:
+   *   n_s, n_x, iderr  layers 1 .. d0_layer: N_S = Tr S_{n-1}, N_X =
+   *                    Tr S_{n-1}^2 (as ||S_{n-1}||_F^2) and IdErr_n =
+   *                    N_S - N_X of Alg. 2, in FP64, as the device used them;
+   *   froerr1_hist     per response slot, the FroErr^(1)_n of Alg. 3 at each
+   *                    layer 1 .. d1_layer[j] (1 .. layers when the slot did
+   *                    not converge) at which the response ran; the test of
+   *                    Alg. 3 reads it from d0_layer on. */
+  double n_s[DMPT_MAX_LAYERS];
+  double n_x[DMPT_MAX_LAYERS];
+  double iderr[DMPT_MAX_LAYERS];
+  double froerr1_hist[DMPT_MAX_K][DMPT_MAX_LAYERS];
 } dmpt_info;
 
 typedef struct dmpt_ctx* dmpt_handle;
@@ -375,10 +391,16 @@ dmpt_status dmpt_autotune(dmpt_handle h, const double* H, const double* H1, int 
  *   scratch comes from one fixed device array of DMPT_STATIC_SCRATCH_BYTES
  *   inside the library, resident on every GPU that loads it until exit.
  *   Limits: n <= DMPT_STATIC_MAX_N, k <= DMPT_STATIC_MAX_K; larger sizes
- *   return DMPT_EINVAL with a message on stderr.  o->timing = 1 returns
- *   DMPT_EUNSUPPORTED (timing creates CUDA events).
+ *   return DMPT_EINVAL.  o->timing = 1 and o->autotune = 1 return
+ *   DMPT_EUNSUPPORTED (both create CUDA events; tuning also runs probe
+ *   solves), and so does o->ckpt_every = 1: this call keeps no S0 tape, so
+ *   dmpt_sp2_backward and dmpt_response_replay cannot follow it.  Every
+ *   refusal sets info->status (info is cleared on entry), the handle's
+ *   dmpt_last_error text and a line on stderr.
  *   The first call on a device looks up the array's device address (with
- *   that device current); make that first call before any stream capture.
+ *   that device current), and looks it up again when the device's context
+ *   has been replaced (e.g. after cudaDeviceReset); make that first call
+ *   before any stream capture.
  *   All calls share the array and it keeps the last call's contents; calls
  *   that overlap on the GPU race on it and must be serialised by the caller.
  *   Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */

@@ -71,12 +71,31 @@ struct DeviceGuard {
   }
 };
 
+// Per-layer histories of the stopping quantities of a finished run (entry
+// n - 1 holds layer n): N_S, N_X and IdErr of Alg. 2 up to the D0 layer, and
+// FroErr^(1) of Alg. 3 for each of `slots` response slots up to the layer
+// whose test fired (`last_layer` for a slot that did not converge).
+void fill_history(dmpt_info* info, const State& S, int slots, int last_layer) {
+  const int d0 = S.d0_layer > 0 ? S.d0_layer : last_layer;
+  for (int m = 1; m <= d0 && m <= DMPT_MAX_LAYERS; ++m) {
+    info->n_s[m - 1] = S.ns_hist[m];
+    info->n_x[m - 1] = S.nx_hist[m];
+    info->iderr[m - 1] = S.iderr[m];
+  }
+  for (int j = 0; j < slots && j < DMPT_MAX_K; ++j) {
+    const int last = S.d1_conv[j] ? S.d1_layer[j] : last_layer;
+    for (int m = 1; m <= last && m <= DMPT_MAX_LAYERS; ++m)
+      info->froerr1_hist[j][m - 1] = S.froerr1[j][m];
+  }
+}
+
 bool valid_options(const dmpt_options* o) {
   if (o->precision < DMPT_FP64 || o->precision > DMPT_DUAL_BF16) return false;
   if (o->max_layers < 1 || o->max_layers > DMPT_MAX_LAYERS) return false;
   if (!(o->c_pt > 0.0) || !(o->c_d0 > 0.0)) return false;
   if (o->sync_every < 1) return false;
-  if (!(o->timeout_s > 0.0)) return false;
+  // finite and capped: the device waits convert it to nanoseconds in 64 bits
+  if (!(o->timeout_s > 0.0) || !(o->timeout_s <= DMPT_MAX_TIMEOUT_S)) return false;
   if (o->ckpt_every < 0 || o->ckpt_every > 1) return false;
   if (o->accum_chunk < 0) return false;
   if (o->cta_pair < 0 || o->cta_pair > 1) return false;
@@ -230,6 +249,7 @@ dmpt_status replay_run(dmpt_handle h, const Layout& L, const double* H1, const d
     info->froerr0 = hs->froerr0;
     info->product_launches = launched;
     for (int m = 1; m <= hs->rp_layers && m <= DMPT_MAX_LAYERS; ++m) info->sigma[m - 1] = hs->sigma[m];
+    fill_history(info, *hs, k, hs->rp_layers);
   }
   delete hs;
   if (status != DMPT_OK) return fail(h, status, "response replay: device status %s", "");
@@ -267,6 +287,11 @@ double layer_mma_flops(const Layout& L, double per /* one full-K single-term pas
 
 namespace dmpt {
 int handle_device(dmpt_handle h) { return h ? h->device : -1; }
+
+dmpt_status report(dmpt_handle h, dmpt_status s, const char* msg) {
+  if (h) snprintf(h->err, sizeof(h->err), "%s", msg);
+  return s;
+}
 }  // namespace dmpt
 
 extern "C" {
@@ -495,6 +520,7 @@ static dmpt_status forward_impl(dmpt_handle h, const double* H, const double* H1
     info->eps_max = S.epsN;
     info->froerr0 = S.froerr0;
     for (int m = 1; m <= S.layers_run && m <= DMPT_MAX_LAYERS; ++m) info->sigma[m - 1] = S.sigma[m];
+    fill_history(info, S, kj, S.layers_run);
     info->product_launches = launched;
     double mma = 0.0, alg = 0.0;
     for (int m = 1; m <= S.layers_run; ++m) {
@@ -1103,6 +1129,7 @@ static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
       }
       I.alg_flops = alg;
       for (int m = 1; m <= S.layers_run && m <= DMPT_MAX_LAYERS; ++m) I.sigma[m - 1] = S.sigma[m];
+      fill_history(&I, S, k, S.layers_run);
     }
   }
   // the caller's stream continues after the batch

@@ -75,6 +75,8 @@ struct State {
   double froerr0;
   double s1_fro2[kMaxK];   // ||S1_k||_F^2 of the current S1_k
   double iderr[kMaxL + 2];
+  double ns_hist[kMaxL + 2];   // N_S of each D0 layer (Alg. 2)
+  double nx_hist[kMaxL + 2];   // N_X of each D0 layer
   double froerr1[kMaxK][kMaxL + 2];
   signed char sigma[kMaxL + 2];
 };
@@ -202,6 +204,8 @@ cudaError_t launch_batch_all_done(const void* base, const long long* offs, int c
 
 // CUDA device of a handle (-1 for NULL).
 int handle_device(dmpt_handle h);
+// Store `msg` as the handle's last error text (dmpt_last_error) and return s.
+dmpt_status report(dmpt_handle h, dmpt_status s, const char* msg);
 
 // State-dependent exponent for the 16-bit copies of S1: chosen so that a
 // bound of the largest element maps to <= 2^14 (FP16 max is 65504).

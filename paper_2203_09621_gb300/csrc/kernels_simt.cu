@@ -372,6 +372,8 @@ __device__ void plan_layer(State* st, int n) {
     const double arg = fabs(2.0 * NS - NX - no) - fabs(NX - no);
     sigma = arg > 0.0 ? 1 : -1;
     st->iderr[n] = iderr;
+    st->ns_hist[n] = NS;
+    st->nx_hist[n] = NX;
     st->sigma[n] = (signed char)sigma;
     bool stop = iderr <= 0.0;
     if (!stop && n > 2 && st->sigma[n - 1] != st->sigma[n - 2] &&

@@ -65,6 +65,10 @@ class DmptInfo(ctypes.Structure):
         ("mma_flops", ctypes.c_double),
         ("alg_flops", ctypes.c_double),
         ("sigma", ctypes.c_byte * DMPT_MAX_LAYERS),
+        ("n_s", ctypes.c_double * DMPT_MAX_LAYERS),
+        ("n_x", ctypes.c_double * DMPT_MAX_LAYERS),
+        ("iderr", ctypes.c_double * DMPT_MAX_LAYERS),
+        ("froerr1_hist", (ctypes.c_double * DMPT_MAX_LAYERS) * DMPT_MAX_K),
     ]
 
 
@@ -169,16 +173,25 @@ class Info:
     mma_flops: float
     alg_flops: float
     sigma: list
+    # per-layer stopping quantities (index n - 1 = layer n): N_S, N_X, IdErr of
+    # Alg. 2 up to d0_layer; FroErr^(1) of Alg. 3 per slot up to `layers`
+    n_s: list = None
+    n_x: list = None
+    iderr: list = None
+    froerr1_hist: list = None
 
     @classmethod
     def from_c(cls, ci: DmptInfo, k: int) -> "Info":
+        d0 = ci.d0_layer if ci.d0_layer > 0 else ci.layers
         return cls(status=ci.status, layers=ci.layers, d0_layer=ci.d0_layer,
                    converged=bool(ci.converged), d1_layer=list(ci.d1_layer[:k]),
                    eps_min=ci.eps_min, eps_max=ci.eps_max, froerr0=ci.froerr0,
                    froerr1=list(ci.froerr1[:k]), ms_layers=ci.ms_layers,
                    product_launches=ci.product_launches, timed_launches=ci.timed_launches,
                    mma_flops=ci.mma_flops, alg_flops=ci.alg_flops,
-                   sigma=list(ci.sigma[:ci.layers]))
+                   sigma=list(ci.sigma[:ci.layers]), n_s=list(ci.n_s[:d0]),
+                   n_x=list(ci.n_x[:d0]), iderr=list(ci.iderr[:d0]),
+                   froerr1_hist=[list(ci.froerr1_hist[j][:ci.layers]) for j in range(k)])
 
 
 def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_scaling=1,

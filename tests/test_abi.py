@@ -177,3 +177,31 @@ def test_c_caller_builds_and_reports_missing_gpu(lib, tmp_path):
     r = subprocess.run([exe, "4", "2", "1", str(src), str(tmp_path / "out.bin")],
                        capture_output=True, text=True, timeout=60)
     assert r.returncode == 1 and "dmpt_create" in r.stderr, (r.returncode, r.stderr)
+
+
+def test_timeout_must_be_finite_and_capped(lib):
+    """timeout_s bounds every device-side wait; it is converted to
+    nanoseconds in 64 bits on the device, so inf, NaN and values above
+    DMPT_MAX_TIMEOUT_S are rejected before any launch."""
+    from paper_2203_09621_gb300 import dmpt
+
+    text = open(HEADER).read()
+    cap = float(re.search(r"#define DMPT_MAX_TIMEOUT_S ([0-9.]+)", text).group(1))
+    o = dmpt.DmptOptions()
+    lib.dmpt_default_options(ctypes.byref(o))
+    for v, ok in ((2.0, True), (cap, True), (1e-3, True), (cap * 1.01, False),
+                  (float("inf"), False), (float("nan"), False), (1.8e10, False), (0.0, False),
+                  (-1.0, False)):
+        o.timeout_s = v
+        assert (lib.dmpt_workspace_size(100, 1, ctypes.byref(o)) > 0) == ok, v
+
+
+def test_info_carries_stopping_histories():
+    """dmpt_info exposes the per-layer quantities the stopping rules test, so
+    a caller can re-check each decision (Alg. 1-3)."""
+    from paper_2203_09621_gb300 import dmpt
+
+    names = [f[0] for f in dmpt.DmptInfo._fields_]
+    for f in ("n_s", "n_x", "iderr", "froerr1_hist"):
+        assert f in names
+    assert dmpt.DmptInfo.froerr1_hist.size == 8 * dmpt.DMPT_MAX_K * dmpt.DMPT_MAX_LAYERS
