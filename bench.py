@@ -143,6 +143,60 @@ class ClockSampler:
                 "power_w": pw_sorted[len(pw_sorted) // 2] if pw_sorted else None}
 
 
+def measure_matmul_peaks(n, dev, dtype_name, sustained_s=4.0, best_of=10):
+    """torch.matmul n^3 (2 n^3 flops) in `dtype_name`: best of `best_of` single
+    products (burst) and the mean rate of back-to-back products for about
+    `sustained_s` seconds (sustained, under the power cap)."""
+    import torch
+    dt = {"fp16": torch.float16, "bf16": torch.bfloat16, "fp64": torch.float64}[dtype_name]
+    a = torch.randn(n, n, device=dev).to(dt)
+    b = torch.randn(n, n, device=dev).to(dt)
+    for _ in range(3):
+        torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(best_of):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    flops = 2.0 * n ** 3
+    out = {"burst_tflops": flops / (best * 1e-3) / 1e12}
+    if sustained_s > 0:
+        reps = max(1, int(sustained_s / (best * 1e-3)))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        out["sustained_tflops"] = reps * flops / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        out["sustained_reps"] = reps
+    out["how"] = (f"torch.matmul {dtype_name} {n}^3 (2 n^3 flops): best of {best_of} (burst)"
+                  + (f", {out.get('sustained_reps')} back to back (sustained)" if sustained_s > 0 else ""))
+    del a, b
+    return out
+
+
+def measure_copy_bandwidth(host, dev_t, stream):
+    """Pinned host <-> device copy rates (GB/s) of one tensor each way."""
+    import torch
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    dev_t.copy_(host, non_blocking=True)
+    host.copy_(dev_t, non_blocking=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    dev_t.copy_(host, non_blocking=True)
+    e1.record(stream)
+    host.copy_(dev_t, non_blocking=True)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    nb = host.numel() * host.element_size()
+    return nb / (e0.elapsed_time(e1) * 1e-3) / 1e9, nb / (e1.elapsed_time(e2) * 1e-3) / 1e9
+
+
 INPUT_BACKEND = "torch"
 
 
@@ -169,6 +223,45 @@ def oracle_sample(inst_cpu_H, inst_cpu_H1, n_occ, layers):
     t = time.perf_counter()
     oracle.sp2_pt(inst_cpu_H, inst_cpu_H1, n_occ, max_layers=layers)
     return time.perf_counter() - t
+
+
+_ONE_CORE_SNIPPET = """
+import sys, time
+sys.path.insert(0, {root!r})
+import oracle
+from paper_2203_09621_gb300.workloads import make_workload
+inst = make_workload(3, n={n}, k={k})
+t = time.perf_counter()
+oracle.sp2_pt(inst.H, inst.H1, inst.n_occ, max_layers=1)
+print(time.perf_counter() - t)
+"""
+
+
+def cpu_oracle_extra(k, n_small=2048):
+    """The oracle on one host core (a child process with the BLAS thread pools
+    set to 1) on one layer at n = n_small, and the sum-over-states oracle
+    (eigh + Daleckii-Krein transforms) on all cores at the same size."""
+    import numpy as np
+    import oracle
+    from paper_2203_09621_gb300.workloads import make_workload
+    out = {}
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", _ONE_CORE_SNIPPET.format(root=ROOT, n=n_small, k=k)],
+                           capture_output=True, text=True, env=env, timeout=300)
+        t1 = float(r.stdout.strip().splitlines()[-1])
+        out["one_core"] = {"value": alg_flops_layers(n_small, k, 1) / t1 / 1e12, "unit": "TFLOP/s",
+                           "cores": 1, "sample": f"first layer of Alg. 1-3 at n={n_small}, k={k} "
+                                                 f"({t1:.1f} s)"}
+    except (subprocess.SubprocessError, ValueError, IndexError) as e:
+        out["one_core"] = {"unavailable": f"{type(e).__name__}"}
+    inst = make_workload(3, n=n_small, k=k)
+    t = time.perf_counter()
+    oracle.response_sos(inst.H, inst.H1, inst.n_occ)
+    t = time.perf_counter() - t
+    out["sum_over_states"] = {"seconds": t, "cores": cpu_cores(),
+                              "sample": f"eigh + {k} Daleckii-Krein transforms at n={n_small}"}
+    return out
 
 
 def alg_flops_layers(n, k, layers):
@@ -271,10 +364,15 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--k", type=int, default=K_DEFAULT)
     ap.add_argument("--precision", default="dual_fp16")
-    ap.add_argument("--forms", default="fp32,fp64",
-                    help="extra precision forms timed once (comma list); fp64 on a bounded sample")
+    ap.add_argument("--forms", default="fp32,dual_bf16,fp64",
+                    help="extra precision forms timed once to convergence (comma list); fp64 on "
+                         "a bounded sample unless --fp64-full")
     ap.add_argument("--fp64-layers", type=int, default=2,
                     help="layers of the FP64 form timed (its full solve takes minutes at n = 8192)")
+    ap.add_argument("--fp64-full", action="store_true",
+                    help="run the FP64 form to convergence (about two minutes at n = 8192)")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip measuring the FP16 / FP64 matmul peaks used as denominators")
     ap.add_argument("--oracle-layers", type=int, default=1)
     ap.add_argument("--oracle-n", type=int, default=4096,
                     help="size of the bounded oracle sample (same recipe)")
@@ -368,6 +466,23 @@ def main():
     torch.cuda.synchronize()
     peaks, peak_src = load_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    peak_source = f"{peak_src} bf16_tflops_sustained (FP16 dense = BF16 dense)"
+    measured_peaks = None
+    if not args.no_peaks:
+        # the products run in FP16: measure the dense FP16 rate (cuBLAS through
+        # torch.matmul, 8192^3) as the denominator, sustained like the layer
+        # kernel inside a seconds-long solve; FP64 as context for the FP64 form
+        measured_peaks = {"fp16": measure_matmul_peaks(8192, dev, "fp16"),
+                          "fp64": measure_matmul_peaks(min(n, 8192), dev, "fp64",
+                                                       sustained_s=0.0, best_of=3)}
+        if args.precision == "dual_fp16":
+            peak = measured_peaks["fp16"]["sustained_tflops"]
+            peak_source = ("measured in this run: torch.matmul fp16 8192^3 back to back "
+                           "(sustained); burst (best of 10) in measured_peaks")
+        elif args.precision == "dual_bf16":
+            measured_peaks["bf16"] = measure_matmul_peaks(8192, dev, "bf16")
+            peak = measured_peaks["bf16"]["sustained_tflops"]
+            peak_source = "measured in this run: torch.matmul bf16 8192^3 back to back (sustained)"
     achieved = tinfo.alg_flops / (tinfo.ms_layers * 1e-3) / 1e12 if tinfo.ms_layers else None
     executed = tinfo.mma_flops / (tinfo.ms_layers * 1e-3) / 1e12 if tinfo.ms_layers else None
 
@@ -393,9 +508,16 @@ def main():
     e2e_same = bool(torch.equal(P1e[-1], P1.cpu()))
     h2d = (H.numel() + H1.numel()) * 8
     d2h = P1.numel() * 8
+    # the host link, measured alone: what the copies of one step cost if
+    # nothing overlapped them, against the step's exposed extra time
+    Htmp = torch.empty_like(H)
+    h2d_gbs, d2h_gbs = measure_copy_bandwidth(Hh, Htmp, stream)
+    del Htmp
+    copy_ms_serial = (h2d / (h2d_gbs * 1e9) + d2h / (d2h_gbs * 1e9)) * 1e3
 
     # ---- other precision forms, one timed solve each (time-to-solution)
     forms = {}
+    form_results = {}      # precision -> (P, P1) on the host, for the accuracy check
     for f in [x for x in args.forms.split(",") if x and x != "fp64"]:
         kwf = dict(kw, precision=f)
         ctx.sp2_response(H, H1, inst.n_occ, **kwf)  # warm-up
@@ -407,7 +529,9 @@ def main():
         torch.cuda.synchronize()
         fms = a.elapsed_time(b)
         forms[f] = {"ms": fms, "tflops": fi.alg_flops / (fms * 1e-3) / 1e12,
-                    "layers": fi.layers, "d0_layer": fi.d0_layer}
+                    "layers": fi.layers, "d0_layer": fi.d0_layer, "converged": fi.converged}
+        if not args.no_check and rank == 0:
+            form_results[f] = (P.cpu().numpy(), P1.cpu().numpy())
     if "fp32" in forms:
         # context only: cuBLAS SGEMM (TF32 off) at the same n, one product
         # (2 n^3 flops), beside the SIMT form's per-layer rate
@@ -427,7 +551,21 @@ def main():
         torch.backends.cuda.matmul.allow_tf32 = prev_tf32
         forms["fp32"]["cublas_sgemm_tflops"] = 3 * 2.0 * n ** 3 / (ga.elapsed_time(gb) * 1e-3) / 1e12
         del a32, b32
-    if "fp64" in args.forms.split(",") and args.fp64_layers > 0:
+    if "fp64" in args.forms.split(",") and args.fp64_full:
+        # the FP64 form to convergence (time to solution and accuracy)
+        kwf = dict(kw, precision="fp64")
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, _, fi = ctx.sp2_response(H, H1, inst.n_occ, **kwf)
+        b.record(stream)
+        torch.cuda.synchronize()
+        fms = a.elapsed_time(b)
+        forms["fp64"] = {"ms": fms, "tflops": fi.alg_flops / (fms * 1e-3) / 1e12,
+                         "layers": fi.layers, "d0_layer": fi.d0_layer,
+                         "converged": fi.converged, "sample": "full solve"}
+        if not args.no_check and rank == 0:
+            form_results["fp64"] = (P.cpu().numpy(), P1.cpu().numpy())
+    elif "fp64" in args.forms.split(",") and args.fp64_layers > 0:
         # bounded sample: the first layers of the FP64 form (each a full D0
         # layer), per-launch times by CUDA events; the time to solution is
         # extrapolated to the dual form's layer count
@@ -438,8 +576,10 @@ def main():
         lay = infos[0].layers
         forms["fp64"] = {"ms_per_layer": per_layer, "layers_timed": fi.timed_launches,
                          "tflops": fi.alg_flops / (fi.ms_layers * 1e-3) / 1e12 if fi.ms_layers else None,
-                         "extrapolated_ms": per_layer * lay, "extrapolated_to_layers": lay,
-                         "sample": f"first {fi.timed_launches} layer(s) of the FP64 form at n={n}, k={k}"}
+                         "estimated_ms": per_layer * lay, "estimated_for_layers": lay,
+                         "sample": f"first {fi.timed_launches} layer(s) of the FP64 form at n={n}, "
+                                   f"k={k}; estimated_ms = time per layer x the dual form's layer "
+                                   f"count (an estimate, not a measured solve)"}
     # restore the dual-FP16 result in P1 for the accuracy check
     _, _, info = ctx.sp2_response(H, H1, inst.n_occ, **kw)
     torch.cuda.synchronize()
@@ -510,55 +650,79 @@ def main():
         batch["autotuned_ms"] = b0.elapsed_time(b1)
         del binst, bH, bH1
 
-    # ---- adjoint (L = Tr[G P]): n = 4096 forward with the S0 tape + backward
+    # ---- adjoint (L = Tr[G P]): n = 4096 forward keeping the S0 states, then
+    #      the backward; with the full tape (ckpt_every = 1) and with a
+    #      checkpoint every 8 states (ckpt_every = 8, segments recomputed)
     adjoint = None
     if not args.no_adjoint and rank == 0:
         from paper_2203_09621_gb300.workloads import make_workload
         a_inst = make_workload(4, backend="torch", device=dev)
         Ga = a_inst.H1[0]
-        aopts = dmpt.options(precision=args.precision, ckpt_every=1)
-        aws = torch.empty(ctx.workspace_size(a_inst.n, 0, aopts) + 256, dtype=torch.uint8,
-                          device=dev)
-        for _ in range(2):  # warm-up
-            ctx.sp2_response(a_inst.H, None, a_inst.n_occ, precision=args.precision,
-                             ckpt_every=1, workspace=aws)
-            ctx.sp2_backward(Ga, aws)
-        torch.cuda.synchronize()
-        t0, t1, t2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        t0.record(stream)
-        _, _, ainfo = ctx.sp2_response(a_inst.H, None, a_inst.n_occ, precision=args.precision,
-                                       ckpt_every=1, workspace=aws)
-        t1.record(stream)
-        dLdH = ctx.sp2_backward(Ga, aws)
-        t2.record(stream)
-        torch.cuda.synchronize()
         na = float(a_inst.n)
-        U = ainfo.d0_layer - 1
-        f_fwd = ainfo.alg_flops
-        f_bwd = U * 3 * 2 * na ** 3       # one dual response product per adjoint layer
-        adjoint = {"workload": f"adjoint n={a_inst.n} (L = Tr[G P], G sym-Gauss)",
-                   "forward_ms": t0.elapsed_time(t1), "backward_ms": t1.elapsed_time(t2),
-                   "backward_tflops": f_bwd / (t1.elapsed_time(t2) * 1e-3) / 1e12,
-                   "forward_tflops": f_fwd / (t0.elapsed_time(t1) * 1e-3) / 1e12,
-                   "adjoint_layers": U}
+        P1G = None
         if not args.no_check:
             from oracle.sos import response_from_eigs
             _, P1G = response_from_eigs(a_inst.eps.cpu().numpy(), a_inst.Q.cpu().numpy(),
                                         Ga.cpu().numpy(), a_inst.n_occ)
-            g = dLdH.cpu().numpy()
-            adjoint["rel_err_vs_oracle"] = float(np.linalg.norm(g - P1G) / np.linalg.norm(P1G))
-        del aws, a_inst
+        adjoint = {"workload": f"adjoint n={a_inst.n} (L = Tr[G P], G sym-Gauss)"}
+        for ck in (1, 8):
+            aopts = dmpt.options(precision=args.precision, ckpt_every=ck)
+            ws_bytes = ctx.workspace_size(a_inst.n, 0, aopts)
+            aws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
+            for _ in range(2):  # warm-up
+                ctx.sp2_response(a_inst.H, None, a_inst.n_occ, precision=args.precision,
+                                 ckpt_every=ck, workspace=aws)
+                ctx.sp2_backward(Ga, aws)
+            torch.cuda.synchronize()
+            t0, t1, t2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            t0.record(stream)
+            _, _, ainfo = ctx.sp2_response(a_inst.H, None, a_inst.n_occ,
+                                           precision=args.precision, ckpt_every=ck,
+                                           workspace=aws)
+            t1.record(stream)
+            dLdH = ctx.sp2_backward(Ga, aws)
+            t2.record(stream)
+            torch.cuda.synchronize()
+            U = ainfo.d0_layer - 1
+            f_bwd = U * 3 * 2 * na ** 3       # one dual response product per adjoint layer
+            rec = {"workspace_bytes": ws_bytes,
+                   "state_bytes": (U + 1) * 4 * int(na) ** 2 if ck == 1 else
+                   ((U // ck + 1) * 4 + ck * 4) * int(na) ** 2,
+                   "forward_ms": t0.elapsed_time(t1), "backward_ms": t1.elapsed_time(t2),
+                   "backward_tflops": f_bwd / (t1.elapsed_time(t2) * 1e-3) / 1e12,
+                   "forward_tflops": ainfo.alg_flops / (t0.elapsed_time(t1) * 1e-3) / 1e12,
+                   "adjoint_layers": U,
+                   "recomputed_squares": 0 if ck == 1 else U - (U - 1) // ck - 1}
+            if P1G is not None:
+                g = dLdH.cpu().numpy()
+                rec["rel_err_vs_oracle"] = float(np.linalg.norm(g - P1G) / np.linalg.norm(P1G))
+            adjoint["full_tape" if ck == 1 else f"checkpoint_every_{ck}"] = rec
+            del aws, dLdH
+        del a_inst
 
-    # ---- accuracy against the oracle (sampled columns, known eigenpairs)
-    err = None
+    # ---- accuracy against the oracle: the whole P and every P1_k, from the
+    #      known eigenpairs (outside every timed region)
+    accuracy = None
     if not args.no_check and rank == 0:
+        import oracle
         from oracle.sos import response_columns
-        cols = [0, 1, n // 2 - 1, n // 2, n - 1]
+        t_or = time.perf_counter()
         eps = inst.eps.cpu().numpy()
         Q = inst.Q.cpu().numpy()
-        want = response_columns(eps, Q, H1[0].cpu().numpy(), inst.n_occ, cols)
-        got = P1[0][:, cols].cpu().numpy()
-        err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+        Pr = oracle.density_from_eigs(eps, Q, inst.n_occ)
+        P1r = [response_columns(eps, Q, H1[j].cpu().numpy(), inst.n_occ, np.arange(n))
+               for j in range(k)]
+        t_or = time.perf_counter() - t_or
+
+        def errs(Pg, P1g):
+            return {"rel_err_P": float(np.linalg.norm(Pg - Pr) / np.linalg.norm(Pr)),
+                    "rel_err_P1_max_k": max(float(np.linalg.norm(P1g[j] - P1r[j]) /
+                                                  np.linalg.norm(P1r[j])) for j in range(k))}
+        accuracy = dict(errs(P.cpu().numpy(), P1.cpu().numpy()), precision=args.precision,
+                        norm="relative Frobenius, whole matrices", oracle_s=t_or)
+        for f, (Pg, P1g) in form_results.items():
+            forms[f].update(errs(Pg, P1g))
+        del Pr, P1r, form_results
 
     # ---- CPU baseline: FP64 oracle, first layer(s) of the same workload
     cpu = None
@@ -572,6 +736,7 @@ def main():
                "cores": cpu_cores(), "kind": "oracle",
                "sample": f"first {args.oracle_layers} layer(s) of the FP64 numpy Alg. 1-3 on the "
                          f"same recipe at n={ns}, k={k} ({t:.1f} s)"}
+        cpu.update(cpu_oracle_extra(k))
 
     traffic = recorded_traffic({"n": n, "k": k, "precision": args.precision, "cta_pair": args.cta_pair,
                                 "k_snake": args.k_snake, "tile_band": args.tile_band,
@@ -589,7 +754,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single"},
             "time_to_solution_ms": ms_max,
             "layers": infos[0].layers, "d0_layer": infos[0].d0_layer,
-            "rel_err_P1_sampled": err,
+            "accuracy": accuracy,
             "forms": forms,
             "adjoint": adjoint,
             "batch": batch,
@@ -599,11 +764,14 @@ def main():
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                          "kernel": "layer_tc2_kernel" if args.cta_pair else "layer_tc_kernel",
                          "executed_mma_tflops": executed,
-                         "peak_source": f"{peak_src} bf16_tflops_sustained (FP16 dense = BF16 dense)"},
+                         "peak_source": peak_source},
+            "measured_peaks": measured_peaks,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-                    "api": "dmpt_sp2_response_host", "equals_device_result": e2e_same},
+                    "api": "dmpt_sp2_response_host", "equals_device_result": e2e_same,
+                    "h2d_gbs": h2d_gbs, "d2h_gbs": d2h_gbs, "copy_ms_if_serial": copy_ms_serial,
+                    "exposed_ms_per_step": e2e_ms - ms_max},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
         }

@@ -26,13 +26,14 @@ function's own formula.
 """
 
 from .gershgorin import gershgorin_bounds
-from .sos import density_matrix, response_sos, response_from_eigs
+from .sos import density_matrix, density_from_eigs, response_sos, response_from_eigs
 from .sp2 import sp2_pt, SP2Result, sp2_adjoint
 from .scc import scc_response
 
 __all__ = [
     "gershgorin_bounds",
     "density_matrix",
+    "density_from_eigs",
     "response_sos",
     "response_from_eigs",
     "sp2_pt",

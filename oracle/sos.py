@@ -24,6 +24,11 @@ missing.
 D2 = (1/2) d^2P/dlambda^2 (Eq. (eq:D_k), k = 2) by the second-order
 Daleckii-Krein formula.
 
+``density_from_eigs`` and ``response_columns`` evaluate the same
+definitions from a known eigendecomposition (the synthetic inputs are built
+as H = Q diag(eps) Q^T), the latter from the occupied-virtual block of F
+only, which makes the whole P1 at n = 8192 affordable on the host.
+
 Pinned by: the 2x2 closed form differentiated symbolically
 (tests/golden/two_level.json and the sympy test), the invariants P^2 = P,
 Tr P = n_occ, [H, P] = 0, Tr P1 = 0, P P1 + P1 P = P1,
@@ -44,6 +49,15 @@ def _check_gap(eps, n_occ):
     n = eps.shape[0]
     if 0 < n_occ < n and not eps[n_occ - 1] < eps[n_occ]:
         raise ValueError("degenerate HOMO/LUMO: the response is undefined (Sec. III A)")
+
+
+def density_from_eigs(eps, V, n_occ):
+    """P = V diag(f) V^T from a known eigendecomposition (``eps`` ascending):
+    the projector on the first n_occ columns of V, formed as Vo Vo^T."""
+    eps = np.asarray(eps, dtype=np.float64)
+    _check_gap(eps, n_occ)
+    Vo = np.asarray(V, dtype=np.float64)[:, :n_occ]
+    return Vo @ Vo.T
 
 
 def density_matrix(H, n_occ):

@@ -141,6 +141,14 @@ def test_known_eigs_match_eigh(plain128):
     inst, P, P1, r = plain128
     P_b, P1_b = oracle.response_from_eigs(inst.eps, inst.Q, inst.H1[0], inst.n_occ)
     assert rel(P_b, P) < 1e-12 and rel(P1_b, P1) < 1e-11
+    # the projector from the known eigenvectors: eigh route, and its invariants
+    P_c = oracle.density_from_eigs(inst.eps, inst.Q, inst.n_occ)
+    assert rel(P_c, P) < 1e-12
+    assert abs(np.trace(P_c) - inst.n_occ) < 1e-10
+    assert np.linalg.norm(P_c @ P_c - P_c) < 1e-12 * np.linalg.norm(P_c)
+    # every column of P1 from the occupied-virtual block equals the full transform
+    np.testing.assert_allclose(response_columns(inst.eps, inst.Q, inst.H1[0], inst.n_occ,
+                                                np.arange(inst.n)), P1_b, atol=1e-13)
     cols = [0, 5, 77, 127]
     np.testing.assert_allclose(response_columns(inst.eps, inst.Q, inst.H1[0], inst.n_occ, cols),
                                P1[:, cols], atol=1e-13)
