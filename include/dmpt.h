@@ -86,9 +86,18 @@ typedef struct {
                            on `stream` and report it in dmpt_info             */
   double timeout_s;     /* limit of any device-side spin wait, in seconds,
                            0 < timeout_s <= DMPT_MAX_TIMEOUT_S (default 2.0)  */
-  int ckpt_every;       /* 1: keep the 16-bit copies of every S0 layer state in
-                           the workspace (dual forms) for dmpt_sp2_backward;
-                           0: none (default)                                  */
+  int ckpt_every;       /* S0 states kept in the workspace for the adjoint
+                           (dual forms; dmpt_sp2_backward):
+                           0: none (default);
+                           1: the 16-bit copies of every S0 layer state (the
+                              full tape; also what dmpt_response_replay and
+                              dmpt_scc_response read);
+                           k >= 2 (<= DMPT_MAX_LAYERS): the FP32 master of
+                              every k-th S0 state (a checkpoint) plus the
+                              branch sequence; the backward recomputes each
+                              segment of k states from its checkpoint with
+                              the forward's own layer products before running
+                              its adjoint layers (bit-identical states)       */
   int accum_chunk;      /* dual forms: K elements summed per tensor-memory
                            accumulator before the running sum is carried in
                            FP32 on the CUDA cores (0: default 256)             */
@@ -119,6 +128,17 @@ typedef struct {
                            the tiles of a round share their operand panels in
                            L2; 0 = off, for several solves running at once on
                            one GPU (their CTAs need not all be resident)      */
+  int hole_form;        /* 1 (default): when n_occ > n / 2, run the recursion
+                           on the complement Q = I - P (the n - n_occ highest
+                           levels: S_0 = (H - eps_1 I) / (eps_N - eps_1),
+                           S1_0 = +H1 / (eps_N - eps_1)) and return P = I - Q,
+                           P_o = -Q_o; in exact arithmetic the same layers
+                           with every sigma negated (barring exact ties), but
+                           the 16-bit operands then carry ||I - P||_F =
+                           sqrt(n - n_occ) instead of sqrt(n_occ), which keeps
+                           the rounding of the products small next to the
+                           response when few levels are empty; 0: always the
+                           recursion on P as printed                         */
 } dmpt_options;
 
 /* Filled on the host by dmpt_sp2_response (when info != NULL). */
@@ -154,6 +174,9 @@ typedef struct {
   double n_x[DMPT_MAX_LAYERS];
   double iderr[DMPT_MAX_LAYERS];
   double froerr1_hist[DMPT_MAX_K][DMPT_MAX_LAYERS];
+  int hole;                          /* 1: the run used the complement form
+                                        (hole_form); sigma, N_S and N_X are
+                                        then those of the recursion on I - P */
 } dmpt_info;
 
 typedef struct dmpt_ctx* dmpt_handle;
@@ -251,7 +274,7 @@ dmpt_status dmpt_sp2_response_m(dmpt_handle h, const double* H, const double* H1
 
 /* Adjoint of the S0 recursion: the gradient of L = Tr[G P] with respect to H
  * for the P of the preceding dmpt_sp2_response call that used `workspace`
- * with o->ckpt_every = 1 and a dual precision.  The paper has no backward
+ * with o->ckpt_every >= 1 and a dual precision.  The paper has no backward
  * pass; this is the reverse mode of its layer map (Sec. II B, Eq. (eq:Sn)):
  *   Gbar_U = (G + G^T)/2,
  *   Gbar_{m-1} = sigma_m (S_{m-1} Gbar_m + Gbar_m S_{m-1}) + (1 - sigma_m) Gbar_m
@@ -264,8 +287,15 @@ dmpt_status dmpt_sp2_response_m(dmpt_handle h, const double* H, const double* H1
  *   G      device n x n (ld), float64 (need not be symmetric).
  *   o      options for the products (precision is taken from the forward).
  *   dLdH   device n x n (ld) output, float64, symmetric.
- * The forward's response slots are reused as scratch; the S0 tape is left
- * intact, so several backward calls may follow one forward call.  Returns
+ * With checkpoints (ckpt_every = k >= 2) the states S_{ck} .. S_{ck+k-1} of
+ * each segment, newest segment first, are recomputed from the stored S_{ck}
+ * by the forward's square products (its branch choices, its 16-bit copies,
+ * its product options) into a k-state buffer, and the segment's adjoint
+ * layers run on them: about U extra squares for a tape of U / k + k states
+ * instead of U + 1.
+ * The forward's response slots are reused as scratch; the S0 tape (or the
+ * checkpoints) is left intact, so several backward calls may follow one
+ * forward call.  Returns
  * DMPT_EINVAL when the workspace holds no tape of a converged forward run of
  * this n.  Synchronises `stream` once at entry (to read the forward state)
  * and once at exit. */

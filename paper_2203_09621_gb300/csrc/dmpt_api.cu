@@ -89,6 +89,11 @@ void fill_history(dmpt_info* info, const State& S, int slots, int last_layer) {
   }
 }
 
+// The complement form (dmpt_options::hole_form) for more occupied than empty levels.
+int use_hole_form(const dmpt_options* o, int64_t n, int64_t n_occ) {
+  return (o->hole_form == 1 && 2 * n_occ > n) ? 1 : 0;
+}
+
 bool valid_options(const dmpt_options* o) {
   if (o->precision < DMPT_FP64 || o->precision > DMPT_DUAL_BF16) return false;
   if (o->max_layers < 1 || o->max_layers > DMPT_MAX_LAYERS) return false;
@@ -96,7 +101,7 @@ bool valid_options(const dmpt_options* o) {
   if (o->sync_every < 1) return false;
   // finite and capped: the device waits convert it to nanoseconds in 64 bits
   if (!(o->timeout_s > 0.0) || !(o->timeout_s <= DMPT_MAX_TIMEOUT_S)) return false;
-  if (o->ckpt_every < 0 || o->ckpt_every > 1) return false;
+  if (o->ckpt_every < 0 || o->ckpt_every > DMPT_MAX_LAYERS) return false;
   if (o->accum_chunk < 0) return false;
   if (o->cta_pair < 0 || o->cta_pair > 1) return false;
   if (o->k_snake < 0 || o->k_snake > 1) return false;
@@ -105,21 +110,44 @@ bool valid_options(const dmpt_options* o) {
   if (o->inject_stall < 0 || o->inject_stall > 1) return false;
   if (o->autotune < 0 || o->autotune > 1) return false;
   if (o->round_align < 0 || o->round_align > 1) return false;
+  if (o->hole_form < 0 || o->hole_form > 1) return false;
   return true;
 }
 
 // Workspace geometry for (n, k) under options o: response slots (at least
 // one when S0 states are kept, for the adjoint) and tape capacity.
 Layout layout_for(int64_t n, int k, const dmpt_options* o) {
-  const bool tape = o->ckpt_every == 1;
-  const int slots = o->order >= 2 ? o->order * k : ((tape && k == 0) ? 1 : k);
-  return make_layout(n, slots, o->precision, tape ? o->max_layers + 2 : 0);
+  const int ck = o->ckpt_every;
+  const int slots = o->order >= 2 ? o->order * k : ((ck >= 1 && k == 0) ? 1 : k);
+  // ck = 1: every S0 state's 16-bit copies; ck >= 2: FP32 checkpoints of every
+  // ck-th state plus a ck-state tape for the segment the backward recomputes
+  const int tape_states = ck == 1 ? o->max_layers + 2 : (ck >= 2 ? ck : 0);
+  const int ckpt_slots = ck >= 2 ? o->max_layers / ck + 1 : 0;
+  return make_layout(n, slots, o->precision, tape_states, ckpt_slots);
 }
+
+// The forward's product options, kept for the states the backward recomputes.
+struct FwdOpts {
+  int ckpt_k, ckpt_slots, chunk, cta_pair, k_snake, band;
+};
 
 __global__ void state_init_kernel(State* st, int k, int max_layers, int precision, double n_occ,
                                   double c_pt, double c_d0, int tape, int tape_base,
                                   int tape_states, int layout_k, int64_t n, int order = 1,
-                                  int k1 = 0) {
+                                  int k1 = 0, FwdOpts fo = FwdOpts{0, 0, 0, 1, 1, 8},
+                                  int hole = 0) {
+  // complement form: the recursion converges to I - P, whose occupied levels
+  // are the n - n_occ highest ones
+  st->hole = hole;
+  if (hole) n_occ = (double)n - n_occ;
+  st->ckpt_k = fo.ckpt_k;
+  st->ckpt_slots = fo.ckpt_slots;
+  st->ckpt_pending = 0;
+  st->adj_seg_a = 0;
+  st->fwd_chunk = fo.chunk;
+  st->fwd_cta_pair = fo.cta_pair;
+  st->fwd_k_snake = fo.k_snake;
+  st->fwd_band = fo.band;
   st->order = order;
   st->k1 = order >= 2 ? k1 : k;
   st->tape = tape;
@@ -147,6 +175,7 @@ __global__ void state_init_kernel(State* st, int k, int max_layers, int precisio
 // Re-open a finished forward state for the adjoint run (keeps sigma, the
 // bounds, the tape geometry and the number of S0 updates).
 __global__ void adj_state_reset_kernel(State* st) {
+  st->adj_seg_a = 0;
   st->done = 0;
   st->status = DMPT_OK;
   st->timeout_flag = 0;
@@ -175,7 +204,7 @@ dmpt_status read_forward_state(dmpt_handle h, void* workspace, size_t ws_bytes, 
                 "%s: the workspace holds no S0 tape of a dual-precision forward run of this n "
                 "(run dmpt_sp2_response with ckpt_every = 1 first)", who);
   if (out->d0_layer < 1) return fail(h, DMPT_EINVAL, "%s: the forward run did not converge", who);
-  const Layout L = make_layout(n, out->layout_k, out->precision, out->tape_states);
+  const Layout L = make_layout(n, out->layout_k, out->precision, out->tape_states, out->ckpt_slots);
   if (ws_bytes < L.total) return fail(h, DMPT_EWORKSPACE, "%s: workspace too small", who);
   return DMPT_OK;
 }
@@ -250,6 +279,7 @@ dmpt_status replay_run(dmpt_handle h, const Layout& L, const double* H1, const d
     info->product_launches = launched;
     for (int m = 1; m <= hs->rp_layers && m <= DMPT_MAX_LAYERS; ++m) info->sigma[m - 1] = hs->sigma[m];
     fill_history(info, *hs, k, hs->rp_layers);
+    info->hole = hs->hole;
   }
   delete hs;
   if (status != DMPT_OK) return fail(h, status, "response replay: device status %s", "");
@@ -314,6 +344,7 @@ void dmpt_default_options(dmpt_options* o) {
   o->order = 1;
   o->tile_band = 8;
   o->round_align = 1;
+  o->hole_form = 1;
 }
 
 const char* dmpt_status_string(dmpt_status s) {
@@ -411,7 +442,8 @@ static dmpt_status forward_impl(dmpt_handle h, const double* H, const double* H1
   }
   if (o->ckpt_every != 0 && o->precision < DMPT_DUAL_FP16)
     return fail(h, DMPT_EUNSUPPORTED,
-                "dmpt_sp2_response: the S0 tape (ckpt_every = 1) needs a dual precision%s");
+                "dmpt_sp2_response: the S0 tape / checkpoints (ckpt_every >= 1) need a dual "
+                "precision%s");
   cudaStream_t s = (cudaStream_t)stream;
   DeviceGuard g(h->device);
 
@@ -440,9 +472,12 @@ static dmpt_status forward_impl(dmpt_handle h, const double* H, const double* H1
   State* st = (State*)(base + L.off_state);
   cudaError_t e = cudaMemsetAsync(st, 0, sizeof(State), s);
   if (e != cudaSuccess) return cuda_fail(h, e, "state reset");
+  const FwdOpts fo{o->ckpt_every >= 2 ? o->ckpt_every : 0, L.ckpt_slots, o->accum_chunk,
+                   o->cta_pair, o->k_snake, o->tile_band};
   state_init_kernel<<<1, 1, 0, s>>>(st, order >= 2 ? order * k : k, o->max_layers, o->precision,
-                                    (double)n_occ, o->c_pt, o->c_d0, L.tape_states > 0 ? 1 : 0,
-                                    4 * (1 + L.k), L.tape_states, L.k, n, order, k);
+                                    (double)n_occ, o->c_pt, o->c_d0, o->ckpt_every == 1 ? 1 : 0,
+                                    4 * (1 + L.k), L.tape_states, L.k, n, order, k, fo,
+                                    use_hole_form(o, n, n_occ));
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "state init");
   if ((e = launch_bounds(H, n, ld, &st->eps1, s)) != cudaSuccess) return cuda_fail(h, e, "bounds");
   const int init_blocks = 1024;
@@ -451,6 +486,9 @@ static dmpt_status forward_impl(dmpt_handle h, const double* H, const double* H1
     return cuda_fail(h, e, "init");
   if ((e = launch_decide(L, workspace, kDecideInit, init_blocks, s)) != cudaSuccess)
     return cuda_fail(h, e, "decide(init)");
+  const bool ckpt = o->ckpt_every >= 2;
+  if (ckpt && (e = launch_ckpt_store(L, workspace, s)) != cudaSuccess)
+    return cuda_fail(h, e, "checkpoint");
   if (dual && (e = launch_split(L, workspace, 0, s)) != cudaSuccess) return cuda_fail(h, e, "split");
 
   // events for per-launch timing of the layer products
@@ -478,6 +516,8 @@ static dmpt_status forward_impl(dmpt_handle h, const double* H, const double* H1
       if (o->timing) cudaEventRecord(h->events[2 * launched + 1], s);
       if ((e = launch_decide(L, workspace, kDecideLayer, entries, s)) != cudaSuccess)
         return cuda_fail(h, e, "decide(layer)");
+      if (ckpt && (e = launch_ckpt_store(L, workspace, s)) != cudaSuccess)
+        return cuda_fail(h, e, "checkpoint");
       ++launched;
     }
     if ((e = cudaMemcpyAsync(&done, &st->done, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
@@ -521,6 +561,7 @@ static dmpt_status forward_impl(dmpt_handle h, const double* H, const double* H1
     info->froerr0 = S.froerr0;
     for (int m = 1; m <= S.layers_run && m <= DMPT_MAX_LAYERS; ++m) info->sigma[m - 1] = S.sigma[m];
     fill_history(info, S, kj, S.layers_run);
+    info->hole = S.hole;
     info->product_launches = launched;
     double mma = 0.0, alg = 0.0;
     for (int m = 1; m <= S.layers_run; ++m) {
@@ -826,15 +867,19 @@ dmpt_status dmpt_sp2_backward(dmpt_handle h, const double* G, int64_t n, int64_t
   }
   const State fs = *hs;
   delete hs;
-  if (fs.tape != 1 || fs.n != n || !fs.done || fs.d0_updates < 0 ||
-      fs.d0_updates + 1 > fs.tape_states ||
+  const bool ckpt = fs.tape != 1 && fs.ckpt_k >= 2;
+  const bool states_ok =
+      fs.tape == 1 ? fs.d0_updates + 1 <= fs.tape_states
+                   : (ckpt && fs.tape_states >= fs.ckpt_k && fs.d0_updates / fs.ckpt_k < fs.ckpt_slots);
+  if (!states_ok || fs.n != n || !fs.done || fs.d0_updates < 0 ||
       (fs.precision != DMPT_DUAL_FP16 && fs.precision != DMPT_DUAL_BF16))
     return fail(h, DMPT_EINVAL,
-                "dmpt_sp2_backward: the workspace holds no S0 tape of a dual-precision forward "
-                "run of this n (run dmpt_sp2_response with ckpt_every = 1 first)%s");
+                "dmpt_sp2_backward: the workspace holds no S0 tape or checkpoints of a "
+                "dual-precision forward run of this n (run dmpt_sp2_response with ckpt_every >= 1 "
+                "first)%s");
   if (fs.status != DMPT_OK)
     return fail(h, DMPT_EINVAL, "dmpt_sp2_backward: the forward run did not converge%s");
-  const Layout L = make_layout(n, fs.layout_k, fs.precision, fs.tape_states);
+  const Layout L = make_layout(n, fs.layout_k, fs.precision, fs.tape_states, fs.ckpt_slots);
   if (ws_bytes < L.total) return fail(h, DMPT_EWORKSPACE, "dmpt_sp2_backward: workspace too small%s");
 
   const int blocks = 1024;
@@ -847,13 +892,49 @@ dmpt_status dmpt_sp2_backward(dmpt_handle h, const double* G, int64_t n, int64_t
   if ((e = launch_split(L, workspace, 1, s)) != cudaSuccess) return cuda_fail(h, e, "adjoint split");
   int64_t entries = 0;
   double pass_flops = 0.0;
-  for (int m = fs.d0_updates; m >= 1; --m) {
-    if ((e = launch_layer_tc(L, workspace, s, o->timeout_s, o->accum_chunk, o->cta_pair,
-                             o->k_snake, o->tile_band, &entries, &pass_flops, 0,
-                             o->round_align)) != cudaSuccess)
-      return cuda_fail(h, e, "adjoint layer");
-    if ((e = launch_decide(L, workspace, kDecideAdjLayer, entries, s)) != cudaSuccess)
-      return cuda_fail(h, e, "adjoint decide");
+  const int U = fs.d0_updates;
+  // without checkpoints the whole tape is one segment starting at state 0
+  const int K = ckpt ? fs.ckpt_k : U + 1;
+  int64_t rec_item_base = 0;
+  if (ckpt && fs.fwd_cta_pair) {
+    int64_t pt = 0;
+    pair_tile_info(L, &pt, nullptr);   // 2 entries per pair tile
+    rec_item_base = (int64_t)fs.k_fwd * (pt / 2);
+  }
+  for (int c = ckpt ? (U > 0 ? (U - 1) / K : 0) : 0; c >= 0; --c) {
+    const int a = c * K;                       // first state of the segment
+    const int b = U < a + K ? U : a + K;       // adjoint layers b .. a + 1 use states a .. b - 1
+    if (ckpt) {
+      // S_a from its checkpoint, then S_{a+1} .. S_{b-1} by the forward's own
+      // square products (its sigma_m, 16-bit copies and product options)
+      if ((e = launch_seg_load(L, workspace, c, a, s)) != cudaSuccess)
+        return cuda_fail(h, e, "segment load");
+      if ((e = launch_split(L, workspace, 0, s, 1)) != cudaSuccess)
+        return cuda_fail(h, e, "segment split");
+      for (int m = a + 1; m < b; ++m) {
+        // in the forward's D0 layers all k_fwd response jobs ran, and their
+        // items came before the square's in each launch
+        if ((e = launch_recompute_plan(L, workspace, m, a, rec_item_base, s)) != cudaSuccess)
+          return cuda_fail(h, e, "recompute plan");
+        // no round alignment: the skipped leading items are never counted in
+        if ((e = launch_layer_tc(L, workspace, s, o->timeout_s, fs.fwd_chunk, fs.fwd_cta_pair,
+                                 fs.fwd_k_snake, fs.fwd_band, &entries, &pass_flops, 0,
+                                 0)) != cudaSuccess)
+          return cuda_fail(h, e, "recompute layer");
+        if ((e = launch_recompute_done(L, workspace, s)) != cudaSuccess)
+          return cuda_fail(h, e, "recompute done");
+      }
+      if ((e = launch_decide(L, workspace, kDecideAdjResume, 0, s)) != cudaSuccess)
+        return cuda_fail(h, e, "adjoint decide");
+    }
+    for (int m = b; m >= a + 1; --m) {
+      if ((e = launch_layer_tc(L, workspace, s, o->timeout_s, o->accum_chunk, o->cta_pair,
+                               o->k_snake, o->tile_band, &entries, &pass_flops, 0,
+                               o->round_align)) != cudaSuccess)
+        return cuda_fail(h, e, "adjoint layer");
+      if ((e = launch_decide(L, workspace, kDecideAdjLayer, entries, s)) != cudaSuccess)
+        return cuda_fail(h, e, "adjoint decide");
+    }
   }
   if ((e = launch_adj_finalize(L, workspace, dLdH, ld, s)) != cudaSuccess)
     return cuda_fail(h, e, "adjoint finalize");
@@ -995,7 +1076,10 @@ static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
     State* st = (State*)ws;
     if ((e = cudaMemsetAsync(st, 0, sizeof(State), si)) != cudaSuccess) return cuda_fail(h, e, "state");
     state_init_kernel<<<1, 1, 0, si>>>(st, k, o->max_layers, o->precision, (double)n_occ[i],
-                                       o->c_pt, o->c_d0, 0, 4 * (1 + L[i].k), 0, L[i].k, n[i]);
+                                       o->c_pt, o->c_d0, 0, 4 * (1 + L[i].k), 0, L[i].k, n[i],
+                                       1, 0, FwdOpts{0, 0, o->accum_chunk, o->cta_pair,
+                                                     o->k_snake, o->tile_band},
+                                       use_hole_form(o, n[i], n_occ[i]));
     if ((e = launch_bounds(H[i], n[i], ld[i], &st->eps1, si)) != cudaSuccess)
       return cuda_fail(h, e, "batch bounds");
     if ((e = launch_init(L[i], ws, H[i], k ? H1[i] : nullptr, ld[i], k, 1024, si)) != cudaSuccess)
@@ -1130,6 +1214,7 @@ static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
       I.alg_flops = alg;
       for (int m = 1; m <= S.layers_run && m <= DMPT_MAX_LAYERS; ++m) I.sigma[m - 1] = S.sigma[m];
       fill_history(&I, S, k, S.layers_run);
+      I.hole = S.hole;
     }
   }
   // the caller's stream continues after the batch
@@ -1226,7 +1311,7 @@ dmpt_status dmpt_response_replay(dmpt_handle h, const double* H1, int k, int64_t
   if (st != DMPT_OK) return st;
   if (k > fs.layout_k)
     return fail(h, DMPT_EINVAL, "dmpt_response_replay: k exceeds the forward's response slots%s");
-  const Layout L = make_layout(n, fs.layout_k, fs.precision, fs.tape_states);
+  const Layout L = make_layout(n, fs.layout_k, fs.precision, fs.tape_states, fs.ckpt_slots);
   return replay_run(h, L, H1, nullptr, k, ld, o, P1, info, workspace, s);
 }
 
@@ -1252,7 +1337,7 @@ dmpt_status dmpt_scc_response(dmpt_handle h, const double* H1_ext, const double*
   if (st != DMPT_OK) return st;
   if (k > fs.layout_k)
     return fail(h, DMPT_EINVAL, "dmpt_scc_response: k exceeds the forward's response slots%s");
-  const Layout L = make_layout(n, fs.layout_k, fs.precision, fs.tape_states);
+  const Layout L = make_layout(n, fs.layout_k, fs.precision, fs.tape_states, fs.ckpt_slots);
   double* q = (double*)((char*)workspace + L.off_vec);
   double* v = q + (size_t)k * n;
   double* red = v + (size_t)k * n;

@@ -62,6 +62,15 @@ struct State {
   int k1;               // first-order directions (job 1 + (o - 1) k1 + d: order o)
   unsigned round_ctr;   // pair kernel: rounds started by its CTAs (soft alignment);
                         // every decide step resets it before the next launch
+  int hole;             // 1: the recursion runs on I - P (complement form)
+  int ckpt_k;           // >= 2: FP32 checkpoint of every ckpt_k-th S0 state
+  int ckpt_slots;       // checkpoint capacity (states)
+  int ckpt_pending;     // the last decide step made a state that is checkpointed
+  int adj_seg_a;        // adjoint with checkpoints: first state held in the tape
+  int64_t item_base;    // pair kernel: virtual index of its first item (0 except
+                        // when a square is recomputed alone)
+  int fwd_chunk, fwd_cta_pair, fwd_k_snake, fwd_band;   // the forward's product
+                        // options, reused when the backward recomputes states
   int64_t n;
   int cur1[kMaxK];
   int d1_conv[kMaxK];
@@ -88,11 +97,12 @@ struct Layout {
   int precision;
   int tape_states;        // 16-bit S0 copies kept for the adjoint (0: none)
   size_t elem;            // bytes per master element (8 or 4)
-  size_t off_state, off_partials, off_master, off_ops16, off_vec, total;
+  size_t off_state, off_partials, off_master, off_ops16, off_vec, off_ckpt, total;
   int64_t partial_tiles;  // entries per job in the partials array
+  int ckpt_slots;         // FP32 S0 checkpoints (Np x Np each; 0: none)
 };
 
-Layout make_layout(int64_t n, int k, int precision, int tape_states = 0);
+Layout make_layout(int64_t n, int k, int precision, int tape_states = 0, int ckpt_slots = 0);
 
 // 16-bit operand slice of matrix m (0 = S0, 1 + j = S1_j) in ping-pong buffer
 // `buf`, part 0 = hi, 1 = lo.  Tape slices follow the 4 (1 + k) ping-pong ones.
@@ -126,7 +136,22 @@ cudaError_t launch_decide(const Layout& L, void* ws, int mode, int64_t entries,
 // *pass_flops: flops of one full-K, single-term pass over all tiles.
 cudaError_t launch_layer_simt(const Layout& L, void* ws, cudaStream_t s, int64_t* entries,
                               double* pass_flops);
-cudaError_t launch_split(const Layout& L, void* ws, int first_job, cudaStream_t s);
+// 16-bit copies of the current masters of jobs first_job .. first_job + jobs - 1
+// (jobs < 0: every job from first_job on)
+cudaError_t launch_split(const Layout& L, void* ws, int first_job, cudaStream_t s, int jobs = -1);
+// Checkpoints (ckpt_every >= 2): copy the current S0 master into its
+// checkpoint slot when the last decide step asked for it (State::ckpt_pending).
+cudaError_t launch_ckpt_store(const Layout& L, void* ws, cudaStream_t s);
+// Backward with checkpoints: load checkpoint `c` (state a = c * ckpt_k) as the
+// current S0 master (buffer 0) and the first tape state, and plan / finish
+// the recompute of state m from state m - 1 (its 16-bit copies into tape slot
+// m - a) with the forward's sigma_m.
+cudaError_t launch_seg_load(const Layout& L, void* ws, int c, int a, cudaStream_t s);
+// item_base: the forward launch's response items that preceded the square's
+// (pair kernel), so that the square's tiles keep their rounds.
+cudaError_t launch_recompute_plan(const Layout& L, void* ws, int m, int a, int64_t item_base,
+                                  cudaStream_t s);
+cudaError_t launch_recompute_done(const Layout& L, void* ws, cudaStream_t s);
 // adjoint: Gbar = sym(G) into response slot 1 (upper triangle mirrored)
 cudaError_t launch_adj_init(const Layout& L, void* ws, const double* G, int64_t ld, int blocks,
                             cudaStream_t s);
@@ -195,7 +220,8 @@ enum DecideMode {
   kDecideAdjInit = 2,
   kDecideAdjLayer = 3,
   kDecideReplayInit = 4,
-  kDecideReplayLayer = 5
+  kDecideReplayLayer = 5,
+  kDecideAdjResume = 6    // adjoint: plan the pending layer after a segment reload
 };
 
 // batched solves: *flag = 1 when every instance's control block is done

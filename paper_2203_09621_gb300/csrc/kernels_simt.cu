@@ -17,7 +17,7 @@ namespace dmpt {
 
 static inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-Layout make_layout(int64_t n, int k, int precision, int tape_states) {
+Layout make_layout(int64_t n, int k, int precision, int tape_states, int ckpt_slots) {
   Layout L{};
   L.n = n;
   L.Np = ((n + kPad - 1) / kPad) * kPad;
@@ -46,6 +46,10 @@ Layout make_layout(int64_t n, int k, int precision, int tape_states) {
   // small vectors of the self-consistent response: q[k][n], v[k][n], red[k][4]
   L.off_vec = off;
   off = align256(off + ((size_t)(k > 0 ? k : 1) * (2 * (size_t)n + 4)) * sizeof(double));
+  // FP32 checkpoints of every ckpt_k-th S0 state (adjoint with recompute)
+  L.ckpt_slots = ckpt_slots;
+  L.off_ckpt = off;
+  off = align256(off + (size_t)ckpt_slots * mat * 4);
   L.total = off;
   return L;
 }
@@ -157,6 +161,7 @@ __global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const d
   __shared__ double red[3 * 256];
   const double e1 = st->eps1, eN = st->epsN;
   const double w = 1.0 / (eN - e1);
+  const bool hole = st->hole != 0;   // complement form: S_0 = I - (eps_N I - H) w
   const size_t mat = (size_t)Np * Np;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
   const int64_t TB = Np / 32;
@@ -189,7 +194,10 @@ __global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const d
         if (r < n && c < n) {
           double h = src[r * ld + c];
           if (m > 0 && shift != nullptr && r == c) h += shift[(size_t)(m - 1) * n + r];
-          v = m == 0 ? ((r == c ? eN : 0.0) - h) * w : -h * w;
+          if (hole)
+            v = m == 0 ? (h - (r == c ? e1 : 0.0)) * w : h * w;
+          else
+            v = m == 0 ? ((r == c ? eN : 0.0) - h) * w : -h * w;
         }
         tile[rl][tx] = (T)v;   // the stored (rounded) value
       }
@@ -436,15 +444,18 @@ __device__ void plan_replay(State* st, int m) {
 // 256 doubles, sums: (kMaxK + 1) x kNQ doubles of shared memory).
 __device__ void decide_body(State* st, const double* __restrict__ partials, int64_t ptiles,
                             int64_t entries, int mode, double* red, double (*sums)[kNQ]) {
-  if (threadIdx.x == 0) st->round_ctr = 0u;   // for the next pair-kernel launch
+  if (threadIdx.x == 0) {
+    st->round_ctr = 0u;    // for the next pair-kernel launch
+    st->ckpt_pending = 0;  // set again below when this step makes a checkpointed state
+  }
   if (st->done) return;
-  const bool adj = mode == kDecideAdjInit || mode == kDecideAdjLayer;
+  const bool adj = mode == kDecideAdjInit || mode == kDecideAdjLayer || mode == kDecideAdjResume;
   const bool rp = mode == kDecideReplayInit || mode == kDecideReplayLayer;
   const int k = adj ? 1 : st->k;
   for (int job = 0; job <= k; ++job) {
     bool ran;
     if (adj)
-      ran = job == 1;
+      ran = job == 1 && mode != kDecideAdjResume;
     else if (mode == kDecideInit)
       ran = true;
     else if (mode == kDecideReplayInit)
@@ -531,14 +542,14 @@ __device__ void decide_body(State* st, const double* __restrict__ partials, int6
     return;
   }
 
-  if (mode == kDecideAdjInit || mode == kDecideAdjLayer) {
+  if (adj) {
     // ---- adjoint of the S0 recursion, run backwards over the stored states
     if (st->timeout_flag) {
       st->status = DMPT_ETIMEOUT;
       st->done = 1;
       return;
     }
-    if (sums[1][kQBad] > 0.0) {
+    if (mode != kDecideAdjResume && sums[1][kQBad] > 0.0) {
       st->status = DMPT_ENUMERIC;
       st->done = 1;
       return;
@@ -555,11 +566,13 @@ __device__ void decide_body(State* st, const double* __restrict__ partials, int6
                               ? fp16_exponent_for(sqrt(st->s1_fro2[0]))
                               : 0;
       m = st->d0_updates;
-    } else {
+    } else if (mode == kDecideAdjLayer) {
       st->cur1[0] ^= 1;
       st->s1_fro2[0] = sums[1][kQFroNew];
       st->s1_exp_cur[0] = st->s1_exp_next[0];
       m = st->adj_m - 1;
+    } else {
+      m = st->adj_m;   // resume after the host reloaded the tape with an earlier segment
     }
     st->adj_m = m;
     if (m <= 0) {
@@ -568,8 +581,15 @@ __device__ void decide_body(State* st, const double* __restrict__ partials, int6
       st->done = 1;
       return;
     }
+    if (m <= st->adj_seg_a) {
+      // S_{m-1} lies before the states in the tape (checkpointed run): the
+      // host recomputes the previous segment and resumes with layer m
+      st->plan_resp[0] = 0;
+      return;
+    }
     // adjoint of layer m: Gbar <- sigma_m (S_{m-1} Gbar + Gbar S_{m-1}) + (1 - sigma_m) Gbar
-    st->z0_cur = st->tape_base + 2 * (m - 1);
+    // (the tape holds states adj_seg_a, adj_seg_a + 1, ...; 0 without checkpoints)
+    st->z0_cur = st->tape_base + 2 * (m - 1 - st->adj_seg_a);
     st->sigma_cur = st->sigma[m];
     st->plan_resp[0] = 1;
     st->s1_exp_next[0] = st->precision == DMPT_DUAL_FP16
@@ -590,6 +610,7 @@ __device__ void decide_body(State* st, const double* __restrict__ partials, int6
     st->s0_exp = st->precision == DMPT_DUAL_FP16 ? kFp16TargetExp - 1 : 0;
     st->cur0 = 0;
     st->d0_updates = 0;
+    st->ckpt_pending = st->ckpt_k >= 2 ? 1 : 0;   // S_0 is checkpoint 0
     st->z0_cur = st->tape ? st->tape_base : zslice(0, 0, 0, st->layout_k);
     st->z0_next = st->tape ? st->tape_base + 2 : zslice(1, 0, 0, st->layout_k);
     st->d0_conv = 0;
@@ -631,6 +652,7 @@ __device__ void decide_body(State* st, const double* __restrict__ partials, int6
       st->NX = sums[0][kQFroNew];   // ||S_n||_F^2 = Tr S_n^2 (N_X of the next layer)
       st->cur0 ^= 1;
       st->d0_updates += 1;
+      if (st->ckpt_k >= 2 && st->d0_updates % st->ckpt_k == 0) st->ckpt_pending = 1;
       if (st->tape) {
         st->z0_cur = st->z0_next;
         st->z0_next += 2;
@@ -1059,10 +1081,10 @@ __global__ void split_kernel(const State* st, const float* __restrict__ master, 
   }
 }
 
-cudaError_t launch_split(const Layout& L, void* ws, int first_job, cudaStream_t s) {
+cudaError_t launch_split(const Layout& L, void* ws, int first_job, cudaStream_t s, int jobs) {
   char* base = (char*)ws;
   const State* st = (const State*)(base + L.off_state);
-  dim3 grid(152 * 4, 1 + L.k - first_job);
+  dim3 grid(152 * 4, jobs < 0 ? 1 + L.k - first_job : jobs);
   if (L.precision == DMPT_DUAL_FP16)
     split_kernel<__half><<<grid, 256, 0, s>>>(st, (const float*)(base + L.off_master),
                                               (__half*)(base + L.off_ops16), L.Np, L.k,
@@ -1071,6 +1093,93 @@ cudaError_t launch_split(const Layout& L, void* ws, int first_job, cudaStream_t 
     split_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(st, (const float*)(base + L.off_master),
                                                      (__nv_bfloat16*)(base + L.off_ops16),
                                                      L.Np, L.k, first_job);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoints of the S0 recursion (ckpt_every = k >= 2) and the recompute of a
+// segment of states from its checkpoint in the backward pass.
+
+__global__ void ckpt_store_kernel(const State* st, const float4* __restrict__ master,
+                                  float4* ckpt, int64_t Np, int lk) {
+  if (!st->ckpt_pending) return;
+  const int slot = st->d0_updates / st->ckpt_k;
+  if (slot >= st->ckpt_slots) return;   // cannot happen: slots cover max_layers / k + 1
+  const size_t n4 = (size_t)Np * Np / 4;
+  const float4* src = master + (size_t)st->cur0 * (1 + lk) * n4;
+  float4* dst = ckpt + (size_t)slot * n4;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+       i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+cudaError_t launch_ckpt_store(const Layout& L, void* ws, cudaStream_t s) {
+  char* base = (char*)ws;
+  ckpt_store_kernel<<<152 * 4, 256, 0, s>>>((const State*)(base + L.off_state),
+                                            (const float4*)(base + L.off_master),
+                                            (float4*)(base + L.off_ckpt), L.Np, L.k);
+  return cudaGetLastError();
+}
+
+// Checkpoint c (state a) into S0 master buffer 0; it becomes the current S0
+// and its 16-bit copies go to the first tape slot (split afterwards).
+__global__ void seg_load_kernel(State* st, float4* master, const float4* __restrict__ ckpt,
+                                int64_t Np, int c, int a) {
+  const size_t n4 = (size_t)Np * Np / 4;
+  const float4* src = ckpt + (size_t)c * n4;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+       i += (size_t)gridDim.x * blockDim.x)
+    master[i] = src[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->cur0 = 0;
+    st->z0_cur = st->tape_base;
+    st->adj_seg_a = a;
+  }
+}
+
+cudaError_t launch_seg_load(const Layout& L, void* ws, int c, int a, cudaStream_t s) {
+  if (c < 0 || c >= L.ckpt_slots) return cudaErrorInvalidValue;
+  char* base = (char*)ws;
+  seg_load_kernel<<<152 * 4, 256, 0, s>>>((State*)(base + L.off_state),
+                                          (float4*)(base + L.off_master),
+                                          (const float4*)(base + L.off_ckpt), L.Np, c, a);
+  return cudaGetLastError();
+}
+
+// Plan the recompute of S_m = sigma_m S_{m-1}^2 + (1 - sigma_m) S_{m-1}: the
+// square job only, S0 update stored, 16-bit copies into tape slot m - a.
+__global__ void recompute_plan_kernel(State* st, int m, int a, int64_t item_base) {
+  st->round_ctr = 0u;
+  st->item_base = item_base;
+  st->plan_square = 1;
+  st->plan_write0 = 1;
+  st->sigma_cur = st->sigma[m];
+  for (int j = 0; j < kMaxK; ++j) st->plan_resp[j] = 0;
+  st->z0_next = st->tape_base + 2 * (m - a);
+}
+
+// After a recompute layer: the new state is the current S0.
+__global__ void recompute_done_kernel(State* st) {
+  st->round_ctr = 0u;
+  st->item_base = 0;
+  st->cur0 ^= 1;
+  st->z0_cur = st->z0_next;
+  st->plan_square = 0;
+  st->plan_write0 = 0;
+  if (st->timeout_flag) {
+    st->status = DMPT_ETIMEOUT;
+    st->done = 1;
+  }
+}
+
+cudaError_t launch_recompute_plan(const Layout& L, void* ws, int m, int a, int64_t item_base,
+                                  cudaStream_t s) {
+  recompute_plan_kernel<<<1, 1, 0, s>>>((State*)((char*)ws + L.off_state), m, a, item_base);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recompute_done(const Layout& L, void* ws, cudaStream_t s) {
+  recompute_done_kernel<<<1, 1, 0, s>>>((State*)((char*)ws + L.off_state));
   return cudaGetLastError();
 }
 
@@ -1178,11 +1287,13 @@ __global__ void finalize_kernel(const State* st, const T* __restrict__ master, d
   const int cur = m == 0 ? st->cur0 : st->cur1[m - 1];
   const T* src = master + (size_t)(cur * (1 + k) + m) * mat;
   double* dst = y == 0 ? P : P1 + (size_t)(y - 1) * n * ld;
+  const bool hole = st->hole != 0;   // the recursion ran on I - P: P = I - S0, P_o = -S_o
   const int64_t total = n * n;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / n, c = i - r * n;
-    dst[r * ld + c] = (double)src[(size_t)r * Np + c];
+    const double v = (double)src[(size_t)r * Np + c];
+    dst[r * ld + c] = !hole ? v : (y == 0 ? (r == c ? 1.0 : 0.0) - v : -v);
   }
 }
 

@@ -1105,6 +1105,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
   const int s0e = st->s0_exp;
   const int z0c = st->z0_cur, z0n = st->z0_next;
   const int k1 = st->order >= 2 ? st->k1 : k;   // first-order directions
+  // virtual index of the first item (0, except when the backward recomputes
+  // a square alone: it then numbers the square's items as the forward launch
+  // did, after its response items, so each tile keeps its round and K-snake
+  // direction and the recomputed states are bit-identical)
+  const int64_t vbase = st->item_base;
 
   const uint32_t rank = cluster_rank();
   const bool leader = rank == 0;
@@ -1166,7 +1171,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
       bool ok = true;
       int64_t round = 0;
       bool align = round_align != 0;
-      for (int64_t it = pair; it < items && ok; it += npairs, ++round) {
+      for (int64_t v = pair; v < vbase + items && ok; v += npairs, ++round) {
+        if (v < vbase) continue;
+        const int64_t it = v - vbase;
         if (round > 0) round_start(&st->round_ctr, round, items, npairs, align);
         const int job = job_at(jmask, (int)(it / tiles));
         int I2, J;
@@ -1190,7 +1197,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
       // test hook (see the single-CTA kernel)
       bool ok = !(inject_stall &&
                   !mbar_wait(bar_drain, 0, limit_ns, abort_flag, timeout_global));
-      for (int64_t it = pair; it < items && ok; it += npairs) {
+      for (int64_t v = pair; v < vbase + items && ok; v += npairs) {
+        if (v < vbase) continue;
+        const int64_t it = v - vbase;
         const int job = job_at(jmask, (int)(it / tiles));
         ok = mma_item<BF16>(rg, tb, job_passes(job, k1) * kblocks, kblocks, chunk, tmem_base, ring,
                             bar_full, bar_empty, bar_tfull, bar_tempty, limit_ns, abort_flag,
@@ -1216,7 +1225,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     uint32_t abphase = 0;
     bool alive = true;
     int64_t eround = 0;
-    for (int64_t it = pair; it < items && alive; it += npairs, ++eround) {
+    for (int64_t v = pair; v < vbase + items && alive; v += npairs, ++eround) {
+      if (v < vbase) continue;
+      const int64_t it = v - vbase;
       const bool crev = k_snake && (eround & 1);   // same order as the producer
       const int job = job_at(jmask, (int)(it / tiles));
       const int passes = job_passes(job, k1);

@@ -45,6 +45,7 @@ class DmptOptions(ctypes.Structure):
         ("inject_stall", ctypes.c_int),
         ("autotune", ctypes.c_int),
         ("round_align", ctypes.c_int),
+        ("hole_form", ctypes.c_int),
     ]
 
 
@@ -69,6 +70,7 @@ class DmptInfo(ctypes.Structure):
         ("n_x", ctypes.c_double * DMPT_MAX_LAYERS),
         ("iderr", ctypes.c_double * DMPT_MAX_LAYERS),
         ("froerr1_hist", (ctypes.c_double * DMPT_MAX_LAYERS) * DMPT_MAX_K),
+        ("hole", ctypes.c_int),
     ]
 
 
@@ -179,6 +181,7 @@ class Info:
     n_x: list = None
     iderr: list = None
     froerr1_hist: list = None
+    hole: bool = False
 
     @classmethod
     def from_c(cls, ci: DmptInfo, k: int) -> "Info":
@@ -191,13 +194,14 @@ class Info:
                    mma_flops=ci.mma_flops, alg_flops=ci.alg_flops,
                    sigma=list(ci.sigma[:ci.layers]), n_s=list(ci.n_s[:d0]),
                    n_x=list(ci.n_x[:d0]), iderr=list(ci.iderr[:d0]),
-                   froerr1_hist=[list(ci.froerr1_hist[j][:ci.layers]) for j in range(k)])
+                   froerr1_hist=[list(ci.froerr1_hist[j][:ci.layers]) for j in range(k)],
+                   hole=bool(ci.hole))
 
 
 def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_scaling=1,
             sync_every=4, timing=False, timeout_s=2.0, accum_chunk=0,
             cta_pair=1, k_snake=1, ckpt_every=0, order=1, tile_band=8,
-            inject_stall=0, autotune=0, round_align=1) -> DmptOptions:
+            inject_stall=0, autotune=0, round_align=1, hole_form=1) -> DmptOptions:
     lib = load_library()
     o = DmptOptions()
     lib.dmpt_default_options(ctypes.byref(o))
@@ -218,6 +222,7 @@ def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_s
     o.inject_stall = int(inject_stall)
     o.autotune = int(autotune)
     o.round_align = int(round_align)
+    o.hole_form = int(hole_form)
     return o
 
 
@@ -426,7 +431,8 @@ class Context:
 
     def sp2_backward(self, G, workspace, out=None, stream=None, **kw):
         """dL/dH of L = Tr[G P] for the forward run that filled `workspace`
-        (a uint8 CUDA tensor used with ckpt_every=1)."""
+        (a uint8 CUDA tensor used with ckpt_every >= 1: the full S0 tape, or
+        checkpoints every ckpt_every states with recomputation)."""
         import torch
         if G.dtype != torch.float64 or not G.is_cuda:
             raise TypeError("G must be a float64 CUDA tensor")
@@ -607,19 +613,20 @@ def _autograd_function():
     class SP2Density(torch.autograd.Function):
         """P = theta(mu I - H) by DNN-SP2-PT with the hand-written adjoint.
 
-        forward(H, n_occ, precision): runs dmpt_sp2_response with k = 0 and
-        the S0 tape kept in a workspace owned by this node; backward(gP)
-        runs dmpt_sp2_backward on that tape.
+        forward(H, n_occ, precision, ckpt_every): runs dmpt_sp2_response with
+        k = 0 and the S0 states (every state for ckpt_every = 1, else an FP32
+        checkpoint of every ckpt_every-th state) kept in a workspace owned by
+        this node; backward(gP) runs dmpt_sp2_backward on it.
         """
 
         @staticmethod
-        def forward(ctx, H, n_occ, precision="dual_fp16"):
+        def forward(ctx, H, n_occ, precision="dual_fp16", ckpt_every=8):
             c = context(H.device.index or 0)
-            opts = options(precision=precision, ckpt_every=1)
+            opts = options(precision=precision, ckpt_every=ckpt_every)
             nbytes = c.workspace_size(H.shape[0], 0, opts)
             ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=H.device)
             P, _, info = c.sp2_response(H.detach(), None, n_occ, precision=precision,
-                                        ckpt_every=1, workspace=ws)
+                                        ckpt_every=ckpt_every, workspace=ws)
             ctx.ws = ws
             ctx.info = info
             return P
@@ -628,7 +635,7 @@ def _autograd_function():
         def backward(ctx, gP):
             c = context(gP.device.index or 0)
             dLdH = c.sp2_backward(gP.detach().to(torch.float64), ctx.ws)
-            return dLdH, None, None
+            return dLdH, None, None, None
 
     return SP2Density
 
@@ -636,9 +643,12 @@ def _autograd_function():
 _sp2_density = None
 
 
-def density(H, n_occ, precision="dual_fp16"):
-    """Differentiable P(H): torch.autograd-aware wrapper of the CUDA path."""
+def density(H, n_occ, precision="dual_fp16", ckpt_every=8):
+    """Differentiable P(H): torch.autograd-aware wrapper of the CUDA path.
+
+    ckpt_every: 1 keeps every S0 state for the backward; k >= 2 keeps an FP32
+    checkpoint of every k-th state and recomputes the rest (default 8)."""
     global _sp2_density
     if _sp2_density is None:
         _sp2_density = _autograd_function()
-    return _sp2_density.apply(H, n_occ, precision)
+    return _sp2_density.apply(H, n_occ, precision, ckpt_every)

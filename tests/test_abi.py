@@ -86,7 +86,15 @@ def test_host_only_calls(lib):
     t.max_layers = 50
     wt = lib.dmpt_workspace_size(1000, 1, ctypes.byref(t))
     assert wt - w1 >= 52 * 2 * 1024 * 1024 * 2
-    t.ckpt_every = 2
+    # checkpoints every k states: (max_layers / k + 1) FP32 masters plus a
+    # k-state hi/lo tape for the segment being recomputed
+    t.ckpt_every = 8
+    wc = lib.dmpt_workspace_size(1000, 1, ctypes.byref(t))
+    assert wc - w1 >= (50 // 8 + 1) * 4 * 1024 * 1024 + 8 * 2 * 2 * 1024 * 1024
+    assert wc < wt
+    t.ckpt_every = 257      # above DMPT_MAX_LAYERS
+    assert lib.dmpt_workspace_size(1000, 1, ctypes.byref(t)) == 0
+    t.ckpt_every = -1
     assert lib.dmpt_workspace_size(1000, 1, ctypes.byref(t)) == 0
     bad = dmpt.DmptOptions()
     lib.dmpt_default_options(ctypes.byref(bad))

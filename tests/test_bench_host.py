@@ -32,11 +32,22 @@ def test_clock_summary_parses_nvidia_smi_lines():
     assert cs.summary()["samples"] == 0
 
 
-def test_traffic_record_only_for_its_workload():
+def test_traffic_record_only_for_its_workload_and_source(monkeypatch):
+    import hashlib
+    import os
     w = dict(bench.TRAFFIC_RECORD["workload"])
+    with open(os.path.join(bench.ROOT, bench.TRAFFIC_RECORD["source"]), "rb") as f:
+        current = hashlib.sha256(f.read()).hexdigest()
+    # the record counts only while the kernel source is the one it was taken with
+    want = bench.TRAFFIC_RECORD["bytes_per_launch"] \
+        if current == bench.TRAFFIC_RECORD["sha256"] else None
+    assert bench.recorded_traffic(w) == want
+    monkeypatch.setitem(bench.TRAFFIC_RECORD, "sha256", current)
     assert bench.recorded_traffic(w) == bench.TRAFFIC_RECORD["bytes_per_launch"]
     for key, other in (("n", 4096), ("k", 1), ("tile_band", 16), ("precision", "dual_bf16")):
         assert bench.recorded_traffic(dict(w, **{key: other})) is None
+    monkeypatch.setitem(bench.TRAFFIC_RECORD, "sha256", "0" * 64)
+    assert bench.recorded_traffic(w) is None
 
 
 def test_algorithmic_flops():

@@ -38,12 +38,12 @@ def ctx():
     return dmpt.context(0)
 
 
-def forward_with_tape(ctx, H, H1, n_occ, precision):
-    opts = dmpt.options(precision=precision, ckpt_every=1)
+def forward_with_tape(ctx, H, H1, n_occ, precision, ckpt_every=1):
+    opts = dmpt.options(precision=precision, ckpt_every=ckpt_every)
     k = 0 if H1 is None else (1 if H1.dim() == 2 else H1.shape[0])
     ws = torch.empty(ctx.workspace_size(H.shape[0], k, opts) + 256, dtype=torch.uint8,
                      device=DEV)
-    P, P1, info = ctx.sp2_response(H, H1, n_occ, precision=precision, ckpt_every=1,
+    P, P1, info = ctx.sp2_response(H, H1, n_occ, precision=precision, ckpt_every=ckpt_every,
                                    workspace=ws)
     torch.cuda.synchronize()
     return P, P1, info, ws
@@ -148,3 +148,94 @@ def test_adjoint_full_size_n4096(ctx):
     _, P1G = oracle.response_from_eigs(inst.eps.cpu().numpy(), inst.Q.cpu().numpy(),
                                        G.cpu().numpy(), inst.n_occ)
     assert rel(dLdH, P1G) < 1e-3, rel(dLdH, P1G)
+
+
+# --------------------------------------------------------------------------
+# Checkpoints every k S0 states (ckpt_every = k >= 2): the backward recomputes
+# each segment from its FP32 checkpoint with the forward's own products, so
+# the states, and therefore dL/dH, are bit-identical to the full tape's.
+
+@pytest.mark.parametrize("precision", ["dual_fp16", "dual_bf16"])
+@pytest.mark.parametrize("n,ck", [(256, 2), (300, 3), (300, 8), (520, 5)])
+def test_checkpointed_backward_equals_full_tape(ctx, precision, n, ck):
+    inst = make_workload(2, n=n)
+    G = torch.from_numpy(sym_gauss(n, 78)).to(DEV)
+    H = torch.from_numpy(inst.H).to(DEV)
+    P1_, _, info1, ws1 = forward_with_tape(ctx, H, None, inst.n_occ, precision, 1)
+    Pk, _, infok, wsk = forward_with_tape(ctx, H, None, inst.n_occ, precision, ck)
+    assert info1.converged and infok.converged
+    assert torch.equal(P1_, Pk) and info1.sigma == infok.sigma
+    g1 = ctx.sp2_backward(G, ws1)
+    gk = ctx.sp2_backward(G, wsk)
+    torch.cuda.synchronize()
+    assert torch.equal(g1, gk), (n, ck, precision)
+    # the checkpoints survive the backward: a second call gives the same result
+    gk2 = ctx.sp2_backward(G, wsk)
+    torch.cuda.synchronize()
+    assert torch.equal(gk, gk2)
+    _, P1G = oracle.response_sos(inst.H, G.cpu().numpy(), inst.n_occ)
+    assert rel(gk.cpu().numpy(), P1G) < TOL[precision]
+
+
+def test_checkpoint_workspace_is_smaller_and_replay_needs_the_tape(ctx):
+    n = 1024
+    o1 = dmpt.options(ckpt_every=1)
+    o8 = dmpt.options(ckpt_every=8)
+    assert ctx.workspace_size(n, 1, o8) < 0.4 * ctx.workspace_size(n, 1, o1)
+    inst = make_workload(2, n=300)
+    H = torch.from_numpy(inst.H).to(DEV)
+    H1 = torch.from_numpy(inst.H1).to(DEV)
+    _, _, info, ws = forward_with_tape(ctx, H, H1, inst.n_occ, "dual_fp16", 8)
+    assert info.converged
+    with pytest.raises(dmpt.DmptError) as e:          # replay reads every state
+        ctx.response_replay(H1, ws)
+    assert e.value.status == 1
+
+
+@pytest.mark.parametrize("ck", [1, 8])
+def test_config4_n4096_checkpoints(ctx, ck):
+    """Config 4 at its full size (n = 4096, n_occ = 2048, L = Tr[G P]) with
+    the full tape and with checkpoints every 8 S0 states: dL/dH against the
+    oracle (the response to G), against Tr[G P1(E_k)] for 8 random symmetric
+    directions from one k = 8 forward call, and a central finite difference
+    of the oracle's L along E_0."""
+    inst = make_workload(4, backend="torch", device="cuda")
+    n = inst.n
+    G = inst.H1[0]
+    E = torch.stack([torch.from_numpy(sym_gauss(n, 900 + i)) for i in range(8)]).to(DEV)
+    _, P1E, info, ws = forward_with_tape(ctx, inst.H, E, inst.n_occ, "dual_fp16", ck)
+    assert info.converged
+    dLdH = ctx.sp2_backward(G, ws)
+    torch.cuda.synchronize()
+    eps, Q = inst.eps.cpu().numpy(), inst.Q.cpu().numpy()
+    _, P1G = oracle.response_from_eigs(eps, Q, G.cpu().numpy(), inst.n_occ)
+    assert rel(dLdH.cpu().numpy(), P1G) < TOL["dual_fp16"]
+    lhs = torch.einsum("ij,kij->k", dLdH, E).cpu().numpy()
+    rhs = torch.einsum("ij,kij->k", G, P1E).cpu().numpy()
+    scale = np.abs(rhs).max()
+    assert np.abs(lhs - rhs).max() < 2e-3 * scale, (lhs, rhs)
+    if ck == 8:
+        Hn, Gn, E0 = inst.H.cpu().numpy(), G.cpu().numpy(), E[0].cpu().numpy()
+        L = lambda t: float(np.sum(Gn * oracle.density_matrix(Hn + t * E0, inst.n_occ)))
+        h = 1e-4
+        fd = (L(h) - L(-h)) / (2 * h)
+        assert abs(fd - lhs[0]) < 2e-3 * max(abs(fd), scale), (fd, lhs[0])
+
+
+@pytest.mark.parametrize("n,ck", [(520, 4), (1300, 8)])
+def test_checkpointed_backward_after_a_response_forward(ctx, n, ck):
+    """The forward also ran K = 3 response directions in each layer launch;
+    the recompute launches run the square alone.  The square's tiles come
+    first in every launch, so they keep their schedule and the recomputed
+    states, and dL/dH, stay bit-identical to the full tape's."""
+    inst = make_workload(3, n=n, k=3)
+    G = torch.from_numpy(sym_gauss(n, 79)).to(DEV)
+    H = torch.from_numpy(inst.H).to(DEV)
+    H1 = torch.from_numpy(inst.H1).to(DEV)
+    _, P1a, _, ws1 = forward_with_tape(ctx, H, H1, inst.n_occ, "dual_fp16", 1)
+    _, P1b, info, wsk = forward_with_tape(ctx, H, H1, inst.n_occ, "dual_fp16", ck)
+    assert info.converged and torch.equal(P1a, P1b)
+    g1 = ctx.sp2_backward(G, ws1)
+    gk = ctx.sp2_backward(G, wsk)
+    torch.cuda.synchronize()
+    assert torch.equal(g1, gk)

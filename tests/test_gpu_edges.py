@@ -42,10 +42,10 @@ def ctx():
     return dmpt.context(0)
 
 
-def solve_and_check(ctx, inst, precision, tol, p_floor=False):
+def solve_and_check(ctx, inst, precision, tol, p_floor=False, **kw):
     P, P1, info = ctx.sp2_response(torch.from_numpy(inst.H).to(DEV),
                                    torch.from_numpy(inst.H1).to(DEV), inst.n_occ,
-                                   precision=precision)
+                                   precision=precision, **kw)
     torch.cuda.synchronize()
     assert info.converged, (inst.name, precision, info.status, info.layers)
     Pr, P1r = oracle.response_from_eigs(inst.eps, inst.Q, inst.H1[0], inst.n_occ)
@@ -76,10 +76,50 @@ def test_ragged_sizes_fp32(ctx, n):
 @pytest.mark.parametrize("precision", ["dual_fp16", "dual_bf16"])
 @pytest.mark.parametrize("which", ["one_occupied", "one_virtual"])
 def test_extreme_occupations(ctx, precision, which):
+    """n_occ = 1 and n - 1 at the plain tolerance on P and P1.  With n - 1
+    levels occupied the default complement form runs the recursion on I - P
+    (one level), so the products' rounding scales with ||I - P||_F = 1."""
     n = 300
     n_occ = 1 if which == "one_occupied" else n - 1
     inst = make_instance(f"occ_{which}", n, n_occ, (-2.0, -0.1), (0.1, 2.0), seed=7200)
-    solve_and_check(ctx, inst, precision, TOL[precision], p_floor=True)
+    info = solve_and_check(ctx, inst, precision, TOL[precision])
+    assert info.hole == (which == "one_virtual")
+
+
+@pytest.mark.parametrize("precision", ["dual_fp16", "dual_bf16"])
+def test_extreme_occupation_particle_form(ctx, precision):
+    """The recursion on P as printed (hole_form = 0) with n - 1 levels
+    occupied: the rounding of the products is relative to ||P||_F =
+    sqrt(n - 1), not to ||P1||_F, so P1 is bounded by the operands' scale
+    (TOL / 20 ||P||_F) rather than by TOL ||P1||_F."""
+    n = 300
+    inst = make_instance("occ_one_virtual_particle", n, n - 1, (-2.0, -0.1), (0.1, 2.0),
+                         seed=7200)
+    info = solve_and_check(ctx, inst, precision, TOL[precision], p_floor=True, hole_form=0)
+    assert not info.hole
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "dual_fp16", "dual_bf16"])
+@pytest.mark.parametrize("n,n_occ", [(300, 240), (517, 400)])
+def test_complement_form_matches_oracle(ctx, precision, n, n_occ):
+    """More occupied than empty levels: the complement form against the
+    oracle.  In FP64 every branch before the converging layers is the
+    oracle's negated; the layer where IdErr first reaches rounding level may
+    differ by one (the two forms round different numbers)."""
+    inst = make_instance(f"hole{n}", n, n_occ, (-2.0, -0.1), (0.1, 2.0), seed=7500 + n)
+    if precision == "fp32":
+        lo, hi = oracle.gershgorin_bounds(inst.H)
+        tol = max(10 * 2.0 ** -24 * (hi - lo) / 0.2, 1e-5)
+    else:
+        tol = {"fp64": 1e-10}.get(precision, TOL.get(precision))
+    info = solve_and_check(ctx, inst, precision, tol)
+    assert info.hole
+    if precision == "fp64":
+        r = oracle.sp2_pt(inst.H, inst.H1, inst.n_occ)
+        assert abs(info.d0_layer - r.d0_layer) <= 1
+        nc = min(info.d0_layer, r.d0_layer)
+        assert info.sigma[: nc - 1] == [-x for x in r.sigma[: nc - 1]]
+        assert all(info.d0_layer + 2 <= d <= info.d0_layer + 8 for d in info.d1_layer)
 
 
 @pytest.mark.parametrize("precision", ["dual_fp16", "dual_bf16"])

@@ -55,14 +55,15 @@ def golden_module():
     return lambda name: json.load(open(os.path.join(GOLDEN, name)))
 
 
-def solve_fixture(ctx, g, precision, c_pt, c_d0, max_layers=30):
+def solve_fixture(ctx, g, precision, c_pt, c_d0, max_layers=30, hole_form=0):
     H = torch.from_numpy(np.diag(np.array(g["H_diag"]))).to(DEV)
     n = H.shape[0]
     H1 = torch.zeros(1, n, n, dtype=torch.float64, device=DEV)
     for i, j in g["H1_offdiag"]["pairs"]:
         H1[0, i, j] = H1[0, j, i] = g["H1_offdiag"]["value"]
     P, P1, info = ctx.sp2_response(H, H1, g["n_occ"], precision=precision, c_pt=c_pt,
-                                   c_d0=c_d0, max_layers=max_layers, raise_on_error=False)
+                                   c_d0=c_d0, max_layers=max_layers, raise_on_error=False,
+                                   hole_form=hole_form)
     torch.cuda.synchronize()
     return info
 
@@ -84,6 +85,25 @@ def test_dyadic_fixture_decisions(ctx, fixture, precision):
         assert info.froerr1_hist[0][int(layer) - 1] == pytest.approx(v, rel=tol)
     assert info.d1_layer == [g["d1_layer"]]
     assert info.layers == g["d1_layer"]
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_dyadic_fixture_complement_form(ctx, fixture, precision):
+    """3 of 5 levels occupied: with hole_form = 1 the recursion runs on I - P
+    (S_0 = I - (eps_N I - H) / (eps_N - eps_1), again exact dyadic values).
+    N_S, N_X trade places in the branch rule, so every sigma is negated,
+    while IdErr, FroErr^(0) and FroErr^(1) -- and so both stopping layers --
+    are the same numbers."""
+    g = fixture
+    info = solve_fixture(ctx, g, precision, g["c_pt"], g["c_d0"], hole_form=1)
+    tol = VAL_TOL[precision]
+    assert info.hole and info.status == 0 and info.converged
+    assert info.sigma == [-s for s in g["sigma"]]
+    np.testing.assert_allclose(info.iderr, [float(Fraction(s)) for s in g["iderr"]], rtol=tol)
+    assert info.froerr0 == pytest.approx(float(Fraction(g["froerr0_sq"])) ** 0.5, rel=tol)
+    for layer, v in g["froerr1"].items():
+        assert info.froerr1_hist[0][int(layer) - 1] == pytest.approx(v, rel=tol)
+    assert info.d0_layer == g["d0_layer"] and info.d1_layer == [g["d1_layer"]]
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
