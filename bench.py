@@ -39,15 +39,15 @@ N_DEFAULT = 8192
 K_DEFAULT = 3
 
 # DRAM traffic of the layer-product kernel, averaged over the 41 layer launches
-# of one full solve of the default workload (ncu dram__bytes_read.sum +
+# of one timed solve of the default workload (ncu dram__bytes_read.sum +
 # dram__bytes_write.sum, 1-pass capture; profiles/layer_tc2_kernel_dipole3_
 # n8192_k3_dram.md).  Valid only for that kernel source and that workload.
 TRAFFIC_RECORD = {
     "source": "paper_2203_09621_gb300/csrc/kernels_tc.cu",
-    "sha256": "9fafaca2d1fa4e30d3d89402dffa206595546eebd72f4013afcb17c38285deb2",
+    "sha256": "99d264322455882c65c493ed00c8ebd75d23fb9f9be558ef680d3e3342022707",
     "workload": {"n": 8192, "k": 3, "precision": "dual_fp16", "cta_pair": 1, "k_snake": 1,
                  "tile_band": 8, "accum_chunk": 0},
-    "bytes_per_launch": 9.8315e9 + 2.0589e9,
+    "bytes_per_launch": 9.8541e9 + 2.0587e9,
 }
 
 
@@ -449,6 +449,44 @@ def main():
     ms_max, rate = aggregate(ms, alg, world)
     value = rate / 1e12
 
+    # ---- e2e: the C ABI's host-buffer entry point (dmpt_sp2_response_host),
+    #      measured right after the resident steps, before the tuning and peak
+    #      measurements heat the part;
+    #      copies of every step's inputs and of its P1 inside the timed region
+    Hh = H.cpu().pin_memory()
+    H1h = H1.cpu().pin_memory()
+    P1h = [torch.empty(k, n, n, dtype=torch.float64).pin_memory() for _ in range(2)]
+    kwh = {key: v for key, v in kw.items() if key != "out"}
+    ctx.solve_host([Hh], [H1h], inst.n_occ, P1_out=[P1h[0]], **kwh)   # sizes the buffers
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e_steps = max(1, args.steps)
+    e0.record(stream)
+    _, P1e, _ = ctx.solve_host([Hh] * e_steps, [H1h] * e_steps, inst.n_occ,
+                               P1_out=[P1h[i % 2] for i in range(e_steps)], **kwh)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms, e2e_rate = aggregate(e0.elapsed_time(e1) / e_steps, alg, world)
+    e2e_val = e2e_rate / 1e12
+    e2e_same = bool(torch.equal(P1e[-1], P1.cpu()))
+    h2d = (H.numel() + H1.numel()) * 8
+    d2h = P1.numel() * 8
+    # the host link, measured alone: what the copies of one step cost if
+    # nothing overlapped them, against the step's exposed extra time
+    Htmp = torch.empty_like(H)
+    h2d_gbs, d2h_gbs = measure_copy_bandwidth(Hh, Htmp, stream)
+    del Htmp
+    copy_ms_serial = (h2d / (h2d_gbs * 1e9) + d2h / (d2h_gbs * 1e9)) * 1e3
+    # the same pipeline once more with per-launch timing of the layer products
+    # (outside the timed region): their device time per instance while the
+    # copies of the neighbouring instances run, against the resident solve's
+    _, _, hinfos = ctx.solve_host([Hh] * e_steps, [H1h] * e_steps, inst.n_occ,
+                                  P1_out=[P1h[i % 2] for i in range(e_steps)], timing=True, **kwh)
+    torch.cuda.synchronize()
+    kernel_ms_pipeline = sum(i.ms_layers for i in hinfos) / len(hinfos)
+
     # ---- the autotuner's choice for this workload (reported, not used by the
     #      timed steps, whose configuration is the one in `config`)
     tune = None
@@ -485,42 +523,6 @@ def main():
             peak_source = "measured in this run: torch.matmul bf16 8192^3 back to back (sustained)"
     achieved = tinfo.alg_flops / (tinfo.ms_layers * 1e-3) / 1e12 if tinfo.ms_layers else None
     executed = tinfo.mma_flops / (tinfo.ms_layers * 1e-3) / 1e12 if tinfo.ms_layers else None
-
-    # ---- e2e: the C ABI's host-buffer entry point (dmpt_sp2_response_host),
-    #      copies of every step's inputs and of its P1 inside the timed region
-    Hh = H.cpu().pin_memory()
-    H1h = H1.cpu().pin_memory()
-    P1h = [torch.empty(k, n, n, dtype=torch.float64).pin_memory() for _ in range(2)]
-    kwh = {key: v for key, v in kw.items() if key != "out"}
-    ctx.solve_host([Hh], [H1h], inst.n_occ, P1_out=[P1h[0]], **kwh)   # sizes the buffers
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    torch.cuda.synchronize()
-    e_steps = max(1, args.steps)
-    e0.record(stream)
-    _, P1e, _ = ctx.solve_host([Hh] * e_steps, [H1h] * e_steps, inst.n_occ,
-                               P1_out=[P1h[i % 2] for i in range(e_steps)], **kwh)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    e2e_ms, e2e_rate = aggregate(e0.elapsed_time(e1) / e_steps, alg, world)
-    e2e_val = e2e_rate / 1e12
-    e2e_same = bool(torch.equal(P1e[-1], P1.cpu()))
-    h2d = (H.numel() + H1.numel()) * 8
-    d2h = P1.numel() * 8
-    # the host link, measured alone: what the copies of one step cost if
-    # nothing overlapped them, against the step's exposed extra time
-    Htmp = torch.empty_like(H)
-    h2d_gbs, d2h_gbs = measure_copy_bandwidth(Hh, Htmp, stream)
-    del Htmp
-    copy_ms_serial = (h2d / (h2d_gbs * 1e9) + d2h / (d2h_gbs * 1e9)) * 1e3
-    # the same pipeline once more with per-launch timing of the layer products
-    # (outside the timed region): their device time per instance while the
-    # copies of the neighbouring instances run, against the resident solve's
-    _, _, hinfos = ctx.solve_host([Hh] * e_steps, [H1h] * e_steps, inst.n_occ,
-                                  P1_out=[P1h[i % 2] for i in range(e_steps)], timing=True, **kwh)
-    torch.cuda.synchronize()
-    kernel_ms_pipeline = sum(i.ms_layers for i in hinfos) / len(hinfos)
 
     # ---- other precision forms, one timed solve each (time-to-solution)
     forms = {}
@@ -779,6 +781,9 @@ def main():
                     "api": "dmpt_sp2_response_host", "equals_device_result": e2e_same,
                     "h2d_gbs": h2d_gbs, "d2h_gbs": d2h_gbs, "copy_ms_if_serial": copy_ms_serial,
                     "exposed_ms_per_step": e2e_ms - ms_max,
+                    # the pipeline hides every copy but the first copy-in and the
+                    # last copy-out of the sequence
+                    "unhidden_copy_ms_per_step": copy_ms_serial / e_steps,
                     "layer_kernel_ms_per_step_in_pipeline": kernel_ms_pipeline,
                     "layer_kernel_ms_per_step_resident": tinfo.ms_layers},
             "gpu_launches": launches_per_step * args.steps,
