@@ -371,6 +371,9 @@ def main():
                     help="layers of the FP64 form timed (its full solve takes minutes at n = 8192)")
     ap.add_argument("--fp64-full", action="store_true",
                     help="run the FP64 form to convergence (about two minutes at n = 8192)")
+    ap.add_argument("--paper-sizes", action="store_true",
+                    help="also solve the paper's Fig. 4 sizes (n = 5904 ... 19008, n_occ = 2n/3, "
+                         "K = 1) once each, as context beside its A100 figures")
     ap.add_argument("--no-peaks", action="store_true",
                     help="skip measuring the FP16 / FP64 matmul peaks used as denominators")
     ap.add_argument("--oracle-layers", type=int, default=1)
@@ -709,6 +712,42 @@ def main():
             del aws, dLdH
         del a_inst
 
+    # ---- the paper's Fig. 4 sizes (context): n_occ = 2n/3 as in its water
+    #      boxes, one perturbation, gap 0.2; one solve each after one warm-up
+    paper_sizes = None
+    if args.paper_sizes and rank == 0:
+        from paper_2203_09621_gb300.workloads import make_instance
+        from oracle.sos import response_columns
+        # the paper's dual-FP16 rates on one A100, converted to 2 flops per FMA
+        a100 = {5904: 158.4, 10266: 172.2, 12720: 178.0, 16512: 197.2, 19008: 238.0}
+        paper_sizes = []
+        for npap, ref in a100.items():
+            pi = make_instance(f"paper-n{npap}", npap, round(2 * npap / 3), (-2.0, -0.1),
+                               (0.1, 2.0), "gauss", 1, 0.01, seed=7000 + npap,
+                               backend="torch", device=dev)
+            ctx.sp2_response(pi.H, pi.H1, pi.n_occ, precision=args.precision)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            Pp, P1p, pinf = ctx.sp2_response(pi.H, pi.H1, pi.n_occ, precision=args.precision)
+            b.record(stream)
+            torch.cuda.synchronize()
+            pms = a.elapsed_time(b)
+            rec = {"n": npap, "n_occ": pi.n_occ, "ms": pms, "layers": pinf.layers,
+                   "d0_layer": pinf.d0_layer, "hole_form": pinf.hole,
+                   "tflops": pinf.alg_flops / (pms * 1e-3) / 1e12,
+                   "paper_1xA100_tflops_2_per_fma": ref}
+            if not args.no_check:
+                cols = [0, 1, pi.n_occ - 1, pi.n_occ, npap - 1]
+                want = response_columns(pi.eps.cpu().numpy(), pi.Q.cpu().numpy(),
+                                        pi.H1[0].cpu().numpy(), pi.n_occ, cols)
+                got = P1p[0][:, cols].cpu().numpy()
+                rec["rel_err_P1_sampled_columns"] = float(np.linalg.norm(got - want) /
+                                                          np.linalg.norm(want))
+            paper_sizes.append(rec)
+            del pi, Pp, P1p
+        torch.cuda.empty_cache()
+
     # ---- accuracy against the oracle: the whole P and every P1_k, from the
     #      known eigenpairs (outside every timed region)
     accuracy = None
@@ -764,6 +803,7 @@ def main():
             "time_to_solution_ms": ms_max,
             "layers": infos[0].layers, "d0_layer": infos[0].d0_layer,
             "accuracy": accuracy,
+            "paper_sizes": paper_sizes,
             "forms": forms,
             "adjoint": adjoint,
             "batch": batch,

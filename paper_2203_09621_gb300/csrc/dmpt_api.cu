@@ -176,12 +176,14 @@ __global__ void state_init_kernel(State* st, int k, int max_layers, int precisio
 // bounds, the tape geometry and the number of S0 updates).
 __global__ void adj_state_reset_kernel(State* st) {
   st->adj_seg_a = 0;
+  st->item_base = 0;
   st->done = 0;
   st->status = DMPT_OK;
   st->timeout_flag = 0;
 }
 
 __global__ void replay_reset_kernel(State* st, int k) {
+  st->item_base = 0;
   st->done = 0;
   st->status = DMPT_OK;
   st->timeout_flag = 0;

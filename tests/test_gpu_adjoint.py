@@ -239,3 +239,38 @@ def test_checkpointed_backward_after_a_response_forward(ctx, n, ck):
     gk = ctx.sp2_backward(G, wsk)
     torch.cuda.synchronize()
     assert torch.equal(g1, gk)
+
+
+def _ckpt_cases(count=10, seed=3131):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(40, 900))
+        out.append((i, n, int(rng.integers(2, 10)), int(rng.integers(0, 4)),
+                    str(rng.choice(["dual_fp16", "dual_bf16"])), int(rng.integers(0, 2)),
+                    int(rng.choice([0, 4, 8]))))
+    return out
+
+
+@pytest.mark.parametrize("case", _ckpt_cases(), ids=lambda c: f"c{c[0]}_n{c[1]}_k{c[2]}_d{c[3]}")
+def test_checkpoint_soak_bit_identical(ctx, case):
+    """Random sizes, checkpoint intervals, response counts, precisions, tile
+    shapes and bands: the checkpointed backward equals the full tape's bit
+    for bit."""
+    i, n, ck, kdir, precision, cta_pair, band = case
+    inst = make_instance(f"cks{i}", n, n // 2, (-2.0, -0.1), (0.1, 2.0), seed=9100 + i,
+                         k=max(kdir, 1))
+    H = torch.from_numpy(inst.H).to(DEV)
+    H1 = torch.from_numpy(inst.H1[:kdir]).to(DEV) if kdir else None
+    G = torch.from_numpy(sym_gauss(n, 9200 + i)).to(DEV)
+    kw = dict(cta_pair=cta_pair, tile_band=band)
+    outs = []
+    for c in (1, ck):
+        opts = dmpt.options(precision=precision, ckpt_every=c, **kw)
+        ws = torch.empty(ctx.workspace_size(n, kdir, opts) + 256, dtype=torch.uint8, device=DEV)
+        _, _, info = ctx.sp2_response(H, H1, inst.n_occ, precision=precision, ckpt_every=c,
+                                      workspace=ws, **kw)
+        assert info.converged
+        outs.append(ctx.sp2_backward(G, ws, **kw))
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0], outs[1]), case

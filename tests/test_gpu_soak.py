@@ -5,9 +5,10 @@ boundary sizes), the occupation (including 0, 1, n - 1 and n), the number of
 directions k in [0, 8], the precision and the scheduling options (tile
 shape, K-snake, tile band, chunk length).  Every case is checked against the
 oracle: P and each P1 within the form's tolerance, with the floor relative
-to ||P||_F that uneven occupations need (FP32: its derived bound
-10 u (eps_N - eps_1) / gap times ||P||_F; dual forms: TOL / 20 ||P||_F as in
-the extreme-occupation tests), and the trivial occupations exactly.
+to the operands' scale that uneven occupations need (FP32: its derived bound
+10 u (eps_N - eps_1) / gap times ||P||_F; dual forms: TOL / 20 times the
+norm of the projector the recursion runs on, sqrt(min(n_occ, n - n_occ))
+with the default complement form), and the trivial occupations exactly.
 """
 
 import numpy as np
@@ -81,12 +82,16 @@ def test_soak(ctx, case):
         tol = TOL[precision]
     nP = np.linalg.norm(Pr)
     assert np.linalg.norm(P.cpu().numpy() - Pr) <= tol * nP, case
+    # the dual forms' operands are S0 -> P, or I - P in the complement form
+    # that runs by default when more than half the levels are occupied
+    n_ops = np.sqrt(min(n_occ, n - n_occ)) if precision != "fp32" else nP
+    assert info.hole == (2 * n_occ > n)
     for j in range(k):
         _, P1r = oracle.response_from_eigs(inst.eps, inst.Q, inst.H1[j], n_occ)
         err = np.linalg.norm(P1[j].cpu().numpy() - P1r)
         # floor relative to the operands' scale ||P||_F: the FP32 bound
         # 10 u (eps_N - eps_1) / gap is itself that scale's bound; the dual
         # forms' floor is the half-filled error scale (see the edge-case tests)
-        floor = tol * nP if precision == "fp32" else tol / 20 * nP
+        floor = tol * nP if precision == "fp32" else tol / 20 * n_ops
         bound = max(tol * np.linalg.norm(P1r), floor)
         assert err <= bound, (case, j, err / max(np.linalg.norm(P1r), 1e-300))
