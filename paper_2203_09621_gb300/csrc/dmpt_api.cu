@@ -949,7 +949,8 @@ dmpt_status dmpt_sp2_backward(dmpt_handle h, const double* G, int64_t n, int64_t
 }
 
 // Batch scratch: [state offsets, all-done flag] [GroupInst table]
-// [GroupDecide table] [group timeout flag], each 256-byte aligned.
+// [GroupDecide table] [group timeout flag] [grouped item queue], each
+// 256-byte aligned.
 static size_t batch_poll_bytes(int count) {
   return ((size_t)count * sizeof(long long) + 2 * sizeof(int) + 255) & ~size_t(255);
 }
@@ -959,8 +960,10 @@ static size_t batch_ginst_bytes(int count) {
 static size_t batch_gdec_bytes(int count) {
   return ((size_t)count * sizeof(GroupDecide) + 255) & ~size_t(255);
 }
+static size_t batch_queue_bytes() { return (sizeof(GroupQueue) + 255) & ~size_t(255); }
 static size_t batch_scratch_bytes(int count) {
-  return batch_poll_bytes(count) + batch_ginst_bytes(count) + batch_gdec_bytes(count) + 256;
+  return batch_poll_bytes(count) + batch_ginst_bytes(count) + batch_gdec_bytes(count) + 256 +
+         batch_queue_bytes();
 }
 
 size_t dmpt_workspace_size_batch(int count, const int64_t* n, int k, const dmpt_options* o) {
@@ -1047,6 +1050,7 @@ static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
   GroupInst* d_ginst = (GroupInst*)(base + batch_poll_bytes(count));
   GroupDecide* d_gdec = (GroupDecide*)((char*)d_ginst + batch_ginst_bytes(count));
   int* d_gtimeout = (int*)((char*)d_gdec + batch_gdec_bytes(count));
+  GroupQueue* d_gqueue = (GroupQueue*)((char*)d_gtimeout + 256);
   if (n_active > 0 &&
       (e = cudaMemcpyAsync(d_offs, act_offs.data(), sizeof(long long) * n_active,
                            cudaMemcpyHostToDevice, h->origin)) != cudaSuccess)
@@ -1118,6 +1122,7 @@ static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
         (e = cudaMemcpyAsync(d_gdec, gd.data(), sizeof(GroupDecide) * gd.size(),
                              cudaMemcpyHostToDevice, h->origin)) != cudaSuccess ||
         (e = cudaMemsetAsync(d_gtimeout, 0, sizeof(int), h->origin)) != cudaSuccess ||
+        (e = cudaMemsetAsync(d_gqueue, 0, sizeof(GroupQueue), h->origin)) != cudaSuccess ||
         (e = cudaStreamSynchronize(h->origin)) != cudaSuccess)
       return cuda_fail(h, e, "batch group tables");
   }
@@ -1134,9 +1139,10 @@ static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
   cudaError_t ce = cudaEventRecord(h->fork, h->origin);
   if (grouped) {
     ce = launch_layer_tc_group(d_ginst, n_group, o->precision == DMPT_DUAL_BF16, d_gtimeout,
-                               o->timeout_s, o->accum_chunk, o->k_snake, o->tile_band,
+                               d_gqueue, o->timeout_s, o->accum_chunk, o->k_snake, o->tile_band,
                                h->sm_count, h->origin);
-    if (ce == cudaSuccess) ce = launch_decide_group(d_gdec, n_group, d_gtimeout, h->origin);
+    if (ce == cudaSuccess)
+      ce = launch_decide_group(d_gdec, n_group, d_gtimeout, d_gqueue, h->origin);
   }
   for (int i = 0; i < count && ce == cudaSuccess && !grouped; ++i) {
     if (!active[i]) continue;

@@ -199,6 +199,21 @@ struct GroupDecide {
   int64_t entries;
 };
 constexpr int kGroupMax = 1024;   // instances per grouped launch
+// Dynamic item queue of a grouped launch: the leader CTA of each pair claims
+// its next item from `counter` and publishes it in its ring of `slot`s, where
+// the pair's other roles (MMA issuer, the peer CTA's producer, both CTAs'
+// epilogues) read it.  A slot holds (epoch + 1) << 40 | (claim index / ring
+// & 0xFF) << 32 | item (0xFFFFFFFF: no more items), so a stale value from an
+// earlier launch or lap never matches.  The decide step after each grouped
+// launch resets `counter` and advances `epoch`.
+constexpr int kQueueRing = 64;     // claims a pair keeps in flight (>> its pipeline depth)
+constexpr int kQueuePairs = 128;   // CTA pairs per grouped launch (<= 256 SMs)
+struct GroupQueue {
+  unsigned counter;
+  unsigned epoch;
+  unsigned pad[62];
+  unsigned long long slot[kQueuePairs][kQueueRing];
+};
 // Fills `gi` for the instance whose workspace is `ws` (false: no tensor map).
 bool make_group_inst(const Layout& L, void* ws, int sm_count, GroupInst* gi);
 // Partial-sum entries per job and the flops of one single-term pass of the
@@ -207,12 +222,12 @@ void pair_tile_info(const Layout& L, int64_t* entries, double* pass_flops);
 // One layer of every instance in `inst` (device array of `count`) in one
 // launch; a bounded wait that expires sets *group_timeout.
 cudaError_t launch_layer_tc_group(const GroupInst* inst, int count, bool bf16, int* group_timeout,
-                                  double timeout_s, int accum_chunk_k, int k_snake, int band,
-                                  int sm_count, cudaStream_t s);
+                                  GroupQueue* queue, double timeout_s, int accum_chunk_k,
+                                  int k_snake, int band, int sm_count, cudaStream_t s);
 // Decide step of every instance (device array of `count`), one block each; a
 // set *group_timeout marks every instance timed out.
 cudaError_t launch_decide_group(const GroupDecide* args, int count, const int* group_timeout,
-                                cudaStream_t s);
+                                GroupQueue* queue, cudaStream_t s);
 
 enum DecideMode {
   kDecideInit = 0,

@@ -707,9 +707,14 @@ __global__ void __launch_bounds__(256) decide_kernel(State* st, const double* __
 
 // Layer decide of every instance of a grouped launch, one block each.
 __global__ void __launch_bounds__(256) decide_group_kernel(const GroupDecide* __restrict__ args,
-                                                           const int* __restrict__ group_timeout) {
+                                                           const int* __restrict__ group_timeout,
+                                                           GroupQueue* queue) {
   __shared__ double red[kNQ * 256];
   __shared__ double sums[kMaxK + 1][kNQ];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {   // the next grouped launch starts a new queue
+    queue->counter = 0u;
+    queue->epoch += 1u;
+  }
   const GroupDecide a = args[blockIdx.x];
   if (threadIdx.x == 0 && *group_timeout && !a.st->done) a.st->timeout_flag = 1;
   __syncthreads();
@@ -717,9 +722,9 @@ __global__ void __launch_bounds__(256) decide_group_kernel(const GroupDecide* __
 }
 
 cudaError_t launch_decide_group(const GroupDecide* args, int count, const int* group_timeout,
-                                cudaStream_t s) {
+                                GroupQueue* queue, cudaStream_t s) {
   if (count < 1) return cudaSuccess;
-  decide_group_kernel<<<count, 256, 0, s>>>(args, group_timeout);
+  decide_group_kernel<<<count, 256, 0, s>>>(args, group_timeout, queue);
   return cudaGetLastError();
 }
 

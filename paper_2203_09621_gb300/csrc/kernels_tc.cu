@@ -1399,10 +1399,64 @@ __device__ __forceinline__ GroupItem group_item(const GroupInst* __restrict__ in
   return r;
 }
 
+// Dynamic item assignment of a grouped launch (GroupQueue): a pair takes
+// its next item when its producer is ready for one, so pairs that drew short
+// items take more of them.  Everything an item computes still depends on the
+// item alone, so results stay bit-identical to single-instance launches.
+constexpr uint32_t kNoItem = 0xFFFFFFFFu;
+
+__device__ __forceinline__ unsigned long long claim_code(unsigned epoch, int64_t j, uint32_t g) {
+  return ((unsigned long long)((epoch + 1u) & 0xFFFFFFu) << 40) |
+         ((unsigned long long)((j / kQueueRing) & 0xFF) << 32) | g;
+}
+
+// Leader producer: claim the pair's j-th item and publish it.
+__device__ __forceinline__ uint32_t claim_next(GroupQueue* gq, int64_t pair, int64_t j,
+                                               unsigned epoch, int64_t items) {
+  uint32_t g = atomicAdd(&gq->counter, 1u);
+  if ((int64_t)g >= items) g = kNoItem;
+  volatile unsigned long long* slot = &gq->slot[pair][j % kQueueRing];
+  __threadfence();
+  *slot = claim_code(epoch, j, g);
+  return g;
+}
+
+// The pair's j-th item as its leader published it; false when the bounded
+// wait expires (it then raises both abort flags) or another role aborted.
+__device__ __forceinline__ bool claim_wait(GroupQueue* gq, int64_t pair, int64_t j,
+                                           unsigned epoch, uint64_t limit_ns,
+                                           volatile int* abort_smem, int* timeout_global,
+                                           uint32_t* g) {
+  volatile unsigned long long* slot = &gq->slot[pair][j % kQueueRing];
+  const unsigned long long want = claim_code(epoch, j, 0u) >> 32;
+  unsigned long long v = *slot;
+  if ((v >> 32) == want) {
+    *g = (uint32_t)v;
+    return true;
+  }
+  const uint64_t t0 = gtimer();
+  uint32_t it = 0;
+  while (true) {
+    v = *slot;
+    if ((v >> 32) == want) {
+      *g = (uint32_t)v;
+      return true;
+    }
+    if ((++it & 63) == 0) {
+      if (*abort_smem) return false;
+      if (gtimer() - t0 > limit_ns) {
+        *abort_smem = 1;
+        atomicExch(timeout_global, 1);
+        return false;
+      }
+    }
+  }
+}
+
 template <bool BF16>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     layer_tc2_group_kernel(const GroupInst* __restrict__ inst, int count, int* group_timeout,
-                           uint64_t limit_ns, int chunk, int k_snake, int band) {
+                           GroupQueue* gq, uint64_t limit_ns, int chunk, int k_snake, int band) {
   using CV = Cvt<BF16>;
   using H16 = typename CV::T;
   extern __shared__ uint8_t smem_raw[];
@@ -1436,11 +1490,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
   __syncthreads();
   const int64_t items = first[count];
   if (items == 0) return;   // every CTA takes this exit together
+  const unsigned epoch = *(volatile unsigned*)&gq->epoch;   // fixed during the launch
 
   const uint32_t rank = cluster_rank();
   const bool leader = rank == 0;
   const int64_t pair = blockIdx.x >> 1;
-  const int64_t npairs = gridDim.x >> 1;
 
   uint64_t* bars = reinterpret_cast<uint64_t*>(misc);
   const uint32_t bar_full = smem_u32(bars);
@@ -1488,7 +1542,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
       RingPos rg;
       bool ok = true;
       int last_inst = -1;
-      for (int64_t g = pair; g < items && ok; g += npairs) {
+      for (int64_t j = 0; ok; ++j) {
+        uint32_t g;
+        if (leader)
+          g = claim_next(gq, pair, j, epoch, items);
+        else if (!claim_wait(gq, pair, j, epoch, limit_ns, abort_flag, timeout_global, &g))
+          break;
+        if (g == kNoItem) break;
         const GroupItem itm = group_item(inst, first, jmask, count, g, k_snake);
         const GroupInst& gi = inst[itm.inst];
         if (itm.inst != last_inst) {
@@ -1510,7 +1570,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     if (leader && lane == 0) {
       RingPos rg, tb;
       bool ok = true;
-      for (int64_t g = pair; g < items && ok; g += npairs) {
+      for (int64_t j = 0; ok; ++j) {
+        uint32_t g;
+        if (!claim_wait(gq, pair, j, epoch, limit_ns, abort_flag, timeout_global, &g)) break;
+        if (g == kNoItem) break;
         const GroupItem itm = group_item(inst, first, jmask, count, g, k_snake);
         ok = mma_item<BF16>(rg, tb, itm.passes * itm.kblocks, itm.kblocks, chunk, tmem_base,
                             ring, bar_full, bar_empty, bar_tfull, bar_tempty, limit_ns,
@@ -1534,7 +1597,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     int ab = 0;
     uint32_t abphase = 0;
     bool alive = true;
-    for (int64_t g = pair; g < items && alive; g += npairs) {
+    for (int64_t j = 0; alive; ++j) {
+      // lane 0 of each warp reads the claim; every epilogue warp agrees on it
+      uint32_t g = kNoItem;
+      bool got = true;
+      if (lane == 0) got = claim_wait(gq, pair, j, epoch, limit_ns, abort_flag, timeout_global, &g);
+      g = __shfl_sync(0xFFFFFFFFu, g, 0);
+      got = __shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0) != 0;
+      if (!epi_all(got && !*abort_flag)) {
+        alive = false;
+        break;
+      }
+      if (g == kNoItem) break;
       const GroupItem itm = group_item(inst, first, jmask, count, g, k_snake);
       const GroupInst& gi = inst[itm.inst];
       const State* sti = gi.st;
@@ -1750,10 +1824,11 @@ bool make_group_inst(const Layout& L, void* ws, int sm_count, GroupInst* gi) {
 }
 
 cudaError_t launch_layer_tc_group(const GroupInst* inst, int count, bool bf16, int* group_timeout,
-                                  double timeout_s, int accum_chunk_k, int k_snake, int band,
-                                  int sm_count, cudaStream_t s) {
+                                  GroupQueue* queue, double timeout_s, int accum_chunk_k,
+                                  int k_snake, int band, int sm_count, cudaStream_t s) {
   using namespace tc;
-  if (count < 1 || count > kGroupMax) return cudaErrorInvalidValue;
+  if (count < 1 || count > kGroupMax || !queue || sm_count / 2 > kQueuePairs)
+    return cudaErrorInvalidValue;
   const int smem =
       P_SMEM_BYTES + (count + 1) * (int)sizeof(int64_t) + count * (int)sizeof(uint32_t);
   if (device_setup() == 0) return cudaErrorInvalidDevice;
@@ -1762,11 +1837,11 @@ cudaError_t launch_layer_tc_group(const GroupInst* inst, int count, bool bf16, i
   const int chunk = ck / BK < 1 ? 1 : ck / BK;
   const int grid = 2 * (sm_count / 2);
   if (bf16)
-    layer_tc2_group_kernel<true><<<grid, NUM_THREADS, smem, s>>>(inst, count, group_timeout,
-                                                                 limit_ns, chunk, k_snake, band);
+    layer_tc2_group_kernel<true><<<grid, NUM_THREADS, smem, s>>>(
+        inst, count, group_timeout, queue, limit_ns, chunk, k_snake, band);
   else
-    layer_tc2_group_kernel<false><<<grid, NUM_THREADS, smem, s>>>(inst, count, group_timeout,
-                                                                  limit_ns, chunk, k_snake, band);
+    layer_tc2_group_kernel<false><<<grid, NUM_THREADS, smem, s>>>(
+        inst, count, group_timeout, queue, limit_ns, chunk, k_snake, band);
   return cudaGetLastError();
 }
 
