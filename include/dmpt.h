@@ -139,6 +139,11 @@ typedef struct {
                            the rounding of the products small next to the
                            response when few levels are empty; 0: always the
                            recursion on P as printed                         */
+  int group_tile_n;     /* batches on the grouped kernel: tile width 256
+                           (default: 256 x 256 pair tiles, instances padded to
+                           a multiple of 256) or 128 (256 x 128 tiles, four
+                           tensor-memory accumulators, instances padded to a
+                           multiple of 128)                                   */
 } dmpt_options;
 
 /* Filled on the host by dmpt_sp2_response (when info != NULL). */

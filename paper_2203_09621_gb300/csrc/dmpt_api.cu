@@ -40,7 +40,8 @@ struct dmpt_ctx {
   struct BatchTune {
     std::vector<int64_t> Np;   // sorted padded sizes
     int k, precision;
-    int path;                  // 0 grouped, 1 per-instance CTA pairs, 2 per-instance single CTAs
+    int path;                  // 0 grouped, 1 per-instance CTA pairs, 2 per-instance single
+                               // CTAs, 3 grouped on 256 x 128 tiles
   };
   std::vector<BatchTune> batch_tune;
 };
@@ -111,19 +112,20 @@ bool valid_options(const dmpt_options* o) {
   if (o->autotune < 0 || o->autotune > 1) return false;
   if (o->round_align < 0 || o->round_align > 1) return false;
   if (o->hole_form < 0 || o->hole_form > 1) return false;
+  if (o->group_tile_n != 128 && o->group_tile_n != 256) return false;
   return true;
 }
 
 // Workspace geometry for (n, k) under options o: response slots (at least
 // one when S0 states are kept, for the adjoint) and tape capacity.
-Layout layout_for(int64_t n, int k, const dmpt_options* o) {
+Layout layout_for(int64_t n, int k, const dmpt_options* o, int pad = kPad) {
   const int ck = o->ckpt_every;
   const int slots = o->order >= 2 ? o->order * k : ((ck >= 1 && k == 0) ? 1 : k);
   // ck = 1: every S0 state's 16-bit copies; ck >= 2: FP32 checkpoints of every
   // ck-th state plus a ck-state tape for the segment the backward recomputes
   const int tape_states = ck == 1 ? o->max_layers + 2 : (ck >= 2 ? ck : 0);
   const int ckpt_slots = ck >= 2 ? o->max_layers / ck + 1 : 0;
-  return make_layout(n, slots, o->precision, tape_states, ckpt_slots);
+  return make_layout(n, slots, o->precision, tape_states, ckpt_slots, pad);
 }
 
 // The forward's product options, kept for the states the backward recomputes.
@@ -347,6 +349,7 @@ void dmpt_default_options(dmpt_options* o) {
   o->tile_band = 8;
   o->round_align = 1;
   o->hole_form = 1;
+  o->group_tile_n = 256;
 }
 
 const char* dmpt_status_string(dmpt_status s) {
@@ -981,7 +984,8 @@ size_t dmpt_workspace_size_batch(int count, const int64_t* n, int k, const dmpt_
 }
 
 // path: -1 = the default rule (grouped launch for dual forms on CTA pairs),
-// 0 = grouped, 1 = one launch per instance on its own stream.
+// 0 = grouped, 1 = one launch per instance on its own stream, 3 = grouped on
+// 256 x 128 tiles with the instances padded to a multiple of 128.
 static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
                               const double* const* H1, int k, const int64_t* n,
                               const int64_t* ld, const int64_t* n_occ, const dmpt_options* o,
@@ -1027,12 +1031,22 @@ static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
   std::vector<Layout> L(count);
   std::vector<long long> offs(count);
   std::vector<int> active(count, 0);
+  int n_act = 0;
+  for (int i = 0; i < count; ++i) {
+    active[i] = (n_occ[i] > 0 && n_occ[i] < n[i]) ? 1 : 0;
+    n_act += active[i];
+  }
+  // dual precision on CTA pairs: one grouped launch per layer step for all
+  // instances (GroupInst table, batched decide); otherwise one launch per
+  // instance on its own stream
+  const bool can_group = dual && o->cta_pair && o->order == 1 && n_act > 0 && n_act <= kGroupMax;
+  // 256 x 128 tiles, padding to 128
+  const bool n128 = (path == 3 || (path == -1 && o->group_tile_n == 128)) && can_group;
   size_t off = batch_scratch_bytes(count);
   for (int i = 0; i < count; ++i) {
-    L[i] = layout_for(n[i], k, o);
+    L[i] = layout_for(n[i], k, o, n128 ? 128 : kPad);
     offs[i] = (long long)off;
     off += (L[i].total + 255) & ~size_t(255);
-    active[i] = (n_occ[i] > 0 && n_occ[i] < n[i]) ? 1 : 0;
   }
   // fork: the origin stream and every instance stream follow the caller's stream
   if ((e = cudaEventRecord(h->fork, caller)) != cudaSuccess) return cuda_fail(h, e, "batch fork");
@@ -1042,11 +1056,7 @@ static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
   for (int i = 0; i < count; ++i)
     if (active[i]) act_offs.push_back(offs[i]);
   const int n_active = (int)act_offs.size();
-  // dual precision on CTA pairs: one grouped launch per layer step for all
-  // instances (GroupInst table, batched decide); otherwise one launch per
-  // instance on its own stream
-  const bool grouped = path != 1 && dual && o->cta_pair && o->order == 1 && n_active > 0 &&
-                       n_active <= kGroupMax;
+  const bool grouped = path != 1 && can_group;
   GroupInst* d_ginst = (GroupInst*)(base + batch_poll_bytes(count));
   GroupDecide* d_gdec = (GroupDecide*)((char*)d_ginst + batch_ginst_bytes(count));
   int* d_gtimeout = (int*)((char*)d_gdec + batch_gdec_bytes(count));
@@ -1108,9 +1118,9 @@ static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
     for (size_t j = 0; j < order.size(); ++j) {
       const int i = order[j];
       void* ws = base + offs[i];
-      if (!make_group_inst(L[i], ws, h->sm_count, &gi[j]))
+      if (!make_group_inst(L[i], ws, h->sm_count, &gi[j], n128))
         return fail(h, DMPT_ECUDA, "dmpt_sp2_response_batch: %s", "tensor map encoding failed");
-      pair_tile_info(L[i], &entries[i], &pass_flops[i]);
+      pair_tile_info(L[i], &entries[i], &pass_flops[i], n128);
       gd[j].st = gi[j].st;
       gd[j].partials = gi[j].partials;
       gd[j].ptiles = gi[j].ptiles;
@@ -1140,7 +1150,7 @@ static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
   if (grouped) {
     ce = launch_layer_tc_group(d_ginst, n_group, o->precision == DMPT_DUAL_BF16, d_gtimeout,
                                d_gqueue, o->timeout_s, o->accum_chunk, o->k_snake, o->tile_band,
-                               h->sm_count, h->origin);
+                               h->sm_count, h->origin, n128);
     if (ce == cudaSuccess)
       ce = launch_decide_group(d_gdec, n_group, d_gtimeout, d_gqueue, h->origin);
   }
@@ -1248,9 +1258,10 @@ dmpt_status dmpt_sp2_response_batch(dmpt_handle h, int count, const double* cons
         count >= 1 && n != nullptr))
     return batch_impl(h, count, H, H1, k, n, ld, n_occ, o, P, P1, info, workspace, ws_bytes,
                       stream, -1);
-  // autotuned batch: the grouped launch on CTA pairs, or one launch per
-  // instance with 256 x 256 (CTA-pair) or 128 x 256 (single-CTA) tiles;
-  // chosen once per batch signature by timing a short probe of each
+  // autotuned batch: the grouped launch on CTA pairs with 256 x 256 or
+  // 256 x 128 tiles, or one launch per instance with 256 x 256 (CTA-pair) or
+  // 128 x 256 (single-CTA) tiles; chosen once per batch signature by timing a
+  // short probe of each
   std::vector<int64_t> sig(count);
   for (int i = 0; i < count; ++i) sig[i] = n[i] >= 1 ? make_layout(n[i], k, o->precision).Np : 0;
   std::sort(sig.begin(), sig.end());
@@ -1269,11 +1280,12 @@ dmpt_status dmpt_sp2_response_batch(dmpt_handle h, int count, const double* cons
     p.max_layers = 3;
     double best_ms = 1e300;
     for (int rep = 0; rep < 2; ++rep) {   // the first round warms every path up
-      for (int cand = 0; cand < 3; ++cand) {
+      for (int cand = 0; cand < 4; ++cand) {
         p.cta_pair = cand == 2 ? 0 : 1;
         cudaEventRecord(e0, s);
         const dmpt_status st = batch_impl(h, count, H, H1, k, n, ld, n_occ, &p, P, P1, info,
-                                          workspace, ws_bytes, stream, cand == 0 ? 0 : 1);
+                                          workspace, ws_bytes, stream,
+                                          cand == 0 ? 0 : (cand == 3 ? 3 : 1));
         cudaEventRecord(e1, s);
         if (st != DMPT_OK && st != DMPT_ENOTCONV) {
           cudaEventDestroy(e0);
@@ -1296,7 +1308,7 @@ dmpt_status dmpt_sp2_response_batch(dmpt_handle h, int count, const double* cons
   }
   t.cta_pair = path == 2 ? 0 : 1;
   return batch_impl(h, count, H, H1, k, n, ld, n_occ, &t, P, P1, info, workspace, ws_bytes, stream,
-                    path == 0 ? 0 : 1);
+                    path == 0 ? 0 : (path == 3 ? 3 : 1));
 }
 
 dmpt_status dmpt_response_replay(dmpt_handle h, const double* H1, int k, int64_t n,

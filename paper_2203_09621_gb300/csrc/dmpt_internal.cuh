@@ -102,7 +102,10 @@ struct Layout {
   int ckpt_slots;         // FP32 S0 checkpoints (Np x Np each; 0: none)
 };
 
-Layout make_layout(int64_t n, int k, int precision, int tape_states = 0, int ckpt_slots = 0);
+// pad: the internal size Np is n rounded up to a multiple of pad (256; 128
+// for the batch path on 256 x 128 tiles).
+Layout make_layout(int64_t n, int k, int precision, int tape_states = 0, int ckpt_slots = 0,
+                   int pad = kPad);
 
 // 16-bit operand slice of matrix m (0 = S0, 1 + j = S1_j) in ping-pong buffer
 // `buf`, part 0 = hi, 1 = lo.  Tape slices follow the 4 (1 + k) ping-pong ones.
@@ -182,6 +185,7 @@ int tc_tile();
 // the struct takes the map's alignment).
 struct GroupInst {
   CUtensorMap map;     // 3-D map over the instance's 16-bit operand slices
+  CUtensorMap map64;   // the same slices in 64-row boxes (256 x 128 tiles)
   State* st;
   float* master;
   uint16_t* ops;
@@ -214,16 +218,20 @@ struct GroupQueue {
   unsigned pad[62];
   unsigned long long slot[kQueuePairs][kQueueRing];
 };
-// Fills `gi` for the instance whose workspace is `ws` (false: no tensor map).
-bool make_group_inst(const Layout& L, void* ws, int sm_count, GroupInst* gi);
+// Fills `gi` for the instance whose workspace is `ws` (false: no tensor map);
+// n128: also the 64-row map of the 256 x 128 tile kernel.
+bool make_group_inst(const Layout& L, void* ws, int sm_count, GroupInst* gi, bool n128 = false);
 // Partial-sum entries per job and the flops of one single-term pass of the
-// pair kernel for layout L.
-void pair_tile_info(const Layout& L, int64_t* entries, double* pass_flops);
+// pair kernel for layout L (n128: of the grouped 256 x 128 tile kernel).
+void pair_tile_info(const Layout& L, int64_t* entries, double* pass_flops, bool n128 = false);
 // One layer of every instance in `inst` (device array of `count`) in one
 // launch; a bounded wait that expires sets *group_timeout.
+// n128: 256 x 128 tiles (four 128-column accumulators; instances padded to a
+// multiple of 128) instead of 256 x 256.
 cudaError_t launch_layer_tc_group(const GroupInst* inst, int count, bool bf16, int* group_timeout,
                                   GroupQueue* queue, double timeout_s, int accum_chunk_k,
-                                  int k_snake, int band, int sm_count, cudaStream_t s);
+                                  int k_snake, int band, int sm_count, cudaStream_t s,
+                                  bool n128 = false);
 // Decide step of every instance (device array of `count`), one block each; a
 // set *group_timeout marks every instance timed out.
 cudaError_t launch_decide_group(const GroupDecide* args, int count, const int* group_timeout,

@@ -17,10 +17,10 @@ namespace dmpt {
 
 static inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-Layout make_layout(int64_t n, int k, int precision, int tape_states, int ckpt_slots) {
+Layout make_layout(int64_t n, int k, int precision, int tape_states, int ckpt_slots, int pad) {
   Layout L{};
   L.n = n;
-  L.Np = ((n + kPad - 1) / kPad) * kPad;
+  L.Np = ((n + pad - 1) / pad) * pad;
   L.k = k;
   L.precision = precision;
   L.tape_states = tape_states;

@@ -362,7 +362,7 @@ __device__ __forceinline__ uint32_t h16_bits(H16 x) {
 constexpr int XP_STRIDE = 20;                       // words per buffer row
 constexpr int XP_WARP_BYTES = 32 * XP_STRIDE * 4;   // 2560 B per epilogue warp
 static_assert(EPI_WARPS * XP_WARP_BYTES == EPI_SCRATCH, "transpose buffers");
-template <class CV, bool OFF>
+template <class CV, bool OFF, int NG = 8>   // NG groups of 16 columns per thread row
 __device__ __forceinline__ void rolled_tile_epilogue(
     const uint32_t ta_sum, const float* __restrict__ Sold, float* Snew, typename CV::T* hi_new,
     typename CV::T* lo_new, uint32_t* xp, const int lane, const int64_t Np, const int r,
@@ -386,7 +386,7 @@ __device__ __forceinline__ void rolled_tile_epilogue(
 #pragma unroll
   for (int q = 0; q < 16; ++q) olds[q] = __ldg(Sc + q * np);
 #pragma unroll 1
-  for (int g16 = 0; g16 < 8; ++g16) {
+  for (int g16 = 0; g16 < NG; ++g16) {
     uint32_t xs[16];
     tmem_ld16(ta_sum + 16 * g16, xs);
     const int cb16 = c0 + 16 * g16;
@@ -439,7 +439,7 @@ __device__ __forceinline__ void rolled_tile_epilogue(
       }
       xr[gg] = make_float4(nw[0], nw[1], nw[2], nw[3]);
     }
-    if (g16 < 7) {
+    if (g16 < NG - 1) {
 #pragma unroll
       for (int q = 0; q < 16; ++q) olds[q] = __ldg(Sc + (16 * (g16 + 1) + q) * np);
     }
@@ -1729,6 +1729,443 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Grouped pair kernel on 256 x 128 tiles (batches; option of the batch path).
+//
+// The same pool of items, dynamic queue and per-item work as the 256 x 256
+// grouped kernel, with three changes that suit small instances:
+//  - N = 128: each CTA of a pair loads 64 B rows per stage (a 64-row tensor
+//    map), so a stage is 24 KB and the ring holds 8 of them;
+//  - tensor memory holds four 128-column accumulators, so a tile epilogue,
+//    which keeps its tile's sums in the last chunk's accumulator while it
+//    stores, leaves the MMA issuer three accumulators to run ahead with;
+//  - the instances are padded to a multiple of 128 instead of 256.  A row
+//    block of 256 can then extend 128 rows past the matrix: its second CTA
+//    multiplies zeros (the tensor map fills rows past Np with zeros) and skips
+//    its epilogue.
+// Items run their K passes forwards (no K-snake): the queue keeps the items
+// in flight within a few instances, whose operand panels stay in L2.  The
+// tile order differs from the 256 x 256 kernels, so results agree with them
+// to rounding, not bit for bit.
+constexpr int G_BN = 128;                                   // tile columns
+constexpr int G_BROWS = G_BN / 2;                           // B rows per CTA
+constexpr int G_B_BYTES = G_BROWS * BK * 2;                 // 4 KB
+constexpr int G_STAGES = 8;
+constexpr int G_STAGE_BYTES = 2 * A_BYTES + 2 * G_B_BYTES;  // 24 KB
+constexpr int G_ACC = 4;                                    // accumulators of G_BN columns
+static_assert(G_ACC * G_BN == TMEM_COLS, "accumulators fill the allocation");
+constexpr int G_SMEM_BYTES = G_STAGES * G_STAGE_BYTES + 1024 + 1024 + EPI_SCRATCH;
+static_assert(G_SMEM_BYTES == P_SMEM_BYTES, "same shared memory as the 256 x 256 kernel");
+
+__host__ __device__ constexpr uint32_t make_idesc_m256_n128(int ab_type) {
+  return (1u << 4) | ((uint32_t)ab_type << 7) | ((uint32_t)ab_type << 10) |
+         ((uint32_t)(G_BN >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
+}
+
+// 256 x 128 tiles holding some element with row <= col: 256-row block I2 and
+// 128-column block J' with J' >= 2 I2; row-major (I2, then J').
+__host__ __device__ inline int64_t num_tiles128(int64_t Np) {
+  const int64_t tj = Np / G_BN, t2 = (Np + 255) / 256;
+  return t2 * tj - t2 * (t2 - 1);   // sum over I2 < t2 of (tj - 2 I2)
+}
+__device__ __forceinline__ void tile128_coords(int64_t t, int64_t Np, int* I2, int* J) {
+  const int tj = (int)(Np / G_BN);
+  int i = 0;
+  while (t >= tj - 2 * i) {
+    t -= tj - 2 * i;
+    ++i;
+  }
+  *I2 = i;
+  *J = 2 * i + (int)t;
+}
+
+struct GroupItem128 {
+  int inst, job, passes, kblocks;
+  int64_t t;
+};
+
+__device__ __forceinline__ GroupItem128 group_item128(const GroupInst* __restrict__ inst,
+                                                      const int64_t* first, const uint32_t* jmask,
+                                                      int count, int64_t g) {
+  GroupItem128 r;
+  r.inst = group_find(first, count, g);
+  const GroupInst& gi = inst[r.inst];
+  const int64_t loc = g - first[r.inst];
+  const int64_t tiles = num_tiles128(gi.Np);
+  r.job = job_at(jmask[r.inst], (int)(loc / tiles));
+  r.t = loc % tiles;
+  r.passes = job_passes(r.job, gi.k);
+  r.kblocks = (int)(gi.Np / BK);
+  return r;
+}
+
+// Producer of one 256 x 128 item: this CTA's 128 A rows (128-row map) and its
+// 64 B rows (64-row map) per stage, signalled on the leader's full barrier.
+__device__ __forceinline__ bool produce_item128(RingPos& rg, const CUtensorMap* map,
+                                                const CUtensorMap* map64, const State* st,
+                                                int job, int passes, int k, int cur0, int z0c,
+                                                int rowA, int rowB, int kblocks, bool leader,
+                                                uint32_t ring, uint32_t bar_full,
+                                                uint32_t bar_empty, uint32_t lead_full,
+                                                uint64_t limit_ns, volatile int* abort_flag,
+                                                int* timeout_global) {
+  for (int pass = 0; pass < passes; ++pass) {
+    int mA, mB;
+    job_operands(job, pass, k, &mA, &mB);
+    const int bufA = mA == 0 ? cur0 : st->cur1[mA - 1];
+    const int bufB = mB == 0 ? cur0 : st->cur1[mB - 1];
+    const int zAh = zop(mA, bufA, 0, k, z0c), zAl = zop(mA, bufA, 1, k, z0c);
+    const int zBh = zop(mB, bufB, 0, k, z0c), zBl = zop(mB, bufB, 1, k, z0c);
+    for (int kb = 0; kb < kblocks; ++kb) {
+      if (!mbar_wait(bar_empty + 8 * rg.idx, rg.phase ^ 1, limit_ns, abort_flag, timeout_global))
+        return false;
+      const uint32_t sA = ring + rg.idx * G_STAGE_BYTES;
+      if (leader) mbar_expect_tx(bar_full + 8 * rg.idx, 2 * G_STAGE_BYTES);
+      const uint32_t fb = lead_full + 8 * rg.idx;
+      tma_load_3d_pair(sA, map, kb * BK, rowA, zAh, fb);
+      tma_load_3d_pair(sA + A_BYTES, map, kb * BK, rowA, zAl, fb);
+      tma_load_3d_pair(sA + 2 * A_BYTES, map64, kb * BK, rowB, zBh, fb);
+      tma_load_3d_pair(sA + 2 * A_BYTES + G_B_BYTES, map64, kb * BK, rowB, zBl, fb);
+      rg.next(G_STAGES);
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void producer_drain128(RingPos rg, uint32_t bar_empty,
+                                                  uint64_t limit_ns) {
+  for (int i = 0; i < G_STAGES; ++i) {
+    const uint64_t t0 = gtimer();
+    while (!mbar_try_wait(bar_empty + 8 * rg.idx, rg.phase ^ 1) && gtimer() - t0 < limit_ns) {
+    }
+    rg.next(G_STAGES);
+  }
+}
+
+// MMA issuer of one 256 x 128 item (leader CTA, one thread): as mma_item,
+// with N = 128 and four accumulators.
+template <bool BF16>
+__device__ __forceinline__ bool mma_item128(RingPos& rg, RingPos& tb, int nst, int kblocks,
+                                            int chunk, uint32_t tmem_base, uint32_t ring,
+                                            uint32_t bar_full, uint32_t bar_empty,
+                                            uint32_t bar_tfull, uint32_t bar_tempty,
+                                            uint64_t limit_ns, volatile int* abort_flag,
+                                            int* timeout_global) {
+  constexpr uint32_t idesc = make_idesc_m256_n128(BF16 ? 1 : 0);
+  uint32_t d = 0, acc = 0;
+  int sp = 0;   // stage within its K pass
+  int cp = 0;   // stage within its accumulation chunk
+  for (int si = 0; si < nst; ++si) {
+    if (cp == 0) {
+      if (!mbar_wait(bar_tempty + 8 * tb.idx, tb.phase ^ 1, limit_ns, abort_flag, timeout_global))
+        return false;
+      fence_after();
+      d = tmem_base + (uint32_t)(tb.idx * G_BN);
+      acc = 0;
+    }
+    if (!mbar_wait(bar_full + 8 * rg.idx, rg.phase, limit_ns, abort_flag, timeout_global))
+      return false;
+    fence_after();
+    const uint32_t sA = ring + rg.idx * G_STAGE_BYTES;
+    const uint64_t ah = sw64_desc(sA), al = sw64_desc(sA + A_BYTES);
+    const uint64_t bh = sw64_desc(sA + 2 * A_BYTES);
+    const uint64_t bl = sw64_desc(sA + 2 * A_BYTES + G_B_BYTES);
+#pragma unroll
+    for (int kk = 0; kk < BK / 16; ++kk) {
+      const uint64_t off = (uint64_t)((kk * 32) >> 4);
+      mma_f16_pair(d, ah + off, bh + off, idesc, acc);   // hi * hi
+      acc = 1;
+      mma_f16_pair(d, ah + off, bl + off, idesc, 1);     // hi * lo
+      mma_f16_pair(d, al + off, bh + off, idesc, 1);     // lo * hi
+    }
+    mma_commit_pair(bar_empty + 8 * rg.idx);   // frees the stage in both CTAs
+    rg.next(G_STAGES);
+    const bool chunk_end = cp == chunk - 1 || sp == kblocks - 1;
+    if (++cp == chunk || sp == kblocks - 1) cp = 0;
+    if (++sp == kblocks) sp = 0;
+    if (chunk_end) {
+      mma_commit_pair(bar_tfull + 8 * tb.idx);    // chunk ready in both CTAs
+      tb.next(G_ACC);
+    }
+  }
+  return true;
+}
+
+template <bool BF16>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
+    layer_tc2_group128_kernel(const GroupInst* __restrict__ inst, int count, int* group_timeout,
+                              GroupQueue* gq, uint64_t limit_ns, int chunk) {
+  using CV = Cvt<BF16>;
+  using H16 = typename CV::T;
+  extern __shared__ uint8_t smem_raw[];
+
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw);
+  const uint32_t ring = base;
+  uint8_t* misc = gbase + G_STAGES * G_STAGE_BYTES;
+  int64_t* first = reinterpret_cast<int64_t*>(misc + 1024 + EPI_SCRATCH);
+  uint32_t* jmask = reinterpret_cast<uint32_t*>(first + count + 1);
+
+  // ---- this layer's items of every instance (as in the 256 x 256 kernel)
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    const State* sti = inst[i].st;
+    uint32_t jm = 0;
+    if (!sti->done) {
+      jm = sti->plan_square ? 1u : 0u;
+      for (int j = 0; j < inst[i].k; ++j)
+        if (sti->plan_resp[j]) jm |= 1u << (1 + j);
+    }
+    jmask[i] = jm;
+    first[i + 1] = num_tiles128(inst[i].Np) * __popc(jm);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    first[0] = 0;
+    for (int i = 0; i < count; ++i) first[i + 1] += first[i];
+  }
+  __syncthreads();
+  const int64_t items = first[count];
+  if (items == 0) return;   // every CTA takes this exit together
+  const unsigned epoch = *(volatile unsigned*)&gq->epoch;   // fixed during the launch
+
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const int64_t pair = blockIdx.x >> 1;
+
+  uint64_t* bars = reinterpret_cast<uint64_t*>(misc);
+  const uint32_t bar_full = smem_u32(bars);
+  const uint32_t bar_empty = bar_full + 8 * G_STAGES;
+  const uint32_t bar_tfull = bar_empty + 8 * G_STAGES;
+  const uint32_t bar_tempty = bar_tfull + 8 * G_ACC;
+  const uint32_t bar_drain = bar_tempty + 8 * G_ACC;
+  static_assert(8 * (2 * G_STAGES + 2 * G_ACC + 1) <= 256, "barriers below the TMEM slot");
+  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(misc + 256);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(misc + 264);
+  double* red = reinterpret_cast<double*>(misc + 1024);
+  const uint32_t lead_full = map_to_rank(bar_full, 0);
+  const uint32_t lead_tempty = map_to_rank(bar_tempty, 0);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < G_STAGES; ++s) {
+      mbar_init(bar_full + 8 * s, 1);
+      mbar_init(bar_empty + 8 * s, 1);
+    }
+    for (int b = 0; b < G_ACC; ++b) {
+      mbar_init(bar_tfull + 8 * b, 1);
+      mbar_init(bar_tempty + 8 * b, 2 * EPI_WARPS);
+    }
+    mbar_init(bar_drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32((const void*)tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+  }
+  fence_before();
+  cluster_sync_all();   // barriers of both CTAs initialised, TMEM allocated
+  fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  int* timeout_global = group_timeout;
+
+  if (warp == 0) {
+    // ================= TMA producer (both CTAs load their own rows) ======
+    if (lane == 0) {
+      RingPos rg;
+      bool ok = true;
+      int last_inst = -1;
+      for (int64_t j = 0; ok; ++j) {
+        uint32_t g;
+        if (leader)
+          g = claim_next(gq, pair, j, epoch, items);
+        else if (!claim_wait(gq, pair, j, epoch, limit_ns, abort_flag, timeout_global, &g))
+          break;
+        if (g == kNoItem) break;
+        const GroupItem128 itm = group_item128(inst, first, jmask, count, g);
+        const GroupInst& gi = inst[itm.inst];
+        if (itm.inst != last_inst) {
+          tensormap_acquire(&gi.map);
+          tensormap_acquire(&gi.map64);
+          last_inst = itm.inst;
+        }
+        const State* sti = gi.st;
+        int I2, J;
+        tile128_coords(itm.t, gi.Np, &I2, &J);
+        ok = produce_item128(rg, &gi.map, &gi.map64, sti, itm.job, itm.passes, gi.k, sti->cur0,
+                             sti->z0_cur, I2 * 2 * BM + (int)rank * BM,
+                             J * G_BN + (int)rank * G_BROWS, itm.kblocks, leader, ring, bar_full,
+                             bar_empty, lead_full, limit_ns, abort_flag, timeout_global);
+      }
+      producer_drain128(rg, bar_empty, limit_ns);
+    }
+  } else if (warp == 1) {
+    // ================= MMA issuer (leader CTA only) =================
+    if (leader && lane == 0) {
+      RingPos rg, tb;
+      bool ok = true;
+      for (int64_t j = 0; ok; ++j) {
+        uint32_t g;
+        if (!claim_wait(gq, pair, j, epoch, limit_ns, abort_flag, timeout_global, &g)) break;
+        if (g == kNoItem) break;
+        const GroupItem128 itm = group_item128(inst, first, jmask, count, g);
+        ok = mma_item128<BF16>(rg, tb, itm.passes * itm.kblocks, itm.kblocks, chunk, tmem_base,
+                               ring, bar_full, bar_empty, bar_tfull, bar_tempty, limit_ns,
+                               abort_flag, timeout_global);
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              bar_drain)
+          : "memory");
+      const uint64_t t0 = gtimer();
+      while (!mbar_try_wait(bar_drain, 0) && gtimer() - t0 < limit_ns) {
+      }
+    }
+  } else if (warp >= EPI_WARP0) {
+    // ========== epilogue (both CTAs, own 128 rows; warps split 64 + 64 columns) ==========
+    const int q = warp & 3;
+    const int half = (warp - EPI_WARP0) >> 2;
+    const int rloc = 32 * q + lane;
+    const int et = threadIdx.x - 32 * EPI_WARP0;
+    const uint32_t tlane = (uint32_t)(32 * q) << 16;
+    RingPos ab;
+    bool alive = true;
+    for (int64_t j = 0; alive; ++j) {
+      uint32_t g = kNoItem;
+      bool got = true;
+      if (lane == 0) got = claim_wait(gq, pair, j, epoch, limit_ns, abort_flag, timeout_global, &g);
+      g = __shfl_sync(0xFFFFFFFFu, g, 0);
+      got = __shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0) != 0;
+      if (!epi_all(got && !*abort_flag)) {
+        alive = false;
+        break;
+      }
+      if (g == kNoItem) break;
+      const GroupItem128 itm = group_item128(inst, first, jmask, count, g);
+      const GroupInst& gi = inst[itm.inst];
+      const State* sti = gi.st;
+      const int job = itm.job;
+      const int k = gi.k;
+      const int cpp = (itm.kblocks + chunk - 1) / chunk;   // chunks per pass
+      const int nchunks = itm.passes * cpp;
+      const int s0e = sti->s0_exp;
+      // exact power-of-two unscale of the products (first-order jobs and the
+      // square: passes 0 and 1 only)
+      const float u = ldexpf(1.0f, -(s0e + (job == 0 ? s0e : sti->s1_exp_cur[job - 1])));
+      float sum[64];
+#pragma unroll
+      for (int i = 0; i < 64; ++i) sum[i] = 0.0f;
+      for (int ch = 0; ch < nchunks; ++ch) {
+        const bool ok =
+            mbar_wait(bar_tfull + 8 * ab.idx, ab.phase, limit_ns, abort_flag, timeout_global);
+        if (!epi_all(ok && !*abort_flag)) {
+          alive = false;
+          break;
+        }
+        fence_after();
+        const uint32_t ta = tmem_base + tlane + (uint32_t)(ab.idx * G_BN + half * 64);
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          uint32_t x[16];
+          tmem_ld16(ta + 16 * cc, x);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) sum[16 * cc + i] = fmaf(__uint_as_float(x[i]), u, sum[16 * cc + i]);
+        }
+        if (ch + 1 == nchunks) break;   // keep the last chunk's accumulator
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(lead_tempty + 8 * ab.idx);
+        ab.next(G_ACC);
+      }
+      if (!alive) break;
+      // the tile's sums go back into its last chunk's accumulator (rolled epilogue)
+      const uint32_t ta_sum = tmem_base + tlane + (uint32_t)(ab.idx * G_BN + half * 64);
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) tmem_st16(ta_sum + 16 * cc, sum + 16 * cc);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+
+      const int64_t Np = gi.Np;
+      const size_t mat = (size_t)Np * Np;
+      int I2, J;
+      tile128_coords(itm.t, Np, &I2, &J);
+      const int cur0 = sti->cur0;
+      const int curj = job == 0 ? cur0 : sti->cur1[job - 1];
+      const int e_new = job == 0 ? s0e : sti->s1_exp_next[job - 1];
+      const float scale_new = ldexpf(1.0f, e_new);   // exact power of two
+      const float sigma = (float)sti->sigma_cur;
+      const float sg = sigma, om = 1.0f - sigma;
+      const bool write = job != 0 || sti->plan_write0;
+      const int row0 = I2 * 2 * BM + (int)rank * BM;   // this CTA's first row
+      const int r = row0 + rloc;
+      const int c0 = J * G_BN + half * 64;
+      float* master = gi.master;
+      const float* Sold = master + (size_t)(curj * (1 + k) + job) * mat;
+      float* Snew = master + (size_t)((curj ^ 1) * (1 + k) + job) * mat;
+      const int zh_new = job == 0 ? sti->z0_next : zslice(curj ^ 1, job, 0, k);
+      H16* hi_new = reinterpret_cast<H16*>(gi.ops) + (size_t)zh_new * mat;
+      H16* lo_new = reinterpret_cast<H16*>(gi.ops) + (size_t)(zh_new + 1) * mat;
+
+      float fn_s = 0.0f, fn_c = 0.0f, fd = 0.0f, trf = 0.0f;
+      int bad = 0;
+      uint32_t* xp = reinterpret_cast<uint32_t*>(misc + 1024) +
+                     (warp - EPI_WARP0) * (XP_WARP_BYTES / 4);
+      // rows past Np (a 256-row block over a matrix padded to 128): nothing to
+      // store; the products there are zeros
+      if ((int64_t)row0 < Np) {
+        if (c0 >= row0 + BM)   // every column of this warp's block right of every row
+          rolled_tile_epilogue<CV, true, 4>(ta_sum, Sold, Snew, hi_new, lo_new, xp, lane, Np, r,
+                                            c0, sg, om, scale_new, write, fn_s, fn_c, fd, trf,
+                                            bad);
+        else
+          rolled_tile_epilogue<CV, false, 4>(ta_sum, Sold, Snew, hi_new, lo_new, xp, lane, Np, r,
+                                             c0, sg, om, scale_new, write, fn_s, fn_c, fd, trf,
+                                             bad);
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(lead_tempty + 8 * ab.idx);
+      ab.next(G_ACC);
+      epi_sync();   // the reduction array overlays the transpose buffers
+      red[0 * EPI_THREADS + et] = (double)trf;
+      red[1 * EPI_THREADS + et] = (double)fn_s + (double)fn_c;
+      red[2 * EPI_THREADS + et] = (double)fd;
+      red[3 * EPI_THREADS + et] = (double)bad;
+      epi_sync();
+      for (int s2 = EPI_THREADS / 2; s2 > 0; s2 >>= 1) {
+        if (et < s2) {
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) red[qq * EPI_THREADS + et] += red[qq * EPI_THREADS + et + s2];
+        }
+        epi_sync();
+      }
+      if (et == 0) {
+        double* pp = gi.partials + ((size_t)job * gi.ptiles + 2 * itm.t + rank) * kNQ;
+        pp[kQTrace] = red[0];
+        pp[kQFroNew] = red[EPI_THREADS];
+        pp[kQFroDiff] = red[2 * EPI_THREADS];
+        pp[kQBad] = red[3 * EPI_THREADS];
+      }
+      epi_sync();
+    }
+  }
+
+  // ---- teardown: both CTAs done (or aborted); free TMEM of the pair
+  fence_before();
+  __syncthreads();
+  cluster_sync_all();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(TMEM_COLS));
+  }
+}
+
+
+// ---------------------------------------------------------------------------
 // Host side
 
 // Per-device one-time setup of the tensor-core kernels (their shared-memory
@@ -1760,6 +2197,10 @@ int device_setup() {
     cudaFuncSetAttribute(layer_tc2_group_kernel<false>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, group_smem);
     cudaFuncSetAttribute(layer_tc2_group_kernel<true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, group_smem);
+    cudaFuncSetAttribute(layer_tc2_group128_kernel<false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, group_smem);
+    cudaFuncSetAttribute(layer_tc2_group128_kernel<true>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, group_smem);
   });
   return d.sms;
@@ -1797,18 +2238,20 @@ bool make_map(CUtensorMap* map, void* base, int64_t Np, int slices, int box_rows
 
 int tc_tile() { return tc::BN; }
 
-void pair_tile_info(const Layout& L, int64_t* entries, double* pass_flops) {
-  const int64_t tiles = tc::num_pair_tiles(L.Np);
+void pair_tile_info(const Layout& L, int64_t* entries, double* pass_flops, bool n128) {
+  const int64_t tiles = n128 ? tc::num_tiles128(L.Np) : tc::num_pair_tiles(L.Np);
+  const double cols = n128 ? tc::G_BN : tc::BN;
   if (entries) *entries = 2 * tiles;
-  if (pass_flops) *pass_flops = (double)tiles * 2 * tc::BM * tc::BN * (double)L.Np * 2.0;
+  if (pass_flops) *pass_flops = (double)tiles * 2 * tc::BM * cols * (double)L.Np * 2.0;
 }
 
-bool make_group_inst(const Layout& L, void* ws, int sm_count, GroupInst* gi) {
+bool make_group_inst(const Layout& L, void* ws, int sm_count, GroupInst* gi, bool n128) {
   using namespace tc;
   char* base = (char*)ws;
   const bool bf16 = L.precision == DMPT_DUAL_BF16;
   const int slices = 2 * (1 + L.k) * 2 + 2 * L.tape_states;
   if (!make_map(&gi->map, base + L.off_ops16, L.Np, slices, BM, bf16)) return false;
+  if (n128 && !make_map(&gi->map64, base + L.off_ops16, L.Np, slices, G_BROWS, bf16)) return false;
   gi->st = (State*)(base + L.off_state);
   gi->master = (float*)(base + L.off_master);
   gi->ops = (uint16_t*)(base + L.off_ops16);
@@ -1825,7 +2268,8 @@ bool make_group_inst(const Layout& L, void* ws, int sm_count, GroupInst* gi) {
 
 cudaError_t launch_layer_tc_group(const GroupInst* inst, int count, bool bf16, int* group_timeout,
                                   GroupQueue* queue, double timeout_s, int accum_chunk_k,
-                                  int k_snake, int band, int sm_count, cudaStream_t s) {
+                                  int k_snake, int band, int sm_count, cudaStream_t s,
+                                  bool n128) {
   using namespace tc;
   if (count < 1 || count > kGroupMax || !queue || sm_count / 2 > kQueuePairs)
     return cudaErrorInvalidValue;
@@ -1836,6 +2280,15 @@ cudaError_t launch_layer_tc_group(const GroupInst* inst, int count, bool bf16, i
   const int ck = accum_chunk_k > 0 ? accum_chunk_k : DEFAULT_CHUNK_K;
   const int chunk = ck / BK < 1 ? 1 : ck / BK;
   const int grid = 2 * (sm_count / 2);
+  if (n128) {
+    if (bf16)
+      layer_tc2_group128_kernel<true><<<grid, NUM_THREADS, smem, s>>>(inst, count, group_timeout,
+                                                                      queue, limit_ns, chunk);
+    else
+      layer_tc2_group128_kernel<false><<<grid, NUM_THREADS, smem, s>>>(
+          inst, count, group_timeout, queue, limit_ns, chunk);
+    return cudaGetLastError();
+  }
   if (bf16)
     layer_tc2_group_kernel<true><<<grid, NUM_THREADS, smem, s>>>(
         inst, count, group_timeout, queue, limit_ns, chunk, k_snake, band);

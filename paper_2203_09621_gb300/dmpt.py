@@ -46,6 +46,7 @@ class DmptOptions(ctypes.Structure):
         ("autotune", ctypes.c_int),
         ("round_align", ctypes.c_int),
         ("hole_form", ctypes.c_int),
+        ("group_tile_n", ctypes.c_int),
     ]
 
 
@@ -201,7 +202,8 @@ class Info:
 def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_scaling=1,
             sync_every=4, timing=False, timeout_s=2.0, accum_chunk=0,
             cta_pair=1, k_snake=1, ckpt_every=0, order=1, tile_band=8,
-            inject_stall=0, autotune=0, round_align=1, hole_form=1) -> DmptOptions:
+            inject_stall=0, autotune=0, round_align=1, hole_form=1,
+            group_tile_n=256) -> DmptOptions:
     lib = load_library()
     o = DmptOptions()
     lib.dmpt_default_options(ctypes.byref(o))
@@ -223,6 +225,7 @@ def options(precision="dual_fp16", max_layers=100, c_pt=9.0, c_d0=4.5, operand_s
     o.autotune = int(autotune)
     o.round_align = int(round_align)
     o.hole_form = int(hole_form)
+    o.group_tile_n = int(group_tile_n)
     return o
 
 
