@@ -952,8 +952,8 @@ dmpt_status dmpt_sp2_backward(dmpt_handle h, const double* G, int64_t n, int64_t
 }
 
 // Batch scratch: [state offsets, all-done flag] [GroupInst table]
-// [GroupDecide table] [group timeout flag] [grouped item queue], each
-// 256-byte aligned.
+// [GroupDecide table] [group timeout flag] [grouped item queue] [gathered
+// control blocks], each 256-byte aligned.
 static size_t batch_poll_bytes(int count) {
   return ((size_t)count * sizeof(long long) + 2 * sizeof(int) + 255) & ~size_t(255);
 }
@@ -964,9 +964,12 @@ static size_t batch_gdec_bytes(int count) {
   return ((size_t)count * sizeof(GroupDecide) + 255) & ~size_t(255);
 }
 static size_t batch_queue_bytes() { return (sizeof(GroupQueue) + 255) & ~size_t(255); }
+static size_t batch_states_bytes(int count) {
+  return ((size_t)count * sizeof(State) + 255) & ~size_t(255);
+}
 static size_t batch_scratch_bytes(int count) {
   return batch_poll_bytes(count) + batch_ginst_bytes(count) + batch_gdec_bytes(count) + 256 +
-         batch_queue_bytes();
+         batch_queue_bytes() + batch_states_bytes(count);
 }
 
 size_t dmpt_workspace_size_batch(int count, const int64_t* n, int k, const dmpt_options* o) {
@@ -1061,6 +1064,7 @@ static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
   GroupDecide* d_gdec = (GroupDecide*)((char*)d_ginst + batch_ginst_bytes(count));
   int* d_gtimeout = (int*)((char*)d_gdec + batch_gdec_bytes(count));
   GroupQueue* d_gqueue = (GroupQueue*)((char*)d_gtimeout + 256);
+  State* d_states = (State*)((char*)d_gqueue + batch_queue_bytes());
   if (n_active > 0 &&
       (e = cudaMemcpyAsync(d_offs, act_offs.data(), sizeof(long long) * n_active,
                            cudaMemcpyHostToDevice, h->origin)) != cudaSuccess)
@@ -1186,8 +1190,25 @@ static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
     }
   }
   cudaGraphExecDestroy(exec);
+  // every instance's outputs, then every control block in one copy and one
+  // synchronisation
+  for (int i = 0; i < count; ++i) {
+    if (!active[i]) continue;
+    if ((e = launch_finalize(L[i], base + offs[i], P ? P[i] : nullptr, k ? P1[i] : nullptr,
+                             ld[i], k, h->origin)) != cudaSuccess)
+      return cuda_fail(h, e, "batch finalize");
+  }
+  std::vector<State> hs(n_active > 0 ? n_active : 1);
+  if (n_active > 0) {
+    e = launch_gather_states(base, d_offs, n_active, d_states, h->origin);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hs.data(), d_states, sizeof(State) * n_active, cudaMemcpyDeviceToHost,
+                          h->origin);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->origin);
+    if (e != cudaSuccess) return cuda_fail(h, e, "batch state");
+  }
   dmpt_status worst = DMPT_OK;
-  std::vector<State> hs(1);
+  int ia = 0;   // index among the active instances (the order of d_offs)
   for (int i = 0; i < count; ++i) {
     if (!active[i]) {
       if (info) {
@@ -1196,14 +1217,7 @@ static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
       }
       continue;
     }
-    void* ws = base + offs[i];
-    if ((e = launch_finalize(L[i], ws, P ? P[i] : nullptr, k ? P1[i] : nullptr, ld[i], k,
-                             h->origin)) != cudaSuccess)
-      return cuda_fail(h, e, "batch finalize");
-    e = cudaMemcpyAsync(hs.data(), ws, sizeof(State), cudaMemcpyDeviceToHost, h->origin);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->origin);
-    if (e != cudaSuccess) return cuda_fail(h, e, "batch state");
-    const State& S = hs[0];
+    const State& S = hs[ia++];
     const dmpt_status si = S.done ? (dmpt_status)S.status : DMPT_ENOTCONV;
     if (si != DMPT_OK && worst == DMPT_OK) worst = si;
     if (info) {

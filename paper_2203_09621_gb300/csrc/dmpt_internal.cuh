@@ -250,6 +250,9 @@ enum DecideMode {
 // batched solves: *flag = 1 when every instance's control block is done
 cudaError_t launch_batch_all_done(const void* base, const long long* offs, int count, int* flag,
                                   cudaStream_t s);
+// out[b] = the control block at base + offs[b], b < count (device arrays)
+cudaError_t launch_gather_states(const void* base, const long long* offs, int count, State* out,
+                                 cudaStream_t s);
 
 // CUDA device of a handle (-1 for NULL).
 int handle_device(dmpt_handle h);

@@ -1356,4 +1356,20 @@ cudaError_t launch_batch_all_done(const void* base, const long long* offs, int c
   batch_all_done_kernel<<<1, 256, 0, s>>>((const char*)base, offs, count, flag);
   return cudaGetLastError();
 }
+
+// out[b] = the control block at base + offs[b] (one block per instance), so
+// that the host reads every instance's state with one copy.
+__global__ void gather_states_kernel(const char* base, const long long* offs, State* out) {
+  static_assert(sizeof(State) % 4 == 0, "State copied as words");
+  const unsigned* src = (const unsigned*)(base + offs[blockIdx.x]);
+  unsigned* dst = (unsigned*)(out + blockIdx.x);
+  for (int i = threadIdx.x; i < (int)(sizeof(State) / 4); i += blockDim.x) dst[i] = src[i];
+}
+
+cudaError_t launch_gather_states(const void* base, const long long* offs, int count, State* out,
+                                 cudaStream_t s) {
+  if (count < 1) return cudaSuccess;
+  gather_states_kernel<<<count, 256, 0, s>>>((const char*)base, offs, out);
+  return cudaGetLastError();
+}
 }  // namespace dmpt
