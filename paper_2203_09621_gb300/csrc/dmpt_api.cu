@@ -129,49 +129,13 @@ Layout layout_for(int64_t n, int k, const dmpt_options* o, int pad = kPad) {
 }
 
 // The forward's product options, kept for the states the backward recomputes.
-struct FwdOpts {
-  int ckpt_k, ckpt_slots, chunk, cta_pair, k_snake, band;
-};
-
 __global__ void state_init_kernel(State* st, int k, int max_layers, int precision, double n_occ,
                                   double c_pt, double c_d0, int tape, int tape_base,
                                   int tape_states, int layout_k, int64_t n, int order = 1,
                                   int k1 = 0, FwdOpts fo = FwdOpts{0, 0, 0, 1, 1, 8},
                                   int hole = 0) {
-  // complement form: the recursion converges to I - P, whose occupied levels
-  // are the n - n_occ highest ones
-  st->hole = hole;
-  if (hole) n_occ = (double)n - n_occ;
-  st->ckpt_k = fo.ckpt_k;
-  st->ckpt_slots = fo.ckpt_slots;
-  st->ckpt_pending = 0;
-  st->adj_seg_a = 0;
-  st->fwd_chunk = fo.chunk;
-  st->fwd_cta_pair = fo.cta_pair;
-  st->fwd_k_snake = fo.k_snake;
-  st->fwd_band = fo.band;
-  st->order = order;
-  st->k1 = order >= 2 ? k1 : k;
-  st->tape = tape;
-  st->tape_base = tape_base;
-  st->tape_states = tape_states;
-  st->layout_k = layout_k;
-  st->k_fwd = k;
-  st->n = n;
-  st->n_layer = 0;
-  st->round_ctr = 0u;
-  st->done = 0;
-  st->status = DMPT_OK;
-  st->timeout_flag = 0;
-  st->k = k;
-  st->max_layers = max_layers;
-  st->precision = precision;
-  st->n_occ = n_occ;
-  st->c_pt = c_pt;
-  st->c_d0 = c_d0;
-  st->plan_square = 0;
-  st->plan_write0 = 0;
-  for (int j = 0; j < kMaxK; ++j) st->plan_resp[j] = 0;
+  state_init_fields(st, k, max_layers, precision, n_occ, c_pt, c_d0, tape, tape_base,
+                    tape_states, layout_k, n, order, k1, fo, hole);
 }
 
 // Re-open a finished forward state for the adjoint run (keeps sigma, the
@@ -220,7 +184,7 @@ dmpt_status replay_run(dmpt_handle h, const Layout& L, const double* H1, const d
                        void* workspace, cudaStream_t s) {
   State* st = (State*)workspace;
   cudaError_t e;
-  const int blocks = 1024;
+  const int blocks = kInitBlocks;
   replay_reset_kernel<<<1, 1, 0, s>>>(st, k);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "replay reset");
   if ((e = launch_init(L, workspace, nullptr, H1, ld, k, blocks, s, 1, shift)) != cudaSuccess)
@@ -485,7 +449,7 @@ static dmpt_status forward_impl(dmpt_handle h, const double* H, const double* H1
                                     use_hole_form(o, n, n_occ));
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "state init");
   if ((e = launch_bounds(H, n, ld, &st->eps1, s)) != cudaSuccess) return cuda_fail(h, e, "bounds");
-  const int init_blocks = 1024;
+  const int init_blocks = kInitBlocks;
   if ((e = launch_init(L, workspace, H, H1, ld, k, init_blocks, s, 0, nullptr,
                        (order - 1) * k)) != cudaSuccess)
     return cuda_fail(h, e, "init");
@@ -967,9 +931,16 @@ static size_t batch_queue_bytes() { return (sizeof(GroupQueue) + 255) & ~size_t(
 static size_t batch_states_bytes(int count) {
   return ((size_t)count * sizeof(State) + 255) & ~size_t(255);
 }
+static size_t batch_binst_bytes(int count) {
+  return ((size_t)count * sizeof(BatchInst) + 255) & ~size_t(255);
+}
+static size_t batch_first_bytes(int count) {
+  return ((size_t)kBsSteps * (count + 1) * sizeof(int64_t) + 255) & ~size_t(255);
+}
 static size_t batch_scratch_bytes(int count) {
   return batch_poll_bytes(count) + batch_ginst_bytes(count) + batch_gdec_bytes(count) + 256 +
-         batch_queue_bytes() + batch_states_bytes(count);
+         batch_queue_bytes() + batch_states_bytes(count) + batch_binst_bytes(count) +
+         batch_first_bytes(count);
 }
 
 size_t dmpt_workspace_size_batch(int count, const int64_t* n, int k, const dmpt_options* o) {
@@ -1065,11 +1036,49 @@ static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
   int* d_gtimeout = (int*)((char*)d_gdec + batch_gdec_bytes(count));
   GroupQueue* d_gqueue = (GroupQueue*)((char*)d_gtimeout + 256);
   State* d_states = (State*)((char*)d_gqueue + batch_queue_bytes());
+  BatchInst* d_binst = (BatchInst*)((char*)d_states + batch_states_bytes(count));
+  int64_t* d_bfirst = (int64_t*)((char*)d_binst + batch_binst_bytes(count));
+  // tables of the batched set-up and output launches (active instances, in
+  // the order of d_offs)
+  std::vector<BatchInst> bt(n_active > 0 ? n_active : 1);
+  std::vector<int64_t> bfirst((size_t)kBsSteps * (n_active + 1), 0);
+  int64_t units[kBsSteps] = {0, 0, 0, 0};
+  for (int i = 0, a = 0; i < count; ++i) {
+    if (!active[i]) continue;
+    char* ws = base + offs[i];
+    BatchInst& b = bt[a];
+    b.st = (State*)(ws + L[i].off_state);
+    b.master = ws + L[i].off_master;
+    b.ops = (uint16_t*)(ws + L[i].off_ops16);
+    b.partials = (double*)(ws + L[i].off_partials);
+    b.H = H[i];
+    b.H1 = k ? H1[i] : nullptr;
+    b.P = P ? P[i] : nullptr;
+    b.P1 = k ? P1[i] : nullptr;
+    b.n = n[i];
+    b.Np = L[i].Np;
+    b.ld = ld[i];
+    b.ptiles = L[i].partial_tiles;
+    b.n_occ = (double)n_occ[i];
+    b.k = k;
+    b.layout_k = L[i].k;
+    b.hole = use_hole_form(o, n[i], n_occ[i]);
+    b.init_blocks = (int)batch_units(kBsInit, n[i], L[i].Np, k);
+    for (int st = 0; st < kBsSteps; ++st) {
+      const int64_t u = batch_units(st, n[i], L[i].Np, st == kBsSplit ? L[i].k : k);
+      bfirst[(size_t)st * (n_active + 1) + a + 1] = bfirst[(size_t)st * (n_active + 1) + a] + u;
+      units[st] += u;
+    }
+    ++a;
+  }
   if (n_active > 0 &&
-      (e = cudaMemcpyAsync(d_offs, act_offs.data(), sizeof(long long) * n_active,
-                           cudaMemcpyHostToDevice, h->origin)) != cudaSuccess)
-    return cuda_fail(h, e, "batch offsets");
-  if ((e = cudaStreamSynchronize(h->origin)) != cudaSuccess) return cuda_fail(h, e, "batch fork");
+      ((e = cudaMemcpyAsync(d_offs, act_offs.data(), sizeof(long long) * n_active,
+                            cudaMemcpyHostToDevice, h->origin)) != cudaSuccess ||
+       (e = cudaMemcpyAsync(d_binst, bt.data(), sizeof(BatchInst) * n_active,
+                            cudaMemcpyHostToDevice, h->origin)) != cudaSuccess ||
+       (e = cudaMemcpyAsync(d_bfirst, bfirst.data(), sizeof(int64_t) * bfirst.size(),
+                            cudaMemcpyHostToDevice, h->origin)) != cudaSuccess))
+    return cuda_fail(h, e, "batch tables");
   std::vector<int64_t> entries(count, 0);
   std::vector<double> pass_flops(count, 0.0);
   auto issue_step = [&](int i) -> cudaError_t {
@@ -1083,32 +1092,6 @@ static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
     if (r != cudaSuccess) return r;
     return launch_decide(L[i], ws, kDecideLayer, entries[i], si);
   };
-  for (int i = 0; i < count; ++i) {
-    cudaStream_t si = h->streams[i];
-    if ((e = cudaStreamWaitEvent(si, h->fork, 0)) != cudaSuccess) return cuda_fail(h, e, "fork");
-    if (!active[i]) {
-      if ((e = launch_trivial(n[i], k, ld[i], n_occ[i] == n[i], P ? P[i] : nullptr,
-                              k ? P1[i] : nullptr, si)) != cudaSuccess)
-        return cuda_fail(h, e, "batch trivial");
-      continue;
-    }
-    void* ws = base + offs[i];
-    State* st = (State*)ws;
-    if ((e = cudaMemsetAsync(st, 0, sizeof(State), si)) != cudaSuccess) return cuda_fail(h, e, "state");
-    state_init_kernel<<<1, 1, 0, si>>>(st, k, o->max_layers, o->precision, (double)n_occ[i],
-                                       o->c_pt, o->c_d0, 0, 4 * (1 + L[i].k), 0, L[i].k, n[i],
-                                       1, 0, FwdOpts{0, 0, o->accum_chunk, o->cta_pair,
-                                                     o->k_snake, o->tile_band},
-                                       use_hole_form(o, n[i], n_occ[i]));
-    if ((e = launch_bounds(H[i], n[i], ld[i], &st->eps1, si)) != cudaSuccess)
-      return cuda_fail(h, e, "batch bounds");
-    if ((e = launch_init(L[i], ws, H[i], k ? H1[i] : nullptr, ld[i], k, 1024, si)) != cudaSuccess)
-      return cuda_fail(h, e, "batch init");
-    if ((e = launch_decide(L[i], ws, kDecideInit, 1024, si)) != cudaSuccess)
-      return cuda_fail(h, e, "batch decide");
-    if (dual && (e = launch_split(L[i], ws, 0, si)) != cudaSuccess) return cuda_fail(h, e, "split");
-    if (!grouped && (e = issue_step(i)) != cudaSuccess) return cuda_fail(h, e, "batch first layer");
-  }
   int n_group = 0;
   if (grouped) {
     // instances by decreasing size, so the item pool starts with the longest tiles
@@ -1131,19 +1114,40 @@ static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
       gd[j].entries = entries[i];
     }
     n_group = (int)order.size();
+    // copies from pageable memory return once the source is staged
     if ((e = cudaMemcpyAsync(d_ginst, gi.data(), sizeof(GroupInst) * gi.size(),
                              cudaMemcpyHostToDevice, h->origin)) != cudaSuccess ||
         (e = cudaMemcpyAsync(d_gdec, gd.data(), sizeof(GroupDecide) * gd.size(),
                              cudaMemcpyHostToDevice, h->origin)) != cudaSuccess ||
         (e = cudaMemsetAsync(d_gtimeout, 0, sizeof(int), h->origin)) != cudaSuccess ||
-        (e = cudaMemsetAsync(d_gqueue, 0, sizeof(GroupQueue), h->origin)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(h->origin)) != cudaSuccess)
+        (e = cudaMemsetAsync(d_gqueue, 0, sizeof(GroupQueue), h->origin)) != cudaSuccess)
       return cuda_fail(h, e, "batch group tables");
   }
-  // join everything into the origin stream
+  // instances with nothing to compute, then the initial layer of all others:
+  // one launch per step for the whole batch
   for (int i = 0; i < count; ++i) {
-    if ((e = cudaEventRecord(h->joins[i], h->streams[i])) != cudaSuccess) return cuda_fail(h, e, "join");
-    if ((e = cudaStreamWaitEvent(h->origin, h->joins[i], 0)) != cudaSuccess) return cuda_fail(h, e, "join");
+    if (active[i]) continue;
+    if ((e = launch_trivial(n[i], k, ld[i], n_occ[i] == n[i], P ? P[i] : nullptr,
+                            k ? P1[i] : nullptr, h->origin)) != cudaSuccess)
+      return cuda_fail(h, e, "batch trivial");
+  }
+  const BatchCommon common{o->max_layers, o->precision, o->c_pt, o->c_d0,
+                           FwdOpts{0, 0, o->accum_chunk, o->cta_pair, o->k_snake, o->tile_band}};
+  if ((e = launch_batch_setup(d_binst, d_bfirst, n_active, common, units, dual,
+                              o->precision == DMPT_DUAL_BF16, h->origin)) != cudaSuccess)
+    return cuda_fail(h, e, "batch initial layer");
+  if (!grouped) {
+    // the first layer of each instance on its own stream, joined into the origin stream
+    if ((e = cudaEventRecord(h->fork, h->origin)) != cudaSuccess) return cuda_fail(h, e, "fork");
+    for (int i = 0; i < count; ++i) {
+      if (!active[i]) continue;
+      if ((e = cudaStreamWaitEvent(h->streams[i], h->fork, 0)) != cudaSuccess)
+        return cuda_fail(h, e, "fork");
+      if ((e = issue_step(i)) != cudaSuccess) return cuda_fail(h, e, "batch first layer");
+      if ((e = cudaEventRecord(h->joins[i], h->streams[i])) != cudaSuccess ||
+          (e = cudaStreamWaitEvent(h->origin, h->joins[i], 0)) != cudaSuccess)
+        return cuda_fail(h, e, "join");
+    }
   }
   // one CUDA graph = one layer of every active instance, each on its own stream
   cudaGraph_t graph = nullptr;
@@ -1192,12 +1196,9 @@ static dmpt_status batch_impl(dmpt_handle h, int count, const double* const* H,
   cudaGraphExecDestroy(exec);
   // every instance's outputs, then every control block in one copy and one
   // synchronisation
-  for (int i = 0; i < count; ++i) {
-    if (!active[i]) continue;
-    if ((e = launch_finalize(L[i], base + offs[i], P ? P[i] : nullptr, k ? P1[i] : nullptr,
-                             ld[i], k, h->origin)) != cudaSuccess)
-      return cuda_fail(h, e, "batch finalize");
-  }
+  if ((e = launch_batch_finalize(d_binst, d_bfirst, n_active, units[kBsOut],
+                                 o->precision == DMPT_FP64, h->origin)) != cudaSuccess)
+    return cuda_fail(h, e, "batch finalize");
   std::vector<State> hs(n_active > 0 ? n_active : 1);
   if (n_active > 0) {
     e = launch_gather_states(base, d_offs, n_active, d_states, h->origin);

@@ -90,6 +90,53 @@ struct State {
   signed char sigma[kMaxL + 2];
 };
 
+// Product options of a forward run, kept in its control block so that the
+// backward pass recomputes checkpointed states with the same launches.
+struct FwdOpts {
+  int ckpt_k, ckpt_slots, chunk, cta_pair, k_snake, band;
+};
+
+// Fields of a fresh control block (the block is zeroed first).
+__device__ inline void state_init_fields(State* st, int k, int max_layers, int precision,
+                                         double n_occ, double c_pt, double c_d0, int tape,
+                                         int tape_base, int tape_states, int layout_k, int64_t n,
+                                         int order, int k1, FwdOpts fo, int hole) {
+  // complement form: the recursion converges to I - P, whose occupied levels
+  // are the n - n_occ highest ones
+  st->hole = hole;
+  if (hole) n_occ = (double)n - n_occ;
+  st->ckpt_k = fo.ckpt_k;
+  st->ckpt_slots = fo.ckpt_slots;
+  st->ckpt_pending = 0;
+  st->adj_seg_a = 0;
+  st->fwd_chunk = fo.chunk;
+  st->fwd_cta_pair = fo.cta_pair;
+  st->fwd_k_snake = fo.k_snake;
+  st->fwd_band = fo.band;
+  st->order = order;
+  st->k1 = order >= 2 ? k1 : k;
+  st->tape = tape;
+  st->tape_base = tape_base;
+  st->tape_states = tape_states;
+  st->layout_k = layout_k;
+  st->k_fwd = k;
+  st->n = n;
+  st->n_layer = 0;
+  st->round_ctr = 0u;
+  st->done = 0;
+  st->status = DMPT_OK;
+  st->timeout_flag = 0;
+  st->k = k;
+  st->max_layers = max_layers;
+  st->precision = precision;
+  st->n_occ = n_occ;
+  st->c_pt = c_pt;
+  st->c_d0 = c_d0;
+  st->plan_square = 0;
+  st->plan_write0 = 0;
+  for (int j = 0; j < kMaxK; ++j) st->plan_resp[j] = 0;
+}
+
 // Workspace layout (byte offsets from the workspace base, 256-aligned).
 struct Layout {
   int64_t n, Np;          // logical and padded size
@@ -253,6 +300,66 @@ cudaError_t launch_batch_all_done(const void* base, const long long* offs, int c
 // out[b] = the control block at base + offs[b], b < count (device arrays)
 cudaError_t launch_gather_states(const void* base, const long long* offs, int count, State* out,
                                  cudaStream_t s);
+
+// Batched set-up and outputs of the batch path: one launch per step of the
+// initial layer (Alg. 1: bounds, S_0 and S_1 of Sec. III A, the first decide)
+// and one for the outputs serve every active instance.  Each step splits its
+// work into units (groups of kBatchRows rows for the bounds, the initial
+// layer's blocks, chunks of kBatchChunk elements for the 16-bit split, groups
+// of kBatchRows rows of one matrix for the outputs); first[s * (count + 1) + i]
+// is the first unit of instance i in step s (exclusive prefix sums), so unit u
+// belongs to the instance i
+// with first[i] <= u < first[i + 1].  Every instance's values are those of
+// its single-instance launches: the bounds are exact minima and maxima, the
+// initial layer keeps its kInitBlocks virtual blocks (the ones without tile
+// pairs only hold zero partial sums, which the set-up writes), and the split
+// and the outputs are elementwise.
+constexpr int kInitBlocks = 1024;   // blocks (partial-sum entries) of the initial layer
+constexpr int kInitTile = 64;       // tile edge of the initial layer (Np is a multiple of 128)
+constexpr int kBatchRows = 8;       // rows per warp of the batched bounds; rows per
+                                    // block (one per warp) of the batched outputs
+constexpr int kBatchChunk = 4096;   // elements per block of the batched split
+enum BatchStep { kBsRows = 0, kBsInit = 1, kBsSplit = 2, kBsOut = 3, kBsSteps = 4 };
+struct BatchInst {
+  State* st;
+  void* master;        // FP32 (FP64 form: FP64) masters
+  uint16_t* ops;       // 16-bit operand slices (dual forms)
+  double* partials;
+  const double* H;     // inputs, row stride ld
+  const double* H1;
+  double* P;           // outputs, row stride ld (P may be null when k > 0)
+  double* P1;
+  int64_t n, Np, ld, ptiles;
+  double n_occ;
+  int k, layout_k, hole;
+  int init_blocks;     // initial-layer blocks that hold tile pairs (<= kInitBlocks)
+};
+// Per-batch fields of the fresh control blocks.
+struct BatchCommon {
+  int max_layers, precision;
+  double c_pt, c_d0;
+  FwdOpts fo;
+};
+// Units of each step for one instance (host and device agree on them).
+__host__ __device__ inline int64_t batch_units(int step, int64_t n, int64_t Np, int k) {
+  const int64_t tb = Np / kInitTile, pairs = tb * (tb + 1) / 2;
+  switch (step) {
+    case kBsRows: return (n + kBatchRows - 1) / kBatchRows;
+    case kBsInit: return pairs < kInitBlocks ? pairs : kInitBlocks;
+    case kBsSplit: return (int64_t)(1 + k) * ((Np * Np + kBatchChunk - 1) / kBatchChunk);
+    default: return (int64_t)(1 + k) * ((n + kBatchRows - 1) / kBatchRows);
+  }
+}
+// Fresh control blocks, bounds keys and the zero partial sums of the
+// initial layer's empty blocks; then the bounds, the initial layer, its
+// decide step and (dual forms) the 16-bit split, each one launch over all
+// `count` instances (device tables `bi`, `first`).
+cudaError_t launch_batch_setup(const BatchInst* bi, const int64_t* first, int count,
+                               const BatchCommon& c, const int64_t* units, bool dual, bool bf16,
+                               cudaStream_t s);
+// P, P1 of every instance (one launch).
+cudaError_t launch_batch_finalize(const BatchInst* bi, const int64_t* first, int count,
+                                  int64_t units, bool fp64, cudaStream_t s);
 
 // CUDA device of a handle (-1 for NULL).
 int handle_device(dmpt_handle h);

@@ -144,143 +144,168 @@ cudaError_t launch_bounds(const double* H, int64_t n, int64_t ld, double* eps_ou
 // matrices are exactly symmetric.  Partial sums per block: Tr S0, ||S0||_F^2,
 // ||S1_k||_F^2 and a count of non-finite values.
 
+// Block vb of a grid of vgrid blocks (256 threads): tile pairs vb, vb + vgrid,
+// ... of each matrix in turn (S0, then S1_1 .. S1_k).
 template <typename T>
-__global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const double* __restrict__ H,
-                                                   const double* __restrict__ H1, int64_t n,
-                                                   int64_t Np, int64_t ld, int k, int lk,
-                                                   int first_m, const double* __restrict__ shift,
-                                                   int k_zero, double* partials, int64_t ptiles) {
-  // 32 x 32 tile pairs (bi <= bj): the upper tile is read row-wise (coalesced),
-  // written in place and, through shared memory, transposed into the mirror
-  // tile, so both triangles of S come from the upper triangle of the input.
-  // Each value is formed in FP64 and rounded once to T.  The squared norms
-  // are summed in FP64 for the FP64 form; for T = float, as exact FP32
-  // products with TwoSum compensation (the FP64 rate of the part is low).
+__device__ __forceinline__ void init_body(State* st, T* master, const double* __restrict__ H,
+                                          const double* __restrict__ H1, int64_t n, int64_t Np,
+                                          int64_t ld, int k, int first_m,
+                                          const double* __restrict__ shift, int k_zero,
+                                          double* partials, int64_t ptiles, int64_t vb,
+                                          int64_t vgrid) {
+  // 64 x 64 tile pairs (bi <= bj): the upper tile is read row-wise (coalesced,
+  // every load of the tile in flight at once), written in place and, through
+  // shared memory, transposed into the mirror tile, so both triangles of S
+  // come from the upper triangle of the input.  Each value is formed in FP64
+  // and rounded once to T (for T = float, the off-diagonal values are formed
+  // in FP32).  The squared norms are summed in FP64 for the FP64 form; for
+  // T = float, as exact FP32 products with TwoSum compensation (the FP64 rate
+  // of the part is low).
   constexpr bool F32 = sizeof(T) == 4;
-  __shared__ T tile[32][33];
-  __shared__ double red[3 * 256];
+  constexpr int TS = kInitTile;
+  constexpr int RPT = TS * TS / 256;   // rows of the tile per thread
+  constexpr int RS = TS / RPT;         // row step between them
+  __shared__ T tile[TS][TS + 1];
+  __shared__ double red[2 * 256];
   const double e1 = st->eps1, eN = st->epsN;
-  const double w = 1.0 / (eN - e1);
+  __shared__ double w_sh;   // one FP64 division per block
+  if (threadIdx.x == 0) w_sh = 1.0 / (eN - e1);
+  __syncthreads();
+  const double w = w_sh;
+  const float wf = (float)w;
   const bool hole = st->hole != 0;   // complement form: S_0 = I - (eps_N I - H) w
   const size_t mat = (size_t)Np * Np;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
-  const int64_t TB = Np / 32;
+  const int tx = threadIdx.x % TS, ty = threadIdx.x / TS;   // 64 x 4 threads
+  const int64_t TB = Np / TS;
   const int64_t pairs = TB * (TB + 1) / 2;
-  double tr = 0.0, f0 = 0.0, bad = 0.0;
-  double f1[kMaxK];
-  float f0s = 0.0f, f0c = 0.0f;
-  float f1s[kMaxK], f1c[kMaxK];
+  int nbad = 0;
+  for (int m = first_m; m <= k; ++m) {
+    const double* src = m == 0 ? H : H1 + (size_t)(m - 1) * n * ld;
+    T* dst = master + (size_t)m * mat;   // buffer 0 (slots 0 .. layout k)
+    double tr = 0.0, fd = 0.0;
+    float fs = 0.0f, fc = 0.0f;
+    for (int64_t tp = vb; tp < pairs; tp += vgrid) {
+      // tile pair index -> (bi, bj), bj-major: tp = bj (bj + 1) / 2 + bi (an
+      // FP32 estimate of bj, corrected in integers)
+      int64_t bj = (int64_t)((sqrtf(8.0f * (float)tp + 1.0f) - 1.0f) * 0.5f);
+      while ((bj + 1) * (bj + 2) / 2 <= tp) ++bj;
+      while (bj * (bj + 1) / 2 > tp) --bj;
+      const int64_t bi = tp - bj * (bj + 1) / 2;
+      double hv[RPT];
+      {
+        const int64_t r0 = bi * TS + ty, c = bj * TS + tx;
+        const double* sp = src + r0 * ld + c;
+        // row r0 + RS i lies in the matrix when RS i < lim
+        const int lim = c < n ? (int)min((int64_t)TS, n - r0) : 0;
 #pragma unroll
-  for (int j = 0; j < kMaxK; ++j) {
-    f1[j] = 0.0;
-    f1s[j] = 0.0f;
-    f1c[j] = 0.0f;
-  }
-  for (int64_t tp = blockIdx.x; tp < pairs; tp += gridDim.x) {
-    // tile pair index -> (bi, bj), bj-major: tp = bj (bj + 1) / 2 + bi
-    int64_t bj = (int64_t)((sqrt(8.0 * (double)tp + 1.0) - 1.0) * 0.5);
-    while ((bj + 1) * (bj + 2) / 2 <= tp) ++bj;
-    while (bj * (bj + 1) / 2 > tp) --bj;
-    const int64_t bi = tp - bj * (bj + 1) / 2;
-    // m runs over a compile-time range so that the per-direction sums stay in registers
+        for (int i = 0; i < RPT; ++i) hv[i] = RS * i < lim ? sp[(int64_t)(RS * i) * ld] : 0.0;
+      }
+      if constexpr (F32) {
+        // off the diagonal in FP32 arithmetic (the FP64 rate of the part is
+        // low): v = -+ fl32(h) w32, within 1.5 units in the last place; zero
+        // outside the matrix (h = 0 there)
 #pragma unroll
-    for (int m = 0; m <= kMaxK; ++m) {
-      if (m < first_m || m > k) continue;   // uniform across the block
-      const double* src = m == 0 ? H : H1 + (size_t)(m - 1) * n * ld;
-      for (int i = 0; i < 4; ++i) {
-        const int rl = ty + 8 * i;
-        const int64_t r = bi * 32 + rl, c = bj * 32 + tx;
-        double v = 0.0;
-        if (r < n && c < n) {
-          double h = src[r * ld + c];
-          if (m > 0 && shift != nullptr && r == c) h += shift[(size_t)(m - 1) * n + r];
-          if (hole)
-            v = m == 0 ? (h - (r == c ? e1 : 0.0)) * w : h * w;
-          else
-            v = m == 0 ? ((r == c ? eN : 0.0) - h) * w : -h * w;
+        for (int i = 0; i < RPT; ++i) {
+          const float hw = (float)hv[i] * wf;
+          tile[ty + RS * i][tx] = hole ? hw : -hw;
         }
-        tile[rl][tx] = (T)v;   // the stored (rounded) value
+        // the diagonal element of column tx, formed in FP64 and rounded once
+        if (bi == bj && tx % RS == ty) {
+          const int64_t r = bi * TS + tx;
+          if (r < n) {
+            double h = src[r * ld + r];
+            if (m > 0 && shift != nullptr) h += shift[(size_t)(m - 1) * n + r];
+            const double x = hole ? (m == 0 ? (h - e1) * w : h * w)
+                                  : (m == 0 ? (eN - h) * w : -h * w);
+            const float xv = (float)x;
+            tile[tx][tx] = xv;
+            if (m == 0) tr += (double)xv;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+          const int rl = ty + RS * i;
+          const int64_t r = bi * TS + rl, c = bj * TS + tx;
+          double x = 0.0;
+          if (r < n && c < n) {
+            double h = hv[i];
+            if (m > 0 && shift != nullptr && r == c) h += shift[(size_t)(m - 1) * n + r];
+            if (hole)
+              x = m == 0 ? (h - (r == c ? e1 : 0.0)) * w : h * w;
+            else
+              x = m == 0 ? ((r == c ? eN : 0.0) - h) * w : -h * w;
+          }
+          tile[rl][tx] = (T)x;
+          if (m == 0 && r == c) tr += x;
+        }
       }
       __syncthreads();
-      T* dst = master + (size_t)m * mat;   // buffer 0 (slots 0 .. lk)
-      (void)lk;
-      for (int i = 0; i < 4; ++i) {
-        const int rl = ty + 8 * i;
-        const int64_t r = bi * 32 + rl, c = bj * 32 + tx;
+#pragma unroll 4
+      for (int i = 0; i < RPT; ++i) {
+        const int rl = ty + RS * i;
+        const int64_t r = bi * TS + rl, c = bj * TS + tx;
         // diagonal tile: the lower half mirrors the upper half
         const T v = (bi < bj || rl <= tx) ? tile[rl][tx] : tile[tx][rl];
         dst[(size_t)r * Np + c] = v;
-        if (m == 0 && r == c) tr += (double)v;
         if constexpr (F32) {
           const float wgt = bi < bj ? 2.0f : 1.0f;   // the mirror tile holds the same values
           const float p = wgt * v * v;
           const float e = wgt * fmaf(v, v, -v * v);
-          float& fs = m == 0 ? f0s : f1s[m - 1];
-          float& fc = m == 0 ? f0c : f1c[m - 1];
           const float tt = fs + p;
           const float bp = tt - fs;
           fc += (fs - (tt - bp)) + (p - bp) + e;
           fs = tt;
-          if (!isfinite(v)) bad += 1.0;
         } else {
           const double wgt = bi < bj ? 2.0 : 1.0;
-          if (m == 0)
-            f0 += wgt * (double)v * (double)v;
-          else
-            f1[m - 1] += wgt * (double)v * (double)v;
-          if (!isfinite((double)v)) bad += 1.0;
+          fd += wgt * v * v;
         }
-        if (bi < bj) dst[(size_t)(bj * 32 + rl) * Np + bi * 32 + tx] = tile[tx][rl];
+        nbad += isfinite(v) ? 0 : 1;
+        if (bi < bj) dst[(size_t)(bj * TS + rl) * Np + bi * TS + tx] = tile[tx][rl];
       }
       __syncthreads();
     }
-  }
-  if constexpr (F32) {
-    f0 = (double)f0s + (double)f0c;
-#pragma unroll
-    for (int j = 0; j < kMaxK; ++j) f1[j] = (double)f1s[j] + (double)f1c[j];
+    // partial sums of job m: Tr S0 (job 0) and ||S_m||_F^2
+    double v[2] = {tr, F32 ? (double)fs + (double)fc : fd};
+    block_sum<2, 256>(v, red);
+    if (threadIdx.x == 0) {
+      double* p = partials + ((size_t)m * ptiles + vb) * kNQ;
+      p[kQTrace] = m == 0 ? v[0] : 0.0;
+      p[kQFroNew] = v[1];
+      p[kQFroDiff] = 0.0;
+      p[kQBad] = 0.0;
+    }
   }
   // higher-order slots start at zero (a linear perturbation: H^(o) = 0, o >= 2)
   for (int m = k + 1; m <= k + k_zero; ++m) {
     T* dst = master + (size_t)m * mat;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)mat;
-         idx += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t idx = vb * blockDim.x + threadIdx.x; idx < (int64_t)mat;
+         idx += vgrid * blockDim.x)
       dst[idx] = (T)0;
     if (threadIdx.x == 0) {
-      double* p = partials + ((size_t)m * ptiles + blockIdx.x) * kNQ;
+      double* p = partials + ((size_t)m * ptiles + vb) * kNQ;
       p[kQTrace] = 0.0;
       p[kQFroNew] = 0.0;
       p[kQFroDiff] = 0.0;
       p[kQBad] = 0.0;
     }
   }
-  // job 0: trace, fro, bad (bad of the S1 part is reported under job 1 in replay)
-  {
-    double v[3] = {tr, f0, bad};
-    block_sum<3, 256>(v, red);
-    if (threadIdx.x == 0 && first_m == 0) {
-      double* p = partials + ((size_t)0 * ptiles + blockIdx.x) * kNQ;
-      p[kQTrace] = v[0];
-      p[kQFroNew] = v[1];
-      p[kQFroDiff] = 0.0;
-      p[kQBad] = v[2];
-    }
-    if (threadIdx.x == 0 && first_m == 1 && k > 0) {
-      double* p = partials + ((size_t)1 * ptiles + blockIdx.x) * kNQ;
-      p[kQBad] = v[2];
-    }
-  }
-  for (int j = 0; j < k; ++j) {
-    double v[1] = {f1[j]};
-    block_sum<1, 256>(v, red);
-    if (threadIdx.x == 0) {
-      double* p = partials + ((size_t)(1 + j) * ptiles + blockIdx.x) * kNQ;
-      p[kQTrace] = 0.0;
-      p[kQFroNew] = v[0];
-      p[kQFroDiff] = 0.0;
-      if (!(first_m == 1 && j == 0)) p[kQBad] = 0.0;
-    }
-  }
+  // the count of non-finite values goes with job 0 (job 1 in a replay, which
+  // starts at S1_1)
+  double vb_bad[1] = {(double)nbad};
+  block_sum<1, 256>(vb_bad, red);
+  if (threadIdx.x == 0 && (first_m == 0 || k > 0))
+    partials[((size_t)first_m * ptiles + vb) * kNQ + kQBad] = vb_bad[0];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) init_kernel(State* st, T* master, const double* __restrict__ H,
+                                                   const double* __restrict__ H1, int64_t n,
+                                                   int64_t Np, int64_t ld, int k, int first_m,
+                                                   const double* __restrict__ shift, int k_zero,
+                                                   double* partials, int64_t ptiles) {
+  init_body<T>(st, master, H, H1, n, Np, ld, k, first_m, shift, k_zero, partials, ptiles,
+               blockIdx.x, gridDim.x);
 }
 
 cudaError_t launch_init(const Layout& L, void* ws, const double* H, const double* H1,
@@ -291,12 +316,12 @@ cudaError_t launch_init(const Layout& L, void* ws, const double* H, const double
   double* partials = (double*)(base + L.off_partials);
   if (L.precision == DMPT_FP64)
     init_kernel<double><<<blocks, 256, 0, s>>>(st, (double*)(base + L.off_master), H, H1, L.n,
-                                               L.Np, ld, k, L.k, first_m, shift, k_zero,
-                                               partials, L.partial_tiles);
+                                               L.Np, ld, k, first_m, shift, k_zero, partials,
+                                               L.partial_tiles);
   else
     init_kernel<float><<<blocks, 256, 0, s>>>(st, (float*)(base + L.off_master), H, H1, L.n,
-                                              L.Np, ld, k, L.k, first_m, shift, k_zero,
-                                              partials, L.partial_tiles);
+                                              L.Np, ld, k, first_m, shift, k_zero, partials,
+                                              L.partial_tiles);
   return cudaGetLastError();
 }
 
@@ -1066,24 +1091,45 @@ __device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float x) {
 __device__ __forceinline__ float from16(__half x) { return __half2float(x); }
 __device__ __forceinline__ float from16(__nv_bfloat16 x) { return __bfloat162float(x); }
 
+__device__ __forceinline__ unsigned short bits16(__half x) { return __half_as_ushort(x); }
+__device__ __forceinline__ unsigned short bits16(__nv_bfloat16 x) {
+  return __bfloat16_as_ushort(x);
+}
+
+// Elements idx .. idx + 3 (idx a multiple of 4) of a master: x = src 2^e,
+// hi = x rounded to 16 bits, lo = (x - hi) rounded to 16 bits.
 template <typename H16>
-__global__ void split_kernel(const State* st, const float* __restrict__ master, H16* ops,
-                             int64_t Np, int k, int first_job) {
-  const size_t mat = (size_t)Np * Np;
+__device__ __forceinline__ void split4(const float* __restrict__ src, unsigned short* hi,
+                                       unsigned short* lo, size_t idx, int e) {
+  const float4 v = *reinterpret_cast<const float4*>(src + idx);
+  const float x[4] = {ldexpf(v.x, e), ldexpf(v.y, e), ldexpf(v.z, e), ldexpf(v.w, e)};
+  unsigned short hb[4], lb[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const H16 h = to16<H16>(x[t]);
+    hb[t] = bits16(h);
+    lb[t] = bits16(to16<H16>(x[t] - from16(h)));
+  }
+  *reinterpret_cast<uint2*>(hi + idx) =
+      make_uint2(hb[0] | ((unsigned)hb[1] << 16), hb[2] | ((unsigned)hb[3] << 16));
+  *reinterpret_cast<uint2*>(lo + idx) =
+      make_uint2(lb[0] | ((unsigned)lb[1] << 16), lb[2] | ((unsigned)lb[3] << 16));
+}
+
+template <typename H16>
+__global__ void split_kernel(const State* st, const float* __restrict__ master,
+                             unsigned short* ops, int64_t Np, int k, int first_job) {
+  const size_t mat = (size_t)Np * Np;   // a multiple of 4
   const int m = first_job + blockIdx.y;  // matrix: 0 = S0, 1 + j = S1_j
   const int cur = m == 0 ? st->cur0 : st->cur1[m - 1];
   const int e = m == 0 ? st->s0_exp : st->s1_exp_cur[m - 1];
   const float* src = master + (size_t)(cur * (1 + k) + m) * mat;
   const int zh = m == 0 ? st->z0_cur : zslice(cur, m, 0, k);
-  H16* hi = ops + (size_t)zh * mat;
-  H16* lo = ops + (size_t)(zh + 1) * mat;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < mat;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const float x = ldexpf(src[i], e);
-    const H16 h = to16<H16>(x);
-    hi[i] = h;
-    lo[i] = to16<H16>(x - from16(h));
-  }
+  unsigned short* hi = ops + (size_t)zh * mat;
+  unsigned short* lo = ops + (size_t)(zh + 1) * mat;
+  for (size_t i = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i < mat;
+       i += (size_t)gridDim.x * blockDim.x * 4)
+    split4<H16>(src, hi, lo, i, e);
 }
 
 cudaError_t launch_split(const Layout& L, void* ws, int first_job, cudaStream_t s, int jobs) {
@@ -1092,11 +1138,11 @@ cudaError_t launch_split(const Layout& L, void* ws, int first_job, cudaStream_t 
   dim3 grid(152 * 4, jobs < 0 ? 1 + L.k - first_job : jobs);
   if (L.precision == DMPT_DUAL_FP16)
     split_kernel<__half><<<grid, 256, 0, s>>>(st, (const float*)(base + L.off_master),
-                                              (__half*)(base + L.off_ops16), L.Np, L.k,
+                                              (unsigned short*)(base + L.off_ops16), L.Np, L.k,
                                               first_job);
   else
     split_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(st, (const float*)(base + L.off_master),
-                                                     (__nv_bfloat16*)(base + L.off_ops16),
+                                                     (unsigned short*)(base + L.off_ops16),
                                                      L.Np, L.k, first_job);
   return cudaGetLastError();
 }
@@ -1280,11 +1326,31 @@ cudaError_t launch_adj_finalize(const Layout& L, void* ws, double* dLdH, int64_t
 // ---------------------------------------------------------------------------
 // Outputs: P = S0, P1_k = S1_k (orthogonal basis, Z = I), as float64.
 
+// One output row r of matrix y (0 = P, 1 + j = P1_j) by one warp; the
+// complement form (the recursion ran on I - P) gives P = I - S0, P_o = -S_o.
+template <typename T>
+__device__ __forceinline__ void finalize_row(const T* __restrict__ srow, double* drow, int64_t n,
+                                             int64_t r, int y, bool hole, int lane) {
+  for (int64_t c0 = 0; c0 < n; c0 += 128) {
+    double v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t c = c0 + 32 * q + lane;
+      v[q] = c < n ? (double)srow[c] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t c = c0 + 32 * q + lane;
+      if (c < n) drow[c] = !hole ? v[q] : (y == 0 ? (r == c ? 1.0 : 0.0) - v[q] : -v[q]);
+    }
+  }
+}
+
 template <typename T>
 __global__ void finalize_kernel(const State* st, const T* __restrict__ master, double* P,
                                 double* P1, int64_t n, int64_t Np, int64_t ld, int k, int slot0) {
   // k: layout slots; grid.y = 1 + the number of blocks written to P1, which
-  // come from slots slot0, slot0 + 1, ...
+  // come from slots slot0, slot0 + 1, ...; one warp per row
   const size_t mat = (size_t)Np * Np;
   const int y = blockIdx.y;
   if (y == 0 && P == nullptr) return;
@@ -1292,14 +1358,11 @@ __global__ void finalize_kernel(const State* st, const T* __restrict__ master, d
   const int cur = m == 0 ? st->cur0 : st->cur1[m - 1];
   const T* src = master + (size_t)(cur * (1 + k) + m) * mat;
   double* dst = y == 0 ? P : P1 + (size_t)(y - 1) * n * ld;
-  const bool hole = st->hole != 0;   // the recursion ran on I - P: P = I - S0, P_o = -S_o
-  const int64_t total = n * n;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / n, c = i - r * n;
-    const double v = (double)src[(size_t)r * Np + c];
-    dst[r * ld + c] = !hole ? v : (y == 0 ? (r == c ? 1.0 : 0.0) - v : -v);
-  }
+  const bool hole = st->hole != 0;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += nw)
+    finalize_row(src + r * Np, dst + r * ld, n, r, y, hole, lane);
 }
 
 cudaError_t launch_finalize(const Layout& L, void* ws, double* P, double* P1, int64_t ld,
@@ -1370,6 +1433,200 @@ cudaError_t launch_gather_states(const void* base, const long long* offs, int co
                                  cudaStream_t s) {
   if (count < 1) return cudaSuccess;
   gather_states_kernel<<<count, 256, 0, s>>>((const char*)base, offs, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Batched set-up and outputs of the batch path (one launch per step for every
+// instance; the values are those of the single-instance kernels above).
+
+// The instance that owns unit u: the largest i with first[i] <= u
+// (first[0] = 0 <= u < first[count]).
+__device__ __forceinline__ int batch_find(const int64_t* __restrict__ first, int count,
+                                          int64_t u) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= u)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// One block per instance: a zeroed control block with its fields, the bounds
+// keys, and zero partial sums for the initial layer's blocks that hold no
+// tile pair.
+__global__ void __launch_bounds__(256) batch_setup_kernel(const BatchInst* __restrict__ bi,
+                                                          BatchCommon c) {
+  const BatchInst& b = bi[blockIdx.x];
+  static_assert(sizeof(State) % 4 == 0, "State zeroed as words");
+  unsigned* w = reinterpret_cast<unsigned*>(b.st);
+  for (int i = threadIdx.x; i < (int)(sizeof(State) / 4); i += blockDim.x) w[i] = 0u;
+  const int64_t empty = (int64_t)(kInitBlocks - b.init_blocks) * kNQ;
+  for (int j = 0; j <= b.k; ++j) {
+    double* p = b.partials + ((size_t)j * b.ptiles + b.init_blocks) * kNQ;
+    for (int64_t e = threadIdx.x; e < empty; e += blockDim.x) p[e] = 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    state_init_fields(b.st, b.k, c.max_layers, c.precision, b.n_occ, c.c_pt, c.c_d0, 0,
+                      4 * (1 + b.layout_k), 0, b.layout_k, b.n, 1, 0, c.fo, b.hole);
+    long long* key = reinterpret_cast<long long*>(&b.st->eps1);
+    key[0] = dkey(INFINITY);
+    key[1] = dkey(-INFINITY);
+  }
+}
+
+// Gershgorin discs (as bounds_rows_kernel): one warp per kBatchRows rows of
+// one instance, each row's radius summed in the same lane order.
+__global__ void batch_bounds_rows_kernel(const BatchInst* __restrict__ bi,
+                                         const int64_t* __restrict__ first, int count) {
+  const int lane = threadIdx.x & 31;
+  const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (u >= first[count]) return;   // uniform across the warp
+  const int i = batch_find(first, count, u);
+  const BatchInst& b = bi[i];
+  const int64_t r0 = (u - first[i]) * kBatchRows;
+  double lo = INFINITY, hi = -INFINITY;
+  for (int64_t r = r0; r < r0 + kBatchRows && r < b.n; ++r) {
+    const double* row = b.H + r * b.ld;
+    double s = 0.0;
+    for (int64_t j = lane; j < b.n; j += 32) s += fabs(row[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const double d = row[r];
+    const double rad = s - fabs(d);
+    lo = fmin(lo, d - rad);
+    hi = fmax(hi, d + rad);
+  }
+  if (lane == 0) {
+    long long* key = reinterpret_cast<long long*>(&b.st->eps1);
+    atomicMin(&key[0], dkey(lo));
+    atomicMax(&key[1], dkey(hi));
+  }
+}
+
+__global__ void batch_bounds_fin_kernel(const BatchInst* __restrict__ bi, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  long long* key = reinterpret_cast<long long*>(&bi[i].st->eps1);
+  const double lo = dkey_inv(key[0]);
+  const double hi = dkey_inv(key[1]);
+  bi[i].st->eps1 = lo;
+  bi[i].st->epsN = hi;
+}
+
+// Initial layer: unit u is virtual block u - first[i] of instance i's grid of
+// kInitBlocks blocks.
+template <typename T>
+__global__ void __launch_bounds__(256) batch_init_kernel(const BatchInst* __restrict__ bi,
+                                                         const int64_t* __restrict__ first,
+                                                         int count) {
+  const int64_t u = blockIdx.x;
+  const int i = batch_find(first, count, u);
+  const BatchInst& b = bi[i];
+  init_body<T>(b.st, static_cast<T*>(b.master), b.H, b.H1, b.n, b.Np, b.ld, b.k, 0, nullptr, 0,
+               b.partials, b.ptiles, u - first[i], kInitBlocks);
+}
+
+__global__ void __launch_bounds__(256) batch_decide_init_kernel(const BatchInst* __restrict__ bi) {
+  __shared__ double red[kNQ * 256];
+  __shared__ double sums[kMaxK + 1][kNQ];
+  const BatchInst& b = bi[blockIdx.x];
+  decide_body(b.st, b.partials, b.ptiles, kInitBlocks, kDecideInit, red, sums);
+}
+
+// 16-bit split of matrices 0 .. layout k (as split_kernel), kBatchChunk
+// elements per block, four per thread and step.
+template <typename H16>
+__global__ void __launch_bounds__(256) batch_split_kernel(const BatchInst* __restrict__ bi,
+                                                          const int64_t* __restrict__ first,
+                                                          int count) {
+  const int64_t u = blockIdx.x;
+  const int i = batch_find(first, count, u);
+  const BatchInst& b = bi[i];
+  const State* st = b.st;
+  const int lk = b.layout_k;
+  const size_t mat = (size_t)b.Np * b.Np;   // a multiple of 4
+  const int64_t cpm = (int64_t)((mat + kBatchChunk - 1) / kBatchChunk);
+  const int64_t c = u - first[i];
+  const int m = (int)(c / cpm);
+  const size_t e0 = (size_t)(c - (int64_t)m * cpm) * kBatchChunk;
+  const int cur = m == 0 ? st->cur0 : st->cur1[m - 1];
+  const int e = m == 0 ? st->s0_exp : st->s1_exp_cur[m - 1];
+  const float* src = static_cast<const float*>(b.master) + (size_t)(cur * (1 + lk) + m) * mat;
+  const int zh = m == 0 ? st->z0_cur : zslice(cur, m, 0, lk);
+  unsigned short* hi = b.ops + (size_t)zh * mat;
+  unsigned short* lo = b.ops + (size_t)(zh + 1) * mat;
+#pragma unroll
+  for (int q = 0; q < kBatchChunk / (4 * 256); ++q) {
+    const size_t idx = e0 + (size_t)(q * 256 + threadIdx.x) * 4;
+    if (idx >= mat) break;
+    split4<H16>(src, hi, lo, idx, e);
+  }
+}
+
+// Outputs (as finalize_kernel with slot0 = 1): unit c of matrix y (0 = P,
+// 1 + j = P1_j) is rows [c, c + 1) * kBatchRows, one warp per row.
+template <typename T>
+__global__ void __launch_bounds__(256) batch_finalize_kernel(const BatchInst* __restrict__ bi,
+                                                             const int64_t* __restrict__ first,
+                                                             int count) {
+  static_assert(kBatchRows == 256 / 32, "one warp per row of a unit");
+  const int64_t u = blockIdx.x;
+  const int i = batch_find(first, count, u);
+  const BatchInst& b = bi[i];
+  const int64_t n = b.n;
+  const int64_t cpm = (n + kBatchRows - 1) / kBatchRows;
+  const int64_t c = u - first[i];
+  const int y = (int)(c / cpm);
+  if (y == 0 && b.P == nullptr) return;
+  const int64_t r = (c - (int64_t)y * cpm) * kBatchRows + (threadIdx.x >> 5);
+  if (r >= n) return;
+  const State* st = b.st;
+  const size_t mat = (size_t)b.Np * b.Np;
+  const int cur = y == 0 ? st->cur0 : st->cur1[y - 1];
+  const T* src = static_cast<const T*>(b.master) + (size_t)(cur * (1 + b.layout_k) + y) * mat;
+  double* dst = y == 0 ? b.P : b.P1 + (size_t)(y - 1) * n * b.ld;
+  finalize_row(src + r * b.Np, dst + r * b.ld, n, r, y, st->hole != 0, threadIdx.x & 31);
+}
+
+cudaError_t launch_batch_setup(const BatchInst* bi, const int64_t* first, int count,
+                               const BatchCommon& c, const int64_t* units, bool dual, bool bf16,
+                               cudaStream_t s) {
+  if (count < 1) return cudaSuccess;
+  const int64_t* f_rows = first + kBsRows * (count + 1);
+  const int64_t* f_init = first + kBsInit * (count + 1);
+  const int64_t* f_split = first + kBsSplit * (count + 1);
+  batch_setup_kernel<<<count, 256, 0, s>>>(bi, c);
+  batch_bounds_rows_kernel<<<(unsigned)((units[kBsRows] * 32 + 255) / 256), 256, 0, s>>>(
+      bi, f_rows, count);
+  batch_bounds_fin_kernel<<<(count + 255) / 256, 256, 0, s>>>(bi, count);
+  if (c.precision == DMPT_FP64)
+    batch_init_kernel<double><<<(unsigned)units[kBsInit], 256, 0, s>>>(bi, f_init, count);
+  else
+    batch_init_kernel<float><<<(unsigned)units[kBsInit], 256, 0, s>>>(bi, f_init, count);
+  batch_decide_init_kernel<<<count, 256, 0, s>>>(bi);
+  if (dual && units[kBsSplit] > 0) {
+    if (bf16)
+      batch_split_kernel<__nv_bfloat16><<<(unsigned)units[kBsSplit], 256, 0, s>>>(bi, f_split,
+                                                                                  count);
+    else
+      batch_split_kernel<__half><<<(unsigned)units[kBsSplit], 256, 0, s>>>(bi, f_split, count);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_finalize(const BatchInst* bi, const int64_t* first, int count,
+                                  int64_t units, bool fp64, cudaStream_t s) {
+  if (count < 1 || units < 1) return cudaSuccess;
+  const int64_t* f_out = first + kBsOut * (count + 1);
+  if (fp64)
+    batch_finalize_kernel<double><<<(unsigned)units, 256, 0, s>>>(bi, f_out, count);
+  else
+    batch_finalize_kernel<float><<<(unsigned)units, 256, 0, s>>>(bi, f_out, count);
   return cudaGetLastError();
 }
 }  // namespace dmpt
