@@ -473,6 +473,10 @@ def main():
     # hosts a buffer's first transfers can run at a tenth of the link rate)
     ctx.solve_host([Hh] * e_steps, [H1h] * e_steps, inst.n_occ,
                    P1_out=[P1h[i % 2] for i in range(e_steps)], **kwh)
+    # the host link just before the timed steps (it is measured again after them)
+    Htmp = torch.empty_like(H)
+    link_before = measure_copy_bandwidth(Hh, Htmp, stream)
+    del Htmp
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
@@ -832,6 +836,9 @@ def main():
                     "api": "dmpt_sp2_response_host", "equals_device_result": e2e_same,
                     "h2d_gbs": h2d_gbs, "d2h_gbs": d2h_gbs,
                     "h2d_gbs_slowest_of_5": h2d_min, "d2h_gbs_slowest_of_5": d2h_min,
+                    "link_gbs_before_timed_steps": {
+                        "h2d": link_before[0], "d2h": link_before[1],
+                        "h2d_slowest_of_5": link_before[2], "d2h_slowest_of_5": link_before[3]},
                     "copy_ms_if_serial": copy_ms_serial,
                     "exposed_ms_per_step": e2e_ms - ms_max,
                     # the pipeline hides every copy but the first copy-in and the
