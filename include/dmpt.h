@@ -309,11 +309,18 @@ dmpt_status dmpt_sp2_backward(dmpt_handle h, const double* G, int64_t n, int64_t
                               size_t ws_bytes, void* stream);
 
 /* Many independent instances of dmpt_sp2_response in one call (uneven
- * sizes), e.g. a batch of molecules.  Each instance runs its own layer loop
- * (Algorithms 1-3) on its own internal stream with layer-product kernels
- * sized to its tile count, so small instances share the GPU; one CUDA graph
- * holds one layer of every instance and is replayed until all have
- * converged (kernels of finished instances exit at once).
+ * sizes), e.g. a batch of molecules; each instance keeps its own control
+ * block and takes its own decisions (Algorithms 1-3).  The initial layer
+ * (bounds, S_0 and S_1 of Sec. III A, its decide step, the 16-bit split)
+ * and the outputs of all instances take one launch per step.  In the dual
+ * forms on CTA pairs (first order, up to 1024 non-trivial instances) one
+ * grouped tensor-core launch per layer step serves every instance from one
+ * pool of tiles, claimed through a device-side queue, followed by one
+ * batched decide launch; otherwise every instance's layer kernels run on an
+ * internal stream of its own.  One CUDA graph holds a layer step and is
+ * replayed until all instances have converged (finished instances add no
+ * work).  Each instance's results equal those of its own dmpt_sp2_response
+ * call bit for bit, except on 256 x 128 tiles (o->group_tile_n = 128).
  *   count       instances; H, H1, P, P1: host arrays of `count` device
  *               pointers (H1/P1 entries: k blocks of n_i x n_i (ld_i)).
  *   n, ld, n_occ: host arrays of `count` values.
