@@ -1148,6 +1148,33 @@ cudaError_t launch_split(const Layout& L, void* ws, int first_job, cudaStream_t 
 }
 
 // ---------------------------------------------------------------------------
+// Whole-matrix readers of the masters.  The tensor-core layer epilogue keeps
+// an FP32 master in one orientation only (element (r, c) at (max, min): the
+// lower triangle with the diagonal); the other kernels write both.  So a
+// reader takes output tile (bi, bj) (32 x 32, 256 threads) from the lower
+// tile (max(bi, bj), min(bi, bj)): loaded row by row (coalesced) into shared
+// memory, written row by row, transposed where the output tile lies above
+// the diagonal.  `put(r, c, v)` writes the value of element (r, c), r, c < n.
+template <typename T, class Put>
+__device__ __forceinline__ void sym_tile(const T* __restrict__ src, int64_t Np, int64_t n,
+                                         int64_t bi, int64_t bj, T (*t)[33], Put put) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+  const int64_t lr = 32 * (bi > bj ? bi : bj), lc = 32 * (bi > bj ? bj : bi);
+#pragma unroll
+  for (int i = ty; i < 32; i += 8) t[i][tx] = src[(lr + i) * Np + lc + tx];
+  __syncthreads();
+#pragma unroll
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t r = 32 * bi + i, c = 32 * bj + tx;
+    if (r < n && c < n) {
+      const T v = bi > bj ? t[i][tx] : (bi < bj ? t[tx][i] : (tx <= i ? t[i][tx] : t[tx][i]));
+      put(r, c, v);
+    }
+  }
+  __syncthreads();   // the block's next tile reuses t
+}
+
+// ---------------------------------------------------------------------------
 // Checkpoints of the S0 recursion (ckpt_every = k >= 2) and the recompute of a
 // segment of states from its checkpoint in the backward pass.
 
@@ -1188,12 +1215,26 @@ __global__ void seg_load_kernel(State* st, float4* master, const float4* __restr
   }
 }
 
+// The upper triangle of an Np x Np master from its lower triangle (a
+// checkpoint of a state that a tensor-core layer wrote holds only the lower
+// one; the hi/lo split that follows a reload reads the whole matrix).
+__global__ void __launch_bounds__(256) mirror_lower_kernel(float* M, int64_t Np) {
+  __shared__ float t[32][33];
+  const int64_t tb = Np / 32;
+  for (int64_t tile = blockIdx.x; tile < tb * tb; tile += gridDim.x) {
+    const int64_t bi = tile / tb, bj = tile % tb;
+    if (bi > bj) continue;   // uniform across the block: lower tiles are only read
+    sym_tile<float>(M, Np, Np, bi, bj, t, [&](int64_t r, int64_t c, float v) { M[r * Np + c] = v; });
+  }
+}
+
 cudaError_t launch_seg_load(const Layout& L, void* ws, int c, int a, cudaStream_t s) {
   if (c < 0 || c >= L.ckpt_slots) return cudaErrorInvalidValue;
   char* base = (char*)ws;
   seg_load_kernel<<<152 * 4, 256, 0, s>>>((State*)(base + L.off_state),
                                           (float4*)(base + L.off_master),
                                           (const float4*)(base + L.off_ckpt), L.Np, c, a);
+  mirror_lower_kernel<<<152 * 16, 256, 0, s>>>((float*)(base + L.off_master), L.Np);
   return cudaGetLastError();
 }
 
@@ -1301,23 +1342,25 @@ cudaError_t launch_adj_init(const Layout& L, void* ws, const double* G, int64_t 
   return cudaGetLastError();
 }
 
-__global__ void adj_finalize_kernel(const State* st, const float* __restrict__ master,
-                                    double* dLdH, int64_t n, int64_t Np, int64_t ld, int lk) {
+__global__ void __launch_bounds__(256) adj_finalize_kernel(const State* st,
+                                                           const float* __restrict__ master,
+                                                           double* dLdH, int64_t n, int64_t Np,
+                                                           int64_t ld, int lk) {
+  __shared__ float t[32][33];
   const size_t mat = (size_t)Np * Np;
   const float* src = master + (size_t)(st->cur1[0] * (1 + lk) + 1) * mat;
   const double scale = -1.0 / (st->epsN - st->eps1);
-  const int64_t total = n * n;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / n, c = i - r * n;
-    dLdH[r * ld + c] = scale * (double)src[(size_t)r * Np + c];
-  }
+  const int64_t tb = (n + 31) / 32;
+  for (int64_t tile = blockIdx.x; tile < tb * tb; tile += gridDim.x)
+    sym_tile<float>(src, Np, n, tile / tb, tile % tb, t, [&](int64_t r, int64_t c, float v) {
+      dLdH[r * ld + c] = scale * (double)v;
+    });
 }
 
 cudaError_t launch_adj_finalize(const Layout& L, void* ws, double* dLdH, int64_t ld,
                                 cudaStream_t s) {
   char* base = (char*)ws;
-  adj_finalize_kernel<<<152 * 4, 256, 0, s>>>((const State*)(base + L.off_state),
+  adj_finalize_kernel<<<152 * 16, 256, 0, s>>>((const State*)(base + L.off_state),
                                               (const float*)(base + L.off_master), dLdH, L.n,
                                               L.Np, ld, L.k);
   return cudaGetLastError();
@@ -1326,31 +1369,21 @@ cudaError_t launch_adj_finalize(const Layout& L, void* ws, double* dLdH, int64_t
 // ---------------------------------------------------------------------------
 // Outputs: P = S0, P1_k = S1_k (orthogonal basis, Z = I), as float64.
 
-// One output row r of matrix y (0 = P, 1 + j = P1_j) by one warp; the
-// complement form (the recursion ran on I - P) gives P = I - S0, P_o = -S_o.
-template <typename T>
-__device__ __forceinline__ void finalize_row(const T* __restrict__ srow, double* drow, int64_t n,
-                                             int64_t r, int y, bool hole, int lane) {
-  for (int64_t c0 = 0; c0 < n; c0 += 128) {
-    double v[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t c = c0 + 32 * q + lane;
-      v[q] = c < n ? (double)srow[c] : 0.0;
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t c = c0 + 32 * q + lane;
-      if (c < n) drow[c] = !hole ? v[q] : (y == 0 ? (r == c ? 1.0 : 0.0) - v[q] : -v[q]);
-    }
-  }
+// Output element (r, c) of matrix y (0 = P, 1 + j = P1_j) from master value v;
+// the complement form (the recursion ran on I - P) gives P = I - S0,
+// P_o = -S_o.
+__device__ __forceinline__ double out_value(double v, int64_t r, int64_t c, int y, bool hole) {
+  return !hole ? v : (y == 0 ? (r == c ? 1.0 : 0.0) - v : -v);
 }
 
 template <typename T>
-__global__ void finalize_kernel(const State* st, const T* __restrict__ master, double* P,
-                                double* P1, int64_t n, int64_t Np, int64_t ld, int k, int slot0) {
+__global__ void __launch_bounds__(256) finalize_kernel(const State* st,
+                                                       const T* __restrict__ master, double* P,
+                                                       double* P1, int64_t n, int64_t Np,
+                                                       int64_t ld, int k, int slot0) {
   // k: layout slots; grid.y = 1 + the number of blocks written to P1, which
-  // come from slots slot0, slot0 + 1, ...; one warp per row
+  // come from slots slot0, slot0 + 1, ...; 32 x 32 output tiles
+  __shared__ T t[32][33];
   const size_t mat = (size_t)Np * Np;
   const int y = blockIdx.y;
   if (y == 0 && P == nullptr) return;
@@ -1359,17 +1392,18 @@ __global__ void finalize_kernel(const State* st, const T* __restrict__ master, d
   const T* src = master + (size_t)(cur * (1 + k) + m) * mat;
   double* dst = y == 0 ? P : P1 + (size_t)(y - 1) * n * ld;
   const bool hole = st->hole != 0;
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += nw)
-    finalize_row(src + r * Np, dst + r * ld, n, r, y, hole, lane);
+  const int64_t tb = (n + 31) / 32;
+  for (int64_t tile = blockIdx.x; tile < tb * tb; tile += gridDim.x)
+    sym_tile<T>(src, Np, n, tile / tb, tile % tb, t, [&](int64_t r, int64_t c, T v) {
+      dst[r * ld + c] = out_value((double)v, r, c, y, hole);
+    });
 }
 
 cudaError_t launch_finalize(const Layout& L, void* ws, double* P, double* P1, int64_t ld,
                             int k_out, cudaStream_t s, int slot0) {
   char* base = (char*)ws;
   const State* st = (const State*)(base + L.off_state);
-  dim3 grid(152 * 4, 1 + k_out);
+  dim3 grid(152 * 16, 1 + k_out);
   if (L.precision == DMPT_FP64)
     finalize_kernel<double><<<grid, 256, 0, s>>>(st, (const double*)(base + L.off_master), P,
                                                  P1, L.n, L.Np, ld, L.k, slot0);
@@ -1569,28 +1603,31 @@ __global__ void __launch_bounds__(256) batch_split_kernel(const BatchInst* __res
 }
 
 // Outputs (as finalize_kernel with slot0 = 1): unit c of matrix y (0 = P,
-// 1 + j = P1_j) is rows [c, c + 1) * kBatchRows, one warp per row.
+// 1 + j = P1_j) is output tile c of that matrix (32 x 32 tiles, row-major).
 template <typename T>
 __global__ void __launch_bounds__(256) batch_finalize_kernel(const BatchInst* __restrict__ bi,
                                                              const int64_t* __restrict__ first,
                                                              int count) {
-  static_assert(kBatchRows == 256 / 32, "one warp per row of a unit");
+  __shared__ T t[32][33];
   const int64_t u = blockIdx.x;
   const int i = batch_find(first, count, u);
   const BatchInst& b = bi[i];
   const int64_t n = b.n;
-  const int64_t cpm = (n + kBatchRows - 1) / kBatchRows;
+  const int64_t tb = (n + 31) / 32;
   const int64_t c = u - first[i];
-  const int y = (int)(c / cpm);
+  const int y = (int)(c / (tb * tb));
   if (y == 0 && b.P == nullptr) return;
-  const int64_t r = (c - (int64_t)y * cpm) * kBatchRows + (threadIdx.x >> 5);
-  if (r >= n) return;
+  const int64_t tile = c - (int64_t)y * tb * tb;
   const State* st = b.st;
   const size_t mat = (size_t)b.Np * b.Np;
   const int cur = y == 0 ? st->cur0 : st->cur1[y - 1];
   const T* src = static_cast<const T*>(b.master) + (size_t)(cur * (1 + b.layout_k) + y) * mat;
   double* dst = y == 0 ? b.P : b.P1 + (size_t)(y - 1) * n * b.ld;
-  finalize_row(src + r * b.Np, dst + r * b.ld, n, r, y, st->hole != 0, threadIdx.x & 31);
+  const bool hole = st->hole != 0;
+  const int64_t ld = b.ld;
+  sym_tile<T>(src, b.Np, n, tile / tb, tile % tb, t, [&](int64_t r, int64_t cc, T v) {
+    dst[r * ld + cc] = out_value((double)v, r, cc, y, hole);
+  });
 }
 
 cudaError_t launch_batch_setup(const BatchInst* bi, const int64_t* first, int count,

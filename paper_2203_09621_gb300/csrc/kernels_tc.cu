@@ -340,23 +340,25 @@ __device__ __forceinline__ uint32_t h16_bits(H16 x) {
 // Forms S_new = sigma X + (1 - sigma) S_old (Eq. (eq:Sn) / Eq. (dB)), its
 // FP16/BF16 hi/lo split (Sec. II C), the partial sums (||S_new||_F^2 with
 // TwoSum compensation, ||S_old - X||_F^2, trace, non-finite count) and stores
-// each owned element (column >= row) at (r, c) and (c, r).  OFF: the tile is
-// off the diagonal (every column > every row).
+// each owned element (column >= row).  OFF: the tile is off the diagonal
+// (every column > every row).
 //
 // Memory access pattern.  A warp holds 32 consecutive rows (one per lane)
 // and the same columns, so an access down a column (lane = row) is one
 // contiguous segment while an access along its rows touches 32 lines.
-//  * S_old is read down the columns: the masters are exactly symmetric
-//    (both halves are written with the same value), so S_old[r][c] is read
-//    at (c, r), 16 columns per batch of loads; the next batch is loaded
-//    while the current one is stored.
-//  * The mirror (c, r) is stored down the columns directly.
-//  * The row-direction stores (r, c) go through this warp's transpose
-//    buffer `xp` in shared memory (32 rows of XP_STRIDE words; 16 columns at
-//    a time): each lane writes its row, then the warp stores 4 rows x 64 B
-//    (FP32) or 4 rows x 32 B (hi, lo) per instruction.  The row stride of
-//    20 words keeps both the 16-byte row writes and the column-pair reads
-//    free of bank conflicts.
+//  * The FP32 master is kept in one orientation only: element (r, c),
+//    c >= r, at (c, r) (the lower triangle with the diagonal), written and
+//    read down the columns.  S_old[r][c] is read there, 16 columns per batch
+//    of loads; the next batch is loaded while the current one is stored.
+//    The readers of a whole master (outputs, checkpoint reloads) take
+//    element (r, c) from (max(r, c), min(r, c)).
+//  * The 16-bit operand copies, which the tensor maps read as row panels,
+//    are stored in both orientations: the mirror (c, r) down the columns,
+//    and (r, c) through this warp's transpose buffer `xp` in shared memory
+//    (32 rows of XP_STRIDE words; 16 columns at a time): each lane writes
+//    its row, then the warp stores 4 rows x 32 B (hi, lo) per instruction.
+//    The row stride of 20 words keeps both the 16-byte row writes and the
+//    column-pair reads free of bank conflicts.
 // The sums run over the columns in ascending order, so every thread's
 // partial sums do not depend on the memory access pattern.
 constexpr int XP_STRIDE = 20;                       // words per buffer row
@@ -378,7 +380,6 @@ __device__ __forceinline__ void rolled_tile_epilogue(
   float* Snc = Snew + col_base;
   uint16_t* hic = reinterpret_cast<uint16_t*>(hi_new) + col_base;
   uint16_t* loc = reinterpret_cast<uint16_t*>(lo_new) + col_base;
-  float* Snr = Snew + row_base;
   uint16_t* hir = reinterpret_cast<uint16_t*>(hi_new) + row_base;
   uint16_t* lor = reinterpret_cast<uint16_t*>(lo_new) + row_base;
   float olds[16];   // S_old of the current 16 columns; the next 16 are loaded
@@ -390,10 +391,8 @@ __device__ __forceinline__ void rolled_tile_epilogue(
     uint32_t xs[16];
     tmem_ld16(ta_sum + 16 * g16, xs);
     const int cb16 = c0 + 16 * g16;
-    // FP32 values go to the transpose buffer as each group of 4 is formed;
     // the hi/lo bits stay in registers, packed in column pairs, until the
-    // FP32 rows have been stored
-    float4* xr = reinterpret_cast<float4*>(xp + lane * XP_STRIDE);
+    // group's values are formed
     uint32_t hp[8], lp[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) hp[i] = lp[i] = 0u;
@@ -401,7 +400,6 @@ __device__ __forceinline__ void rolled_tile_epilogue(
     for (int gg = 0; gg < 4; ++gg) {
       const int cb = cb16 + 4 * gg;
       if (!OFF && r > cb + 3) continue;
-      float nw[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int e = 4 * gg + i;
@@ -414,7 +412,6 @@ __device__ __forceinline__ void rolled_tile_epilogue(
         const float dd = old - xv;
         fd = own ? fmaf(w * dd, dd, fd) : fd;
         const float n1 = sg * xv + om * old;
-        nw[i] = n1;
         if (own && write) {
           const float p = w * n1 * n1;
           const float ee = w * fmaf(n1, n1, -n1 * n1);
@@ -430,35 +427,22 @@ __device__ __forceinline__ void rolled_tile_epilogue(
         const uint32_t lbits = h16_bits(CV::to(y - CV::from(h)));
         hp[e >> 1] |= hbits << (16 * (e & 1));
         lp[e >> 1] |= lbits << (16 * (e & 1));
-        if (write && (OFF || c > r)) {   // mirror (c, r), down the column
+        if (write && own) {   // (c, r), down the column
           const int m = (c - c0) * np;
           Snc[m] = n1;
-          hic[m] = (uint16_t)hbits;
-          loc[m] = (uint16_t)lbits;
+          if (OFF || c > r) {   // the 16-bit mirror; the diagonal goes with the rows
+            hic[m] = (uint16_t)hbits;
+            loc[m] = (uint16_t)lbits;
+          }
         }
       }
-      xr[gg] = make_float4(nw[0], nw[1], nw[2], nw[3]);
     }
     if (g16 < NG - 1) {
 #pragma unroll
       for (int q = 0; q < 16; ++q) olds[q] = __ldg(Sc + (16 * (g16 + 1) + q) * np);
     }
     if (!write) continue;
-    // ---- row direction (r, c) through the transpose buffer
-    __syncwarp();
-#pragma unroll
-    for (int sidx = 0; sidx < 8; ++sidx) {
-      const int i = (sidx & 3) + 16 * (sidx >> 2) + 4 * (lane >> 3);   // rows i, +4, +8, +12
-      const int w2 = 2 * (lane & 7);
-      const float2 v = *reinterpret_cast<const float2*>(xp + i * XP_STRIDE + w2);
-      const int rr = r0 + i, c = cb16 + w2;
-      float* dst = Snr + i * np + (c - c0);
-      if (OFF || c >= rr)
-        *reinterpret_cast<float2*>(dst) = v;
-      else if (c + 1 >= rr)
-        dst[1] = v.y;
-    }
-    __syncwarp();
+    // ---- 16-bit copies in the row direction (r, c) through the transpose buffer
     uint4* xr4 = reinterpret_cast<uint4*>(xp + lane * XP_STRIDE);
     xr4[0] = make_uint4(hp[0], hp[1], hp[2], hp[3]);
     xr4[1] = make_uint4(hp[4], hp[5], hp[6], hp[7]);
