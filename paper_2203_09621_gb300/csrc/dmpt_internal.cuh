@@ -305,14 +305,14 @@ cudaError_t launch_gather_states(const void* base, const long long* offs, int co
 // initial layer (Alg. 1: bounds, S_0 and S_1 of Sec. III A, the first decide)
 // and one for the outputs serve every active instance.  Each step splits its
 // work into units (groups of kBatchRows rows for the bounds, the initial
-// layer's blocks, chunks of kBatchChunk elements for the 16-bit split, 32 x 32
+// layer's blocks, chunks of kBatchChunk elements for the 16-bit split, 64 x 64
 // tiles of one output matrix); first[s * (count + 1) + i] is the first unit
 // of instance i in step s (exclusive prefix sums), so unit u belongs to the
 // instance i with first[i] <= u < first[i + 1].  Every instance's values are those of
 // its single-instance launches: the bounds are exact minima and maxima, the
 // initial layer keeps its kInitBlocks virtual blocks (the ones without tile
 // pairs only hold zero partial sums, which the set-up writes), and the split
-// and the outputs are elementwise (the outputs through the same 32 x 32 tiles).
+// and the outputs are elementwise (the outputs through the same 64 x 64 tiles).
 constexpr int kInitBlocks = 1024;   // blocks (partial-sum entries) of the initial layer
 constexpr int kInitTile = 64;       // tile edge of the initial layer (Np is a multiple of 128)
 constexpr int kBatchRows = 8;       // rows per warp of the batched bounds
@@ -345,7 +345,7 @@ __host__ __device__ inline int64_t batch_units(int step, int64_t n, int64_t Np, 
     case kBsRows: return (n + kBatchRows - 1) / kBatchRows;
     case kBsInit: return pairs < kInitBlocks ? pairs : kInitBlocks;
     case kBsSplit: return (int64_t)(1 + k) * ((Np * Np + kBatchChunk - 1) / kBatchChunk);
-    default: return (int64_t)(1 + k) * ((n + 31) / 32) * ((n + 31) / 32);
+    default: return (int64_t)(1 + k) * ((n + 63) / 64) * ((n + 63) / 64);   // output tiles
   }
 }
 // Fresh control blocks, bounds keys and the zero partial sums of the

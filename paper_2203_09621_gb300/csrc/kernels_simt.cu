@@ -1151,24 +1151,31 @@ cudaError_t launch_split(const Layout& L, void* ws, int first_job, cudaStream_t 
 // Whole-matrix readers of the masters.  The tensor-core layer epilogue keeps
 // an FP32 master in one orientation only (element (r, c) at (max, min): the
 // lower triangle with the diagonal); the other kernels write both.  So a
-// reader takes output tile (bi, bj) (32 x 32, 256 threads) from the lower
-// tile (max(bi, bj), min(bi, bj)): loaded row by row (coalesced) into shared
-// memory, written row by row, transposed where the output tile lies above
-// the diagonal.  `put(r, c, v)` writes the value of element (r, c), r, c < n.
+// reader takes output tile (bi, bj) (kSymTile x kSymTile, 256 threads) from
+// the lower tile (max(bi, bj), min(bi, bj)): loaded row by row (coalesced,
+// every load of the tile in flight at once) into shared memory, written row
+// by row, transposed where the output tile lies above the diagonal.
+// `put(r, c, v)` writes the value of element (r, c), r, c < n.
+constexpr int kSymTile = 64;
 template <typename T, class Put>
 __device__ __forceinline__ void sym_tile(const T* __restrict__ src, int64_t Np, int64_t n,
-                                         int64_t bi, int64_t bj, T (*t)[33], Put put) {
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
-  const int64_t lr = 32 * (bi > bj ? bi : bj), lc = 32 * (bi > bj ? bj : bi);
+                                         int64_t bi, int64_t bj, T (*t)[kSymTile + 1], Put put) {
+  constexpr int TS = kSymTile, RS = 256 / TS, RPT = TS / RS;   // 64 x 4 threads, 16 rows each
+  const int tx = threadIdx.x % TS, ty = threadIdx.x / TS;
+  const int64_t lr = TS * (bi > bj ? bi : bj), lc = TS * (bi > bj ? bj : bi);
+  T v[RPT];
 #pragma unroll
-  for (int i = ty; i < 32; i += 8) t[i][tx] = src[(lr + i) * Np + lc + tx];
+  for (int j = 0; j < RPT; ++j) v[j] = src[(lr + ty + RS * j) * Np + lc + tx];
+#pragma unroll
+  for (int j = 0; j < RPT; ++j) t[ty + RS * j][tx] = v[j];
   __syncthreads();
 #pragma unroll
-  for (int i = ty; i < 32; i += 8) {
-    const int64_t r = 32 * bi + i, c = 32 * bj + tx;
+  for (int j = 0; j < RPT; ++j) {
+    const int i = ty + RS * j;
+    const int64_t r = TS * bi + i, c = TS * bj + tx;
     if (r < n && c < n) {
-      const T v = bi > bj ? t[i][tx] : (bi < bj ? t[tx][i] : (tx <= i ? t[i][tx] : t[tx][i]));
-      put(r, c, v);
+      const T x = bi > bj ? t[i][tx] : (bi < bj ? t[tx][i] : (tx <= i ? t[i][tx] : t[tx][i]));
+      put(r, c, x);
     }
   }
   __syncthreads();   // the block's next tile reuses t
@@ -1219,8 +1226,8 @@ __global__ void seg_load_kernel(State* st, float4* master, const float4* __restr
 // checkpoint of a state that a tensor-core layer wrote holds only the lower
 // one; the hi/lo split that follows a reload reads the whole matrix).
 __global__ void __launch_bounds__(256) mirror_lower_kernel(float* M, int64_t Np) {
-  __shared__ float t[32][33];
-  const int64_t tb = Np / 32;
+  __shared__ float t[kSymTile][kSymTile + 1];
+  const int64_t tb = Np / kSymTile;
   for (int64_t tile = blockIdx.x; tile < tb * tb; tile += gridDim.x) {
     const int64_t bi = tile / tb, bj = tile % tb;
     if (bi > bj) continue;   // uniform across the block: lower tiles are only read
@@ -1346,11 +1353,11 @@ __global__ void __launch_bounds__(256) adj_finalize_kernel(const State* st,
                                                            const float* __restrict__ master,
                                                            double* dLdH, int64_t n, int64_t Np,
                                                            int64_t ld, int lk) {
-  __shared__ float t[32][33];
+  __shared__ float t[kSymTile][kSymTile + 1];
   const size_t mat = (size_t)Np * Np;
   const float* src = master + (size_t)(st->cur1[0] * (1 + lk) + 1) * mat;
   const double scale = -1.0 / (st->epsN - st->eps1);
-  const int64_t tb = (n + 31) / 32;
+  const int64_t tb = (n + kSymTile - 1) / kSymTile;
   for (int64_t tile = blockIdx.x; tile < tb * tb; tile += gridDim.x)
     sym_tile<float>(src, Np, n, tile / tb, tile % tb, t, [&](int64_t r, int64_t c, float v) {
       dLdH[r * ld + c] = scale * (double)v;
@@ -1382,8 +1389,8 @@ __global__ void __launch_bounds__(256) finalize_kernel(const State* st,
                                                        double* P1, int64_t n, int64_t Np,
                                                        int64_t ld, int k, int slot0) {
   // k: layout slots; grid.y = 1 + the number of blocks written to P1, which
-  // come from slots slot0, slot0 + 1, ...; 32 x 32 output tiles
-  __shared__ T t[32][33];
+  // come from slots slot0, slot0 + 1, ...; kSymTile x kSymTile output tiles
+  __shared__ T t[kSymTile][kSymTile + 1];
   const size_t mat = (size_t)Np * Np;
   const int y = blockIdx.y;
   if (y == 0 && P == nullptr) return;
@@ -1392,7 +1399,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(const State* st,
   const T* src = master + (size_t)(cur * (1 + k) + m) * mat;
   double* dst = y == 0 ? P : P1 + (size_t)(y - 1) * n * ld;
   const bool hole = st->hole != 0;
-  const int64_t tb = (n + 31) / 32;
+  const int64_t tb = (n + kSymTile - 1) / kSymTile;
   for (int64_t tile = blockIdx.x; tile < tb * tb; tile += gridDim.x)
     sym_tile<T>(src, Np, n, tile / tb, tile % tb, t, [&](int64_t r, int64_t c, T v) {
       dst[r * ld + c] = out_value((double)v, r, c, y, hole);
@@ -1603,17 +1610,18 @@ __global__ void __launch_bounds__(256) batch_split_kernel(const BatchInst* __res
 }
 
 // Outputs (as finalize_kernel with slot0 = 1): unit c of matrix y (0 = P,
-// 1 + j = P1_j) is output tile c of that matrix (32 x 32 tiles, row-major).
+// 1 + j = P1_j) is output tile c of that matrix (kSymTile x kSymTile tiles,
+// row-major).
 template <typename T>
 __global__ void __launch_bounds__(256) batch_finalize_kernel(const BatchInst* __restrict__ bi,
                                                              const int64_t* __restrict__ first,
                                                              int count) {
-  __shared__ T t[32][33];
+  __shared__ T t[kSymTile][kSymTile + 1];
   const int64_t u = blockIdx.x;
   const int i = batch_find(first, count, u);
   const BatchInst& b = bi[i];
   const int64_t n = b.n;
-  const int64_t tb = (n + 31) / 32;
+  const int64_t tb = (n + kSymTile - 1) / kSymTile;
   const int64_t c = u - first[i];
   const int y = (int)(c / (tb * tb));
   if (y == 0 && b.P == nullptr) return;
