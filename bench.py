@@ -489,7 +489,7 @@ def main():
     e2e_ms, e2e_rate = aggregate(e0.elapsed_time(e1) / e_steps, alg, world)
     e2e_val = e2e_rate / 1e12
     e2e_same = bool(torch.equal(P1e[-1], P1.cpu()))
-    h2d = (H.numel() + H1.numel()) * 8
+    h2d = ctx.host_copy_in_bytes(n, k)   # the upper triangles of H and H1
     d2h = P1.numel() * 8
     # the host link, measured alone: what the copies of one step cost if
     # nothing overlapped them, against the step's exposed extra time

@@ -45,6 +45,7 @@ extern "C" {
 #define DMPT_MAX_K 8        /* response slots per call: directions x order */
 #define DMPT_MAX_ORDER 8    /* highest response order (k = 1)             */
 #define DMPT_MAX_LAYERS 256 /* upper bound of dmpt_options.max_layers      */
+#define DMPT_HOST_ROW_BLOCK 512 /* rows per copy of dmpt_sp2_response_host  */
 #define DMPT_MAX_TIMEOUT_S 600.0 /* upper bound of dmpt_options.timeout_s  */
 
 typedef enum {
@@ -376,7 +377,11 @@ dmpt_status dmpt_scc_response(dmpt_handle h, const double* H1_ext, const double*
  * (Algorithms 1-3 for each, as dmpt_sp2_response with ld = n).  Inputs are
  * copied in and results copied out on two copy streams of the handle, with
  * two device buffer sets, so that the copy-in of instance i+1 and the
- * copy-out of instance i-1 run while instance i is being solved.
+ * copy-out of instance i-1 run while instance i is being solved.  Only the
+ * upper triangle (j >= i) of each input matrix is read: rows are copied in
+ * blocks of DMPT_HOST_ROW_BLOCK rows, from the block's diagonal to the end of
+ * the row (dmpt_host_copy_in_bytes() bytes per instance, about half of the
+ * matrices), and the device fills the lower triangle from the upper one.
  *   count      instances (>= 0).
  *   H_host     host array of `count` pointers to n x n row-major float64
  *              matrices in host memory.
@@ -395,6 +400,9 @@ dmpt_status dmpt_scc_response(dmpt_handle h, const double* H1_ext, const double*
  * every result is in host memory.  Returns the first instance's non-OK
  * status; the instances after it are not run. */
 size_t dmpt_workspace_size_host(int64_t n, int k, const dmpt_options* o);
+/* Bytes dmpt_sp2_response_host copies to the device per instance of size n
+ * with k directions (0 on invalid n or k). */
+size_t dmpt_host_copy_in_bytes(int64_t n, int k);
 dmpt_status dmpt_sp2_response_host(dmpt_handle h, int count, const double* const* H_host,
                                    const double* const* H1_host, int k, int64_t n,
                                    int64_t n_occ, const dmpt_options* o,

@@ -668,6 +668,18 @@ dmpt_status dmpt_autotune(dmpt_handle h, const double* H, const double* H1, int 
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Bytes one instance's copy-in moves: the upper triangle of each matrix, in
+// row blocks of DMPT_HOST_ROW_BLOCK rows from the block's diagonal onwards.
+size_t dmpt_host_copy_in_bytes(int64_t n, int k) {
+  if (n < 1 || k < 0 || k > DMPT_MAX_K) return 0;
+  size_t per = 0;
+  for (int64_t r0 = 0; r0 < n; r0 += DMPT_HOST_ROW_BLOCK) {
+    const int64_t rows = n - r0 < DMPT_HOST_ROW_BLOCK ? n - r0 : DMPT_HOST_ROW_BLOCK;
+    per += (size_t)rows * (size_t)(n - r0) * sizeof(double);
+  }
+  return per * (size_t)(1 + k);
+}
+
 size_t dmpt_workspace_size_host(int64_t n, int k, const dmpt_options* o) {
   const size_t ws = dmpt_workspace_size(n, k, o);
   if (!ws) return 0;
@@ -730,11 +742,23 @@ dmpt_status dmpt_sp2_response_host(dmpt_handle h, int count, const double* const
   // Instance i uses buffer set i % 2.  The copy-in of i + 1 is issued after
   // the solve of i - 1 has returned (forward_impl synchronises `stream`), so
   // the set it overwrites is no longer read.
+  // Only the upper triangle (j >= i) of each matrix is copied: row blocks of
+  // DMPT_HOST_ROW_BLOCK rows from the block's diagonal to the end of the row;
+  // the solve's stream then fills the lower triangle from the upper one.
   auto copy_in = [&](int i) -> cudaError_t {
     double* d = in[i & 1];
-    cudaError_t r = cudaMemcpyAsync(d, H_host[i], mat, cudaMemcpyHostToDevice, h->copy_in);
-    if (r == cudaSuccess && k > 0)
-      r = cudaMemcpyAsync(d + nn, H1_host[i], mat * k, cudaMemcpyHostToDevice, h->copy_in);
+    cudaError_t r = cudaSuccess;
+    for (int m = 0; m <= k && r == cudaSuccess; ++m) {
+      const double* src = m == 0 ? H_host[i] : H1_host[i] + (size_t)(m - 1) * nn;
+      double* dst = d + (size_t)m * nn;
+      for (int64_t r0 = 0; r0 < n && r == cudaSuccess; r0 += DMPT_HOST_ROW_BLOCK) {
+        const int64_t rows = n - r0 < DMPT_HOST_ROW_BLOCK ? n - r0 : DMPT_HOST_ROW_BLOCK;
+        const size_t off = (size_t)r0 * n + r0;
+        r = cudaMemcpy2DAsync(dst + off, n * sizeof(double), src + off, n * sizeof(double),
+                              (size_t)(n - r0) * sizeof(double), (size_t)rows,
+                              cudaMemcpyHostToDevice, h->copy_in);
+      }
+    }
     if (r == cudaSuccess) r = cudaEventRecord(h->ev_in[i & 1], h->copy_in);
     return r;
   };
@@ -750,6 +774,10 @@ dmpt_status dmpt_sp2_response_host(dmpt_handle h, int count, const double* const
     if ((e = cudaStreamWaitEvent(s, h->ev_in[b], 0)) != cudaSuccess ||
         (i >= 2 && (e = cudaStreamWaitEvent(s, h->ev_out[b], 0)) != cudaSuccess)) {
       status = cuda_fail(h, e, "copy ordering");
+      break;
+    }
+    if ((e = launch_mirror_upper(in[b], n, n, 1 + k, s)) != cudaSuccess) {
+      status = cuda_fail(h, e, "input mirror");
       break;
     }
     double* Pd = out[b];

@@ -211,6 +211,9 @@ cudaError_t launch_adj_finalize(const Layout& L, void* ws, double* dLdH, int64_t
 // P (if not NULL) and k_out response blocks from slots slot0 .. slot0 + k_out - 1
 cudaError_t launch_finalize(const Layout& L, void* ws, double* P, double* P1,
                             int64_t ld, int k_out, cudaStream_t s, int slot0 = 1);
+// The lower triangle of `count` n x n float64 matrices (row stride ld, one
+// after another at n * ld) from their upper triangles.
+cudaError_t launch_mirror_upper(double* M, int64_t n, int64_t ld, int count, cudaStream_t s);
 cudaError_t launch_trivial(int64_t n, int k, int64_t ld, int full, double* P,
                            double* P1, cudaStream_t s);
 int simt_tile(int precision);

@@ -1235,6 +1235,43 @@ __global__ void __launch_bounds__(256) mirror_lower_kernel(float* M, int64_t Np)
   }
 }
 
+// M[r][c] = M[c][r] for r > c, count matrices: lower output tile (bi, bj)
+// from upper tile (bj, bi), loaded row by row and transposed through shared
+// memory; a diagonal tile mirrors its own upper half.
+__global__ void __launch_bounds__(256) mirror_upper_kernel(double* M, int64_t n, int64_t ld) {
+  constexpr int TS = kSymTile, RS = 256 / TS, RPT = TS / RS;
+  __shared__ double t[TS][TS + 1];
+  double* A = M + (size_t)blockIdx.y * n * ld;
+  const int tx = threadIdx.x % TS, ty = threadIdx.x / TS;
+  const int64_t tb = (n + TS - 1) / TS;
+  for (int64_t tile = blockIdx.x; tile < tb * tb; tile += gridDim.x) {
+    const int64_t bi = tile / tb, bj = tile % tb;
+    if (bi < bj) continue;   // uniform across the block: upper tiles are only read
+    double v[RPT];
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+      const int64_t r = TS * bj + ty + RS * j, c = TS * bi + tx;   // upper tile (bj, bi)
+      v[j] = (r < n && c < n) ? A[r * ld + c] : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) t[ty + RS * j][tx] = v[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+      const int i = ty + RS * j;
+      const int64_t r = TS * bi + i, c = TS * bj + tx;
+      if (r < n && c < n && r > c) A[r * ld + c] = t[tx][i];
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_mirror_upper(double* M, int64_t n, int64_t ld, int count, cudaStream_t s) {
+  if (count < 1 || n < 1) return cudaSuccess;
+  mirror_upper_kernel<<<dim3(152 * 8, count), 256, 0, s>>>(M, n, ld);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_seg_load(const Layout& L, void* ws, int c, int a, cudaStream_t s) {
   if (c < 0 || c >= L.ckpt_slots) return cudaErrorInvalidValue;
   char* base = (char*)ws;

@@ -131,6 +131,8 @@ def load_library(path: str = LIB_PATH):
     lib.dmpt_autotune.restype = c_int
     lib.dmpt_workspace_size_host.argtypes = [i64, c_int, ctypes.POINTER(DmptOptions)]
     lib.dmpt_workspace_size_host.restype = ctypes.c_size_t
+    lib.dmpt_host_copy_in_bytes.argtypes = [i64, c_int]
+    lib.dmpt_host_copy_in_bytes.restype = ctypes.c_size_t
     lib.dmpt_sp2_response_host.argtypes = [vp, c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int,
                                            i64, i64, ctypes.POINTER(DmptOptions),
                                            ctypes.POINTER(vp), ctypes.POINTER(vp),
@@ -535,11 +537,16 @@ class Context:
             self._check(st)
         return P1, its.value, res.value, Info.from_c(info, k)
 
+    def host_copy_in_bytes(self, n: int, k: int) -> int:
+        """Bytes solve_host copies to the device per instance (the upper
+        triangles of H and the k perturbations)."""
+        return int(self.lib.dmpt_host_copy_in_bytes(n, k))
+
     def solve_host(self, Hs, H1s, n_occ: int, P1_out=None, P_out=None, precision="dual_fp16",
                    stream=None, raise_on_error=True, workspace=None, **kw):
         """Instances held in host memory (dmpt_sp2_response_host): lists of
         (n, n) and (k, n, n) float64 CPU tensors, pinned for the copies to
-        overlap the solves.  Results go to `P1_out` / `P_out` (lists of CPU
+        overlap the solves; only their upper triangles are read.  Results go to `P1_out` / `P_out` (lists of CPU
         tensors, allocated pinned when None; P is copied out only when
         `P_out` is given).  Returns (P list or None, P1 list, Info list)."""
         import torch

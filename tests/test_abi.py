@@ -150,6 +150,16 @@ def test_host_pipeline_sizes_and_argument_errors(lib):
         assert lib.dmpt_workspace_size_host(n, k, ctypes.byref(o)) == -(-ws // 256) * 256 + 4 * io
     assert lib.dmpt_workspace_size_host(0, 1, ctypes.byref(o)) == 0
     assert lib.dmpt_workspace_size_host(100, 9, ctypes.byref(o)) == 0
+    # the copy-in moves the upper triangles in row blocks of 512 rows
+    lib.dmpt_host_copy_in_bytes.restype = ctypes.c_size_t
+    lib.dmpt_host_copy_in_bytes.argtypes = [ctypes.c_int64, ctypes.c_int]
+    for n, k in ((1000, 1), (8192, 3), (300, 0), (512, 2), (513, 2)):
+        want = sum(min(512, n - r0) * (n - r0) * 8 for r0 in range(0, n, 512)) * (1 + k)
+        got = lib.dmpt_host_copy_in_bytes(n, k)
+        assert got == want, (n, k, got, want)
+        assert n <= 512 or got < n * n * 8 * (1 + k)
+    assert lib.dmpt_host_copy_in_bytes(8192, 3) == 4 * 8192 * 8704 * 4
+    assert lib.dmpt_host_copy_in_bytes(0, 1) == 0 and lib.dmpt_host_copy_in_bytes(10, 9) == 0
     # null handle
     assert lib.dmpt_sp2_response_host(None, 1, None, None, 1, 4, 2, None, None, None, None,
                                       None, 0, None) == 1

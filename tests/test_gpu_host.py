@@ -1,8 +1,9 @@
 """GPU parity of the host-buffer pipeline (dmpt_sp2_response_host).
 
-Each instance is copied in, solved by the same kernels in the same order as
-dmpt_sp2_response on device buffers, and copied out, with the copies of the
-neighbouring instances overlapping the solve; the results must equal the
+Each instance's upper triangles are copied in (the device mirrors them),
+solved by the same kernels in the same order as dmpt_sp2_response on device
+buffers, and copied out, with the copies of the neighbouring instances
+overlapping the solve; for symmetric inputs the results must equal the
 device call's bit for bit and the oracle within the dual tolerance.
 """
 
@@ -53,6 +54,28 @@ def test_pipeline_matches_device_calls(ctx, pinned):
         for j in range(k):
             _, P1r = oracle.response_sos(x.H, x.H1[j], x.n_occ)
             assert rel(P1s[i][j].numpy(), P1r) < 1e-3
+
+
+def test_only_upper_triangles_are_read(ctx):
+    """The pipeline copies the upper triangles only: NaN in the strict lower
+    triangles of the host inputs changes nothing (n = 1100 spans three
+    512-row copy blocks and a ragged tail)."""
+    n, k = 1100, 2
+    x = make_instance("upper", n, n // 2, (-2.0, -0.1), (0.1, 2.0), seed=7300, k=k)
+    low = np.tril(np.ones((n, n), dtype=bool), -1)
+    Hn = x.H.copy()
+    Hn[low] = np.nan
+    H1n = x.H1.copy()
+    H1n[:, low] = np.nan
+    P_out = [torch.empty(n, n, dtype=torch.float64)]
+    Ps, P1s, infos = ctx.solve_host([torch.from_numpy(Hn).pin_memory()],
+                                    [torch.from_numpy(H1n).pin_memory()], x.n_occ, P_out=P_out)
+    Pd, P1d, info_d = ctx.sp2_response(torch.from_numpy(x.H).to(DEV),
+                                       torch.from_numpy(x.H1).to(DEV), x.n_occ)
+    torch.cuda.synchronize()
+    assert infos[0].converged and infos[0].layers == info_d.layers
+    assert torch.equal(Ps[0], Pd.cpu()) and torch.equal(P1s[0], P1d.cpu())
+    assert ctx.host_copy_in_bytes(n, k) < n * n * 8 * (1 + k)
 
 
 def test_single_instance_and_trivial(ctx):
